@@ -1,0 +1,222 @@
+/*
+ * ash.h -- C ABI of the aberration-space holography library (GB300, sm_103a).
+ *
+ * The library computes the compressed spot transform of aberration-space
+ * holography (Christen et al., arXiv 2505.08777) and the weighted
+ * Gerchberg-Saxton loop built on it, with hand-written CUDA kernels. It never
+ * forms the N x M kernel matrix: every kernel value exp(-i C_n . Z_m) is
+ * evaluated on the fly.
+ *
+ * Notation (paper Sec. II and Methods "Computational Scaling"):
+ *   nx, ny  SLM grid; pixel (i, j) = column i, row j; M = nx*ny;
+ *           per-pixel arrays are row-major [ny][nx], flat index m = j*nx + i.
+ *   D       number of basis modes Z_d (Zernike polynomials in Noll order, or
+ *           a caller-supplied basis).
+ *   N       number of spots; C is the N x D coefficient matrix w_d^(n),
+ *           row-major [N][D], radians per unit of basis value.
+ *   A_m     illumination amplitude (real); phi_m SLM phase;
+ *           f_m = A_m exp(i phi_m) the nearfield.
+ *   Forward  E_n = sum_m f_m exp(-i C_n . Z_m)          (Sec. II, F_n = F_c{f})
+ *   Adjoint  g_m = sum_n y_n exp(+i C_n . Z_m)          (Sec. II, f = F_c^-1{F})
+ *   Sums are unnormalised (the paper writes them up to proportionality).
+ *
+ * Zernike basis (when a Noll list is given): pixel coordinates
+ *   x = (i - (nx-1)/2)/R, y = (j - (ny-1)/2)/R, R = min(nx, ny)/2,
+ *   Z = R_n^|m|(rho) cos(m theta) (m >= 0) or R_n^|m|(rho) sin(|m| theta)
+ *   (m < 0), no RMS normalisation; pixels outside the unit disk keep their
+ *   polynomial values. Noll 2/3 are the x/y tilts, Noll 4 defocus (Sec. II).
+ *
+ * Complex arrays are interleaved float pairs (re, im), i.e. complex64.
+ *
+ * Ownership: the caller owns every buffer passed in; all of them are device
+ * pointers unless a parameter says "host". The handle owns its workspace
+ * (basis in a tiled internal layout, copied coefficients, anchor table,
+ * forward partial sums), allocated in ash_hologram_create (through the
+ * allocator hook, see ash_set_allocator) and freed in ash_hologram_destroy.
+ * The handle keeps no pointer to caller buffers after a call returns.
+ *
+ * Streams: every call enqueues its work on `stream` (a cudaStream_t; NULL =
+ * legacy default stream) and returns without synchronising, except where a
+ * description says otherwise. A handle must not be used from two streams at
+ * once (calls share the handle's workspace).
+ *
+ * Errors: every call returns an ash_status. Invalid arguments return
+ * ASH_ERR_INVALID_ARG before anything is launched. CUDA failures return
+ * ASH_ERR_CUDA; ash_last_error() gives a message (per host thread). Nothing
+ * aborts the process. Kernels never spin on another CTA; device-side faults
+ * that a kernel detects set an error word that ash_hologram_check() reports.
+ *
+ * Precision: inputs FP32, arithmetic FP32 with complex64 accumulation;
+ * per-(spot, tile) base phases are reduced exactly in turns from FP64-derived
+ * tables so that tilts of thousands of radians keep ~1e-6 rad phase error.
+ */
+#ifndef ASH_H
+#define ASH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ASH_ABI_VERSION 1
+
+typedef enum {
+  ASH_OK = 0,
+  ASH_ERR_INVALID_ARG = 1,
+  ASH_ERR_CUDA = 2,
+  ASH_ERR_OOM = 3,
+  ASH_ERR_TIMEOUT = 4,
+  ASH_ERR_UNSUPPORTED = 5,
+  ASH_ERR_INJECTED = 6,
+  ASH_ERR_DEVICE = 7
+} ash_status;
+
+/* Opaque handle: one hologram (grid, amplitude, basis, coefficients). */
+typedef struct ash_hologram ash_hologram;
+
+/* Largest supported number of basis modes D. */
+#define ASH_MAX_MODES 16
+
+/* ABI version of the loaded library (ASH_ABI_VERSION at build time). */
+int ash_abi_version(void);
+
+/* Human-readable name of a status code (static string). */
+const char *ash_status_string(ash_status s);
+
+/* Last error message recorded on the calling host thread ("" if none). */
+const char *ash_last_error(void);
+
+/*
+ * Allocator hook for the handle workspaces. alloc(ctx, bytes, stream) returns
+ * a device pointer or NULL (reported as ASH_ERR_OOM); free(ctx, ptr, stream)
+ * releases it. Passing NULL for both restores cudaMallocAsync/cudaFreeAsync.
+ * Process-wide; set it before creating handles.
+ */
+typedef void *(*ash_alloc_fn)(void *ctx, size_t bytes, void *stream);
+typedef void (*ash_free_fn)(void *ctx, void *ptr, void *stream);
+ash_status ash_set_allocator(ash_alloc_fn alloc, ash_free_fn free_fn, void *ctx);
+
+/*
+ * Host-side fault injection for tests: the n-th API call from now (n >= 1)
+ * that would launch work returns ASH_ERR_INJECTED without launching; n = 0
+ * disables it. Process-wide.
+ */
+ash_status ash_debug_fail_after(int n_calls);
+
+/*
+ * Create a hologram (paper Sec. II: kernels K_n built from the N x D matrix
+ * w_d^(n) and the per-pixel basis, Methods "Computational Scaling").
+ *   out     host: receives the handle.
+ *   nx, ny  grid, 1 <= nx, ny <= 16384.
+ *   amp     device float[ny*nx], illumination amplitude A (row-major).
+ *   D       number of modes, 1 <= D <= ASH_MAX_MODES.
+ *   noll    host int[D] Noll indices (>= 1, <= 231) of the Zernike modes, or
+ *           NULL when `basis` is given.
+ *   basis   device float[D*ny*nx], caller basis, row d = Z_d over the grid
+ *           (row-major), or NULL when `noll` is given. Exactly one of noll /
+ *           basis must be non-NULL.
+ *   N       number of spots, 1 <= N <= 1<<20.
+ *   coeff   device float[N*D], C row-major.
+ *   stream  cudaStream_t for the set-up kernels.
+ * The basis is materialised once, relative to per-tile anchor pixels, in a
+ * tiled internal layout (FP64 evaluation of the monomial expansion for Noll
+ * lists). Returns ASH_ERR_OOM if the workspace cannot be allocated.
+ * Synchronises `stream` before returning (the set-up kernels and the
+ * stream-ordered allocations are complete when the handle is returned).
+ */
+ash_status ash_hologram_create(ash_hologram **out, int nx, int ny, const float *amp, int D,
+                               const int *noll, const float *basis, int N, const float *coeff,
+                               void *stream);
+
+/* Destroy a handle (NULL is ignored). Synchronises the device (work on any
+ * stream may still use the workspace), then frees the workspace. */
+void ash_hologram_destroy(ash_hologram *h);
+
+/* Sizes of a handle: any output pointer may be NULL. */
+ash_status ash_hologram_info(const ash_hologram *h, int *nx, int *ny, int *N, int *D,
+                             size_t *workspace_bytes);
+
+/* Replace the coefficient matrix C (device float[N*D]); same N and D. */
+ash_status ash_set_coefficients(ash_hologram *h, const float *coeff, void *stream);
+
+/* Replace the illumination amplitude A (device float[ny*nx]). */
+ash_status ash_set_amplitude(ash_hologram *h, const float *amp, void *stream);
+
+/*
+ * Forward transform of a phase-only hologram (Sec. II, F_n = F_c{f}):
+ *   E_n = sum_m A_m exp(i phase_m) exp(-i C_n . Z_m).
+ *   phase  device float[ny*nx].
+ *   E      device float[2*N] (complex64), overwritten.
+ * Deterministic: partial sums are reduced in a fixed order.
+ */
+ash_status ash_forward(ash_hologram *h, const float *phase, float *E, void *stream);
+
+/*
+ * Forward transform of a general complex nearfield (amplitude ignored):
+ *   E_n = sum_m f_m exp(-i C_n . Z_m).
+ *   field  device float[2*ny*nx] (complex64).
+ *   E      device float[2*N] (complex64), overwritten.
+ */
+ash_status ash_forward_field(ash_hologram *h, const float *field, float *E, void *stream);
+
+/*
+ * Adjoint transform (Sec. II, f = F_c^-1{F}, the merge of all N kernels):
+ *   g_m = sum_n y_n exp(+i C_n . Z_m).
+ *   y          device float[2*N] (complex64).
+ *   g          device float[2*ny*nx] (complex64) or NULL.
+ *   phase_out  device float[ny*nx] or NULL: phase_out_m = arg g_m (0 where
+ *              g_m == 0), the phase-only projection used by GS.
+ * At least one of g / phase_out must be non-NULL.
+ */
+ash_status ash_adjoint(ash_hologram *h, const float *y, float *g, float *phase_out, void *stream);
+
+/*
+ * Weighted Gerchberg-Saxton iterations (Sec. II; Sec. III uses weighted GS).
+ * The paper does not print the update rule; this library implements:
+ *   init (caller): w = T, phase given.   T^ = T/||T||_2
+ *   each iteration:  E = forward(phase);  E^ = |E|/||E||_2;
+ *                    w <- w * T^ / max(E^, 1e-30);  w <- w/||w||_2;
+ *                    phase <- arg adjoint(w exp(i arg E)).
+ *   after the last iteration one more forward gives E_out and the metrics.
+ *   phase        device float[ny*nx], in/out (the loop state).
+ *   w            device float[N], in/out (the loop state).
+ *   target       device float[N], target amplitudes T (> 0).
+ *   iters        >= 0.
+ *   E_out        device float[2*N] or NULL: field of the final phase.
+ *   metrics_out  device float[4] or NULL: {uniformity, efficiency,
+ *                sum |E|^2, min |E|^2/T^2}; uniformity
+ *                U = 1 - (max I^ - min I^)/(max I^ + min I^), I^_n = |E_n|^2/T_n^2;
+ *                efficiency = sum |E|^2 / (M sum A^2).
+ * The state is exactly (phase, w): running k iterations twice equals running
+ * 2k iterations once, bit for bit. The loop is enqueued as a CUDA graph when
+ * iters > 1 (captured on first use per handle and iteration count).
+ */
+ash_status ash_wgs_iterate(ash_hologram *h, float *phase, float *w, const float *target, int iters,
+                           float *E_out, float *metrics_out, void *stream);
+
+/*
+ * Gradient through the forward transform (Methods: gradients propagated
+ * forward and backward through the transform). Given grad_E = dL/dRe(E) +
+ * i dL/dIm(E) for E = forward(phase):
+ *   dphase_m = -Im(f_m conj(h_m)),  h = K^H grad_E      (adjoint pass)
+ *   dcoeff_nd = Im(conj(grad_E_n) S_nd), S_nd = sum_m Z_dm f_m K_nm
+ *               (forward pass with D moments, tiles recomputed).
+ *   phase   device float[ny*nx];  grad_E device float[2*N];
+ *   dphase  device float[ny*nx] or NULL;  dcoeff device float[N*D] or NULL.
+ */
+ash_status ash_grad(ash_hologram *h, const float *phase, const float *grad_E, float *dphase,
+                    float *dcoeff, void *stream);
+
+/*
+ * Synchronise `stream` and report device-side errors recorded by the
+ * handle's kernels (ASH_ERR_DEVICE / ASH_ERR_TIMEOUT), clearing them.
+ */
+ash_status ash_hologram_check(ash_hologram *h, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ASH_H */

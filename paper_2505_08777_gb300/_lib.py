@@ -1,0 +1,75 @@
+"""ctypes loader for libash.so (the C ABI declared in include/ash.h).
+
+Loading never falls back to anything: if the shared library is missing or
+does not export the ABI, an error is raised.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libash.so")
+
+c_int, c_float_p, c_void_p = ctypes.c_int, ctypes.POINTER(ctypes.c_float), ctypes.c_void_p
+c_int_p = ctypes.POINTER(ctypes.c_int)
+c_size_t = ctypes.c_size_t
+
+ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, c_void_p, c_size_t, c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, c_void_p, c_void_p, c_void_p)
+
+# name -> (restype, argtypes); every name here is declared in include/ash.h
+SIGNATURES = {
+    "ash_abi_version": (c_int, []),
+    "ash_status_string": (ctypes.c_char_p, [c_int]),
+    "ash_last_error": (ctypes.c_char_p, []),
+    "ash_set_allocator": (c_int, [ALLOC_FN, FREE_FN, c_void_p]),
+    "ash_debug_fail_after": (c_int, [c_int]),
+    "ash_hologram_create": (c_int, [ctypes.POINTER(c_void_p), c_int, c_int, c_void_p, c_int, c_int_p, c_void_p,
+                                    c_int, c_void_p, c_void_p]),
+    "ash_hologram_destroy": (None, [c_void_p]),
+    "ash_hologram_info": (c_int, [c_void_p, c_int_p, c_int_p, c_int_p, c_int_p, ctypes.POINTER(c_size_t)]),
+    "ash_set_coefficients": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "ash_set_amplitude": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "ash_forward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ash_forward_field": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ash_adjoint": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ash_wgs_iterate": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    "ash_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ash_hologram_check": (c_int, [c_void_p, c_void_p]),
+}
+
+_lib = None
+
+
+class AshError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: {status_name(status)}: {message}")
+        self.status = status
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libash.so not built at {path}; run __graft_entry__.build() "
+                          "(python -m paper_2505_08777_gb300.build)")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)   # AttributeError if the ABI is incomplete
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def status_name(status: int) -> str:
+    lib = load()
+    return lib.ash_status_string(status).decode()
+
+
+def check(status: int, where: str) -> None:
+    if status != 0:
+        lib = load()
+        raise AshError(status, where, lib.ash_last_error().decode())

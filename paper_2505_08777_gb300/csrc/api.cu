@@ -1,0 +1,541 @@
+// C ABI of the library (declared in include/ash.h): argument validation,
+// workspace ownership, launch orchestration, and the CUDA-graph WGS loop.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "ash.h"
+#include "aux_kernels.cuh"
+#include "basis_host.h"
+#include "launch.h"
+
+using namespace ash;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+ash_alloc_fn g_alloc = nullptr;
+ash_free_fn g_free = nullptr;
+void* g_alloc_ctx = nullptr;
+std::mutex g_mu;
+int g_fail_after = 0;   // 0 = off
+
+ash_status set_error(ash_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+ash_status cuda_fail(cudaError_t e, const char* where) {
+  return set_error(ASH_ERR_CUDA, "%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define ASH_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+  } while (0)
+
+// Counts calls that would launch work; returns true if this one is injected to fail.
+bool injected_failure() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (g_fail_after <= 0) return false;
+  if (--g_fail_after == 0) return true;
+  return false;
+}
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+}  // namespace
+
+struct ash_hologram {
+  Geometry g{};
+  int device = 0;
+  cudaStream_t home = nullptr;     // stream the workspace was allocated on
+  LaunchInfo li{};
+  int fwd_grid = 0, fwd_rows = 0, tiles_per_cta = 0;
+  int gradc_gx = 0, gradc_gy = 0;
+  // workspace
+  float* dz = nullptr;
+  float* amp_img = nullptr;
+  float2* anchors = nullptr;
+  float* coeff = nullptr;
+  float* partial = nullptr;
+  float* gradc_partial = nullptr;
+  float2* E = nullptr;
+  float2* y = nullptr;
+  float* wgs_phase = nullptr;
+  float* wgs_w = nullptr;
+  float* wgs_T = nullptr;
+  float2* wgs_E = nullptr;
+  float* wgs_metrics = nullptr;
+  double* sum_a2 = nullptr;
+  MonoTerm* terms = nullptr;
+  int* term_off = nullptr;
+  unsigned* err_word = nullptr;
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  cudaStream_t capture = nullptr;
+  std::map<int, cudaGraphExec_t> graphs;
+};
+
+namespace {
+
+ash_status ws_alloc(ash_hologram* h, void** out, size_t bytes) {
+  bytes = (bytes + 255) & ~(size_t)255;
+  void* p = nullptr;
+  if (g_alloc) {
+    p = g_alloc(g_alloc_ctx, bytes, h->home);
+    if (!p) return set_error(ASH_ERR_OOM, "allocator hook returned NULL for %zu bytes", bytes);
+  } else {
+    cudaError_t e = cudaMallocAsync(&p, bytes, h->home);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(ASH_ERR_OOM, "cudaMallocAsync(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+  }
+  h->allocs.push_back(p);
+  h->bytes += bytes;
+  *out = p;
+  return ASH_OK;
+}
+
+template <typename T>
+ash_status ws(ash_hologram* h, T** out, size_t count) {
+  return ws_alloc(h, reinterpret_cast<void**>(out), count * sizeof(T));
+}
+
+void release(ash_hologram* h) {
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  h->graphs.clear();
+  for (void* p : h->allocs) {
+    if (g_free) g_free(g_alloc_ctx, p, h->home);
+    else cudaFreeAsync(p, h->home);
+  }
+  h->allocs.clear();
+  if (h->capture) cudaStreamDestroy(h->capture);
+  h->capture = nullptr;
+}
+
+cudaError_t prepare(int D, LaunchInfo* li) {
+  switch (range_of(D)) {
+    case 0: return prepare_r0(D, li);
+    case 1: return prepare_r1(D, li);
+    case 2: return prepare_r2(D, li);
+    case 3: return prepare_r3(D, li);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_forward(int D, const FwdParams& p, int grid, cudaStream_t s) {
+  switch (range_of(D)) {
+    case 0: return launch_forward_r0(D, p, grid, s);
+    case 1: return launch_forward_r1(D, p, grid, s);
+    case 2: return launch_forward_r2(D, p, grid, s);
+    case 3: return launch_forward_r3(D, p, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_adjoint(int D, const AdjParams& p, int grid, cudaStream_t s) {
+  switch (range_of(D)) {
+    case 0: return launch_adjoint_r0(D, p, grid, s);
+    case 1: return launch_adjoint_r1(D, p, grid, s);
+    case 2: return launch_adjoint_r2(D, p, grid, s);
+    case 3: return launch_adjoint_r3(D, p, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_gradc(int D, const GradCParams& p, dim3 grid, cudaStream_t s) {
+  switch (range_of(D)) {
+    case 0: return launch_gradc_r0(D, p, grid, s);
+    case 1: return launch_gradc_r1(D, p, grid, s);
+    case 2: return launch_gradc_r2(D, p, grid, s);
+    case 3: return launch_gradc_r3(D, p, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// forward transform into E (device complex [N]).
+ash_status enqueue_forward(ash_hologram* h, int source, const float* phase, const float2* field, float2* E,
+                           cudaStream_t s) {
+  FwdParams p{};
+  p.g = h->g;
+  p.dz = h->dz;
+  p.amp_img = h->amp_img;
+  p.anchors = h->anchors;
+  p.coeff = h->coeff;
+  p.phase = phase;
+  p.field = field;
+  p.source = source;
+  p.partial = h->partial;
+  p.tiles_per_cta = h->tiles_per_cta;
+  cudaError_t e = launch_forward(h->g.D, p, h->fwd_grid, s);
+  if (e != cudaSuccess) return cuda_fail(e, "forward kernel launch");
+  const int cols = 2 * h->g.N;
+  k_col_reduce<<<(cols + 31) / 32, dim3(32, 32), 0, s>>>(h->partial, h->fwd_rows, cols, reinterpret_cast<float*>(E));
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "forward reduce launch");
+  return ASH_OK;
+}
+
+ash_status enqueue_adjoint(ash_hologram* h, const float2* y, float2* g_out, float* phase_out, const float* phase_in,
+                           float* dphase, int epilogue, cudaStream_t s) {
+  AdjParams p{};
+  p.g = h->g;
+  p.dz = h->dz;
+  p.amp_img = h->amp_img;
+  p.anchors = h->anchors;
+  p.coeff = h->coeff;
+  p.y = y;
+  p.g_out = g_out;
+  p.phase_out = phase_out;
+  p.phase_in = phase_in;
+  p.dphase = dphase;
+  p.epilogue = epilogue;
+  cudaError_t e = launch_adjoint(h->g.D, p, h->g.T, s);
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint kernel launch");
+  return ASH_OK;
+}
+
+ash_status enqueue_wgs_body(ash_hologram* h, int iters, cudaStream_t s) {
+  ash_status st;
+  for (int it = 0; it < iters; ++it) {
+    st = enqueue_forward(h, kSrcPhase, h->wgs_phase, nullptr, h->wgs_E, s);
+    if (st != ASH_OK) return st;
+    k_wgs_update<<<1, 1024, 0, s>>>(h->wgs_E, h->wgs_w, h->wgs_T, h->y, h->g.N);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "wgs update launch");
+    st = enqueue_adjoint(h, h->y, nullptr, h->wgs_phase, nullptr, nullptr, kEpiPhase, s);
+    if (st != ASH_OK) return st;
+  }
+  st = enqueue_forward(h, kSrcPhase, h->wgs_phase, nullptr, h->wgs_E, s);
+  if (st != ASH_OK) return st;
+  k_metrics<<<1, 1024, 0, s>>>(h->wgs_E, h->wgs_T, h->g.N, h->sum_a2, (double)h->g.nx * h->g.ny, h->wgs_metrics);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "metrics launch");
+  return ASH_OK;
+}
+
+bool bad_ptr(const void* p) { return p == nullptr; }
+
+}  // namespace
+
+extern "C" {
+
+int ash_abi_version(void) { return ASH_ABI_VERSION; }
+
+const char* ash_status_string(ash_status s) {
+  switch (s) {
+    case ASH_OK: return "ASH_OK";
+    case ASH_ERR_INVALID_ARG: return "ASH_ERR_INVALID_ARG";
+    case ASH_ERR_CUDA: return "ASH_ERR_CUDA";
+    case ASH_ERR_OOM: return "ASH_ERR_OOM";
+    case ASH_ERR_TIMEOUT: return "ASH_ERR_TIMEOUT";
+    case ASH_ERR_UNSUPPORTED: return "ASH_ERR_UNSUPPORTED";
+    case ASH_ERR_INJECTED: return "ASH_ERR_INJECTED";
+    case ASH_ERR_DEVICE: return "ASH_ERR_DEVICE";
+  }
+  return "ASH_ERR_UNKNOWN";
+}
+
+const char* ash_last_error(void) { return g_last_error.c_str(); }
+
+ash_status ash_set_allocator(ash_alloc_fn alloc, ash_free_fn free_fn, void* ctx) {
+  if ((alloc == nullptr) != (free_fn == nullptr))
+    return set_error(ASH_ERR_INVALID_ARG, "allocator hook needs both alloc and free (or neither)");
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_alloc = alloc;
+  g_free = free_fn;
+  g_alloc_ctx = ctx;
+  return ASH_OK;
+}
+
+ash_status ash_debug_fail_after(int n_calls) {
+  if (n_calls < 0) return set_error(ASH_ERR_INVALID_ARG, "n_calls must be >= 0");
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_fail_after = n_calls;
+  return ASH_OK;
+}
+
+ash_status ash_hologram_create(ash_hologram** out, int nx, int ny, const float* amp, int D, const int* noll,
+                               const float* basis, int N, const float* coeff, void* stream) {
+  if (!out) return set_error(ASH_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (nx < 1 || ny < 1 || nx > 16384 || ny > 16384)
+    return set_error(ASH_ERR_INVALID_ARG, "grid %dx%d outside [1, 16384]", nx, ny);
+  if (D < 1 || D > ASH_MAX_MODES) return set_error(ASH_ERR_INVALID_ARG, "D=%d outside [1, %d]", D, ASH_MAX_MODES);
+  if (N < 1 || N > (1 << 20)) return set_error(ASH_ERR_INVALID_ARG, "N=%d outside [1, 2^20]", N);
+  if (bad_ptr(amp) || bad_ptr(coeff)) return set_error(ASH_ERR_INVALID_ARG, "amp and coeff must be device pointers");
+  if ((noll == nullptr) == (basis == nullptr))
+    return set_error(ASH_ERR_INVALID_ARG, "exactly one of noll / basis must be given");
+  std::vector<MonoTerm> terms;
+  std::vector<int> off(1, 0);
+  int max_order = 0;
+  if (noll) {
+    for (int d = 0; d < D; ++d) {
+      int n, m;
+      if (noll[d] < 1 || noll[d] > 231 || !noll_to_nm(noll[d], &n, &m))
+        return set_error(ASH_ERR_INVALID_ARG, "Noll index %d outside [1, 231]", noll[d]);
+      if (!zernike_monomials(n, m, &terms)) return set_error(ASH_ERR_INVALID_ARG, "bad Zernike (%d, %d)", n, m);
+      off.push_back((int)terms.size());
+      max_order = n > max_order ? n : max_order;
+    }
+  }
+  if (injected_failure()) return set_error(ASH_ERR_INJECTED, "injected failure (ash_debug_fail_after)");
+
+  ash_hologram* h = new ash_hologram();
+  cudaStream_t s = as_stream(stream);
+  h->home = s;
+  cudaGetDevice(&h->device);
+  Geometry& g = h->g;
+  g.nx = nx;
+  g.ny = ny;
+  g.tiles_x = (nx + kTileX - 1) / kTileX;
+  g.tiles_y = (ny + kTileY - 1) / kTileY;
+  g.T = g.tiles_x * g.tiles_y;
+  g.D = D;
+  g.N = N;
+  g.P = pixels_per_thread(D);
+  g.NT = kTilePix / g.P;
+
+  auto fail = [&](ash_status st) {
+    release(h);
+    delete h;
+    return st;
+  };
+  cudaError_t ce = prepare(D, &h->li);
+  if (ce != cudaSuccess) return fail(cuda_fail(ce, "kernel preparation"));
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  const int fwd_slots = sms * (h->li.fwd_ctas_per_sm > 0 ? h->li.fwd_ctas_per_sm : 1);
+  h->fwd_grid = g.T < fwd_slots ? g.T : fwd_slots;
+  h->tiles_per_cta = (g.T + h->fwd_grid - 1) / h->fwd_grid;
+  h->fwd_rows = h->fwd_grid * (g.NT / 32);
+  h->gradc_gy = (N + kGradThreads * kGradSpots - 1) / (kGradThreads * kGradSpots);
+  {
+    const int slots = sms * (h->li.gradc_ctas_per_sm > 0 ? h->li.gradc_ctas_per_sm : 1);
+    int gx = slots / h->gradc_gy;
+    if (gx < 1) gx = 1;
+    if (gx > g.T) gx = g.T;
+    h->gradc_gx = gx;
+  }
+  const size_t M = (size_t)nx * ny;
+  const size_t pix = (size_t)g.T * kTilePix;
+  ash_status st;
+  if ((st = ws(h, &h->dz, pix * D)) != ASH_OK) return fail(st);
+  if ((st = ws(h, &h->amp_img, pix)) != ASH_OK) return fail(st);
+  if ((st = ws(h, &h->anchors, (size_t)g.T * D)) != ASH_OK) return fail(st);
+  if ((st = ws(h, &h->coeff, (size_t)N * D)) != ASH_OK) return fail(st);
+  if ((st = ws(h, &h->partial, (size_t)h->fwd_rows * 2 * N)) != ASH_OK) return fail(st);
+  if ((st = ws(h, &h->gradc_partial, (size_t)h->gradc_gx * N * D)) != ASH_OK) return fail(st);
+  if ((st = ws(h, &h->E, (size_t)N)) != ASH_OK) return fail(st);
+  if ((st = ws(h, &h->y, (size_t)N)) != ASH_OK) return fail(st);
+  if ((st = ws(h, &h->wgs_phase, M)) != ASH_OK) return fail(st);
+  if ((st = ws(h, &h->wgs_w, (size_t)N)) != ASH_OK) return fail(st);
+  if ((st = ws(h, &h->wgs_T, (size_t)N)) != ASH_OK) return fail(st);
+  if ((st = ws(h, &h->wgs_E, (size_t)N)) != ASH_OK) return fail(st);
+  if ((st = ws(h, &h->wgs_metrics, 4)) != ASH_OK) return fail(st);
+  if ((st = ws(h, &h->sum_a2, 1)) != ASH_OK) return fail(st);
+  if ((st = ws(h, &h->err_word, 1)) != ASH_OK) return fail(st);
+  if (noll) {
+    if ((st = ws(h, &h->terms, terms.size())) != ASH_OK) return fail(st);
+    if ((st = ws(h, &h->term_off, off.size())) != ASH_OK) return fail(st);
+  }
+  ce = cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking);
+  if (ce != cudaSuccess) return fail(cuda_fail(ce, "capture stream"));
+
+#define CREATE_CUDA(call)                                     \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return fail(cuda_fail(e_, #call)); \
+  } while (0)
+  if (noll) {
+    CREATE_CUDA(cudaMemcpyAsync(h->terms, terms.data(), terms.size() * sizeof(MonoTerm), cudaMemcpyHostToDevice, s));
+    CREATE_CUDA(cudaMemcpyAsync(h->term_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  }
+  CREATE_CUDA(cudaMemsetAsync(h->err_word, 0, sizeof(unsigned), s));
+  CREATE_CUDA(cudaMemcpyAsync(h->coeff, coeff, (size_t)N * D * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  BasisParams bp{};
+  bp.g = g;
+  bp.terms = h->terms;
+  bp.term_off = h->term_off;
+  bp.max_order = max_order;
+  bp.user_basis = basis;
+  bp.dz = h->dz;
+  bp.anchors = h->anchors;
+  k_basis<<<g.T, g.NT, 0, s>>>(bp);
+  CREATE_CUDA(cudaGetLastError());
+  k_amp_image<<<g.T, g.NT, 0, s>>>(g, amp, h->amp_img);
+  CREATE_CUDA(cudaGetLastError());
+  k_sum_sq<<<1, 1024, 0, s>>>(amp, M, h->sum_a2);
+  CREATE_CUDA(cudaGetLastError());
+  // stream-ordered allocations and set-up must be complete before the handle
+  // is used from another stream (the graph capture stream, or the caller's)
+  CREATE_CUDA(cudaStreamSynchronize(s));
+#undef CREATE_CUDA
+  *out = h;
+  return ASH_OK;
+}
+
+void ash_hologram_destroy(ash_hologram* h) {
+  if (!h) return;
+  // work enqueued on any stream may still read the workspace
+  cudaDeviceSynchronize();
+  release(h);
+  delete h;
+}
+
+ash_status ash_hologram_info(const ash_hologram* h, int* nx, int* ny, int* N, int* D, size_t* workspace_bytes) {
+  if (!h) return set_error(ASH_ERR_INVALID_ARG, "handle is NULL");
+  if (nx) *nx = h->g.nx;
+  if (ny) *ny = h->g.ny;
+  if (N) *N = h->g.N;
+  if (D) *D = h->g.D;
+  if (workspace_bytes) *workspace_bytes = h->bytes;
+  return ASH_OK;
+}
+
+ash_status ash_set_coefficients(ash_hologram* h, const float* coeff, void* stream) {
+  if (!h || !coeff) return set_error(ASH_ERR_INVALID_ARG, "NULL argument");
+  if (injected_failure()) return set_error(ASH_ERR_INJECTED, "injected failure");
+  ASH_CUDA(cudaMemcpyAsync(h->coeff, coeff, (size_t)h->g.N * h->g.D * sizeof(float), cudaMemcpyDeviceToDevice,
+                           as_stream(stream)));
+  return ASH_OK;
+}
+
+ash_status ash_set_amplitude(ash_hologram* h, const float* amp, void* stream) {
+  if (!h || !amp) return set_error(ASH_ERR_INVALID_ARG, "NULL argument");
+  if (injected_failure()) return set_error(ASH_ERR_INJECTED, "injected failure");
+  cudaStream_t s = as_stream(stream);
+  k_amp_image<<<h->g.T, h->g.NT, 0, s>>>(h->g, amp, h->amp_img);
+  ASH_CUDA(cudaGetLastError());
+  k_sum_sq<<<1, 1024, 0, s>>>(amp, (size_t)h->g.nx * h->g.ny, h->sum_a2);
+  ASH_CUDA(cudaGetLastError());
+  return ASH_OK;
+}
+
+ash_status ash_forward(ash_hologram* h, const float* phase, float* E, void* stream) {
+  if (!h || !phase || !E) return set_error(ASH_ERR_INVALID_ARG, "NULL argument");
+  if (injected_failure()) return set_error(ASH_ERR_INJECTED, "injected failure");
+  return enqueue_forward(h, kSrcPhase, phase, nullptr, reinterpret_cast<float2*>(E), as_stream(stream));
+}
+
+ash_status ash_forward_field(ash_hologram* h, const float* field, float* E, void* stream) {
+  if (!h || !field || !E) return set_error(ASH_ERR_INVALID_ARG, "NULL argument");
+  if ((reinterpret_cast<uintptr_t>(field) & 7) || (reinterpret_cast<uintptr_t>(E) & 7))
+    return set_error(ASH_ERR_INVALID_ARG, "complex buffers must be 8-byte aligned");
+  if (injected_failure()) return set_error(ASH_ERR_INJECTED, "injected failure");
+  return enqueue_forward(h, kSrcField, nullptr, reinterpret_cast<const float2*>(field), reinterpret_cast<float2*>(E),
+                         as_stream(stream));
+}
+
+ash_status ash_adjoint(ash_hologram* h, const float* y, float* g, float* phase_out, void* stream) {
+  if (!h || !y) return set_error(ASH_ERR_INVALID_ARG, "NULL argument");
+  if (!g && !phase_out) return set_error(ASH_ERR_INVALID_ARG, "need g or phase_out");
+  if ((reinterpret_cast<uintptr_t>(y) & 7) || (reinterpret_cast<uintptr_t>(g) & 7))
+    return set_error(ASH_ERR_INVALID_ARG, "complex buffers must be 8-byte aligned");
+  if (injected_failure()) return set_error(ASH_ERR_INJECTED, "injected failure");
+  int epi = (g ? kEpiField : 0) | (phase_out ? kEpiPhase : 0);
+  return enqueue_adjoint(h, reinterpret_cast<const float2*>(y), reinterpret_cast<float2*>(g), phase_out, nullptr,
+                         nullptr, epi, as_stream(stream));
+}
+
+ash_status ash_wgs_iterate(ash_hologram* h, float* phase, float* w, const float* target, int iters, float* E_out,
+                           float* metrics_out, void* stream) {
+  if (!h || !phase || !w || !target) return set_error(ASH_ERR_INVALID_ARG, "NULL argument");
+  if (iters < 0 || iters > 1000000) return set_error(ASH_ERR_INVALID_ARG, "iters=%d outside [0, 1e6]", iters);
+  if (injected_failure()) return set_error(ASH_ERR_INJECTED, "injected failure");
+  cudaStream_t s = as_stream(stream);
+  const size_t M = (size_t)h->g.nx * h->g.ny;
+  const size_t N = (size_t)h->g.N;
+  ASH_CUDA(cudaMemcpyAsync(h->wgs_phase, phase, M * 4, cudaMemcpyDeviceToDevice, s));
+  ASH_CUDA(cudaMemcpyAsync(h->wgs_w, w, N * 4, cudaMemcpyDeviceToDevice, s));
+  ASH_CUDA(cudaMemcpyAsync(h->wgs_T, target, N * 4, cudaMemcpyDeviceToDevice, s));
+  if (iters >= 2) {
+    auto it = h->graphs.find(iters);
+    cudaGraphExec_t exec = nullptr;
+    if (it != h->graphs.end()) {
+      exec = it->second;
+    } else {
+      cudaGraph_t graph = nullptr;
+      ASH_CUDA(cudaStreamBeginCapture(h->capture, cudaStreamCaptureModeThreadLocal));
+      ash_status st = enqueue_wgs_body(h, iters, h->capture);
+      cudaError_t ce = cudaStreamEndCapture(h->capture, &graph);
+      if (st != ASH_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+      }
+      if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+      ce = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
+      h->graphs[iters] = exec;
+    }
+    ASH_CUDA(cudaGraphLaunch(exec, s));
+  } else {
+    ash_status st = enqueue_wgs_body(h, iters, s);
+    if (st != ASH_OK) return st;
+  }
+  ASH_CUDA(cudaMemcpyAsync(phase, h->wgs_phase, M * 4, cudaMemcpyDeviceToDevice, s));
+  ASH_CUDA(cudaMemcpyAsync(w, h->wgs_w, N * 4, cudaMemcpyDeviceToDevice, s));
+  if (E_out) ASH_CUDA(cudaMemcpyAsync(E_out, h->wgs_E, N * 8, cudaMemcpyDeviceToDevice, s));
+  if (metrics_out) ASH_CUDA(cudaMemcpyAsync(metrics_out, h->wgs_metrics, 16, cudaMemcpyDeviceToDevice, s));
+  return ASH_OK;
+}
+
+ash_status ash_grad(ash_hologram* h, const float* phase, const float* grad_E, float* dphase, float* dcoeff,
+                    void* stream) {
+  if (!h || !phase || !grad_E) return set_error(ASH_ERR_INVALID_ARG, "NULL argument");
+  if (!dphase && !dcoeff) return set_error(ASH_ERR_INVALID_ARG, "need dphase or dcoeff");
+  if (reinterpret_cast<uintptr_t>(grad_E) & 7) return set_error(ASH_ERR_INVALID_ARG, "grad_E must be 8-byte aligned");
+  if (injected_failure()) return set_error(ASH_ERR_INJECTED, "injected failure");
+  cudaStream_t s = as_stream(stream);
+  const float2* gE = reinterpret_cast<const float2*>(grad_E);
+  if (dphase) {
+    ash_status st = enqueue_adjoint(h, gE, nullptr, nullptr, phase, dphase, kEpiGradPhase, s);
+    if (st != ASH_OK) return st;
+  }
+  if (dcoeff) {
+    GradCParams p{};
+    p.g = h->g;
+    p.dz = h->dz;
+    p.amp_img = h->amp_img;
+    p.anchors = h->anchors;
+    p.coeff = h->coeff;
+    p.phase = phase;
+    p.gradE = gE;
+    p.partial = h->gradc_partial;
+    cudaError_t e = launch_gradc(h->g.D, p, dim3(h->gradc_gx, h->gradc_gy), s);
+    if (e != cudaSuccess) return cuda_fail(e, "gradc kernel launch");
+    const int cols = h->g.N * h->g.D;
+    k_col_reduce<<<(cols + 31) / 32, dim3(32, 32), 0, s>>>(h->gradc_partial, h->gradc_gx, cols, dcoeff);
+    ASH_CUDA(cudaGetLastError());
+  }
+  return ASH_OK;
+}
+
+ash_status ash_hologram_check(ash_hologram* h, void* stream) {
+  if (!h) return set_error(ASH_ERR_INVALID_ARG, "handle is NULL");
+  cudaStream_t s = as_stream(stream);
+  unsigned word = 0;
+  ASH_CUDA(cudaMemcpyAsync(&word, h->err_word, sizeof word, cudaMemcpyDeviceToHost, s));
+  ASH_CUDA(cudaStreamSynchronize(s));
+  if (word) {
+    ASH_CUDA(cudaMemsetAsync(h->err_word, 0, sizeof word, s));
+    return set_error(ASH_ERR_DEVICE, "device error word 0x%x", word);
+  }
+  return ASH_OK;
+}
+
+}  // extern "C"

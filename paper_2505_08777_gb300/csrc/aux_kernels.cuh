@@ -1,0 +1,231 @@
+// Set-up and N-length kernels: basis materialisation, layout conversion,
+// deterministic column reductions, the weighted-GS spot update and metrics.
+#pragma once
+
+#include "common.cuh"
+#include "mono.h"
+
+namespace ash {
+
+struct BasisParams {
+  Geometry g;
+  const MonoTerm* terms;   // all modes' terms, concatenated
+  const int* term_off;     // [D + 1] offsets into terms
+  int max_order;           // max px or py over all terms
+  const float* user_basis; // [D][ny][nx] or null (then terms are used)
+  float* dz;               // register image [T][NT][D][P]
+  float2* anchors;         // [T][D]
+};
+
+// Anchor pixel of a tile: centre of its in-grid part.
+__host__ __device__ inline void tile_anchor(const Geometry& g, int tile, int& ia, int& ja) {
+  const int tx = tile % g.tiles_x, ty = tile / g.tiles_x;
+  const int x0 = tx * kTileX, y0 = ty * kTileY;
+  const int x1 = min(x0 + kTileX, g.nx), y1 = min(y0 + kTileY, g.ny);
+  ia = (x0 + x1 - 1) / 2;
+  ja = (y0 + y1 - 1) / 2;
+}
+
+__device__ inline double eval_mono(const MonoTerm* __restrict__ terms, int b, int e, const double* xp,
+                                   const double* yp) {
+  double z = 0.0;
+  for (int q = b; q < e; ++q) z = fma(terms[q].coef, xp[terms[q].px] * yp[terms[q].py], z);
+  return z;
+}
+
+constexpr int kMaxOrder = 24;
+
+// One CTA per tile, NT threads; thread t fills its P pixels x D modes.
+__global__ void k_basis(const BasisParams p) {
+  const Geometry& G = p.g;
+  const int tile = blockIdx.x, t = threadIdx.x;
+  const int P = G.P, NT = G.NT, D = G.D;
+  const int tx = tile % G.tiles_x, ty = tile / G.tiles_x;
+  const int lane = t & 31, w = t >> 5;
+  int ia, ja;
+  tile_anchor(G, tile, ia, ja);
+  const double R = 0.5 * (double)min(G.nx, G.ny);
+  const double cx = 0.5 * (double)(G.nx - 1), cy = 0.5 * (double)(G.ny - 1);
+  double axp[kMaxOrder + 1], ayp[kMaxOrder + 1];
+  double xp[kMaxOrder + 1], yp[kMaxOrder + 1];
+  if (!p.user_basis) {
+    const double xa = ((double)ia - cx) / R, ya = ((double)ja - cy) / R;
+    axp[0] = ayp[0] = 1.0;
+    for (int o = 1; o <= p.max_order; ++o) {
+      axp[o] = axp[o - 1] * xa;
+      ayp[o] = ayp[o - 1] * ya;
+    }
+  }
+  const size_t ma = (size_t)ja * G.nx + ia;
+  for (int k = 0; k < P; ++k) {
+    const int i = tx * kTileX + lane;
+    const int j = ty * kTileY + w + (NT / 32) * k;
+    const bool valid = (i < G.nx) && (j < G.ny);
+    if (!p.user_basis && valid) {
+      const double x = ((double)i - cx) / R, y = ((double)j - cy) / R;
+      xp[0] = yp[0] = 1.0;
+      for (int o = 1; o <= p.max_order; ++o) {
+        xp[o] = xp[o - 1] * x;
+        yp[o] = yp[o - 1] * y;
+      }
+    }
+    for (int d = 0; d < D; ++d) {
+      double v = 0.0;
+      if (valid) {
+        if (p.user_basis) {
+          const size_t plane = (size_t)d * G.nx * G.ny;
+          v = (double)p.user_basis[plane + (size_t)j * G.nx + i] - (double)p.user_basis[plane + ma];
+        } else {
+          const int b = p.term_off[d], e = p.term_off[d + 1];
+          v = eval_mono(p.terms, b, e, xp, yp) - eval_mono(p.terms, b, e, axp, ayp);
+        }
+      }
+      p.dz[(((size_t)tile * NT + t) * D + d) * P + k] = (float)v;
+    }
+  }
+  if (t < D) {
+    const int d = t;
+    double za;
+    if (p.user_basis) {
+      za = (double)p.user_basis[(size_t)d * G.nx * G.ny + ma];
+    } else {
+      za = eval_mono(p.terms, p.term_off[d], p.term_off[d + 1], axp, ayp);
+    }
+    const double turns = za / 6.283185307179586476925286766559;
+    const float hi = (float)turns;
+    const float lo = (float)(turns - (double)hi);
+    p.anchors[(size_t)tile * D + d] = make_float2(hi, lo);
+  }
+}
+
+// Amplitude into the register-image layout (zero outside the grid).
+__global__ void k_amp_image(Geometry G, const float* __restrict__ amp, float* __restrict__ img) {
+  const int tile = blockIdx.x, t = threadIdx.x;
+  const int tx = tile % G.tiles_x, ty = tile / G.tiles_x;
+  const int lane = t & 31, w = t >> 5;
+  for (int k = 0; k < G.P; ++k) {
+    const int i = tx * kTileX + lane;
+    const int j = ty * kTileY + w + (G.NT / 32) * k;
+    const bool valid = (i < G.nx) && (j < G.ny);
+    img[((size_t)tile * G.NT + t) * G.P + k] = valid ? amp[(size_t)j * G.nx + i] : 0.0f;
+  }
+}
+
+// Block-wide sum in a fixed order (deterministic). All threads get the result.
+template <int NTH>
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int q = 0; q < NTH / 32; ++q) s += red[q];
+  return s;
+}
+
+// sum_m A_m^2 in fp64 (one block).
+__global__ void k_sum_sq(const float* __restrict__ a, size_t M, double* out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (size_t m = threadIdx.x; m < M; m += blockDim.x) s += (double)a[m] * (double)a[m];
+  s = block_sum<1024>(s, red);
+  if (threadIdx.x == 0) *out = s;
+}
+
+// out[c] = sum_r in[r][c] (r in fixed order). Block (32, 32): 32 columns,
+// 32 row lanes; smem tree over the row lanes.
+__global__ void k_col_reduce(const float* __restrict__ in, int rows, int cols, float* __restrict__ out) {
+  __shared__ float red[32][33];
+  const int c = blockIdx.x * 32 + threadIdx.x;
+  float s = 0.0f;
+  if (c < cols) {
+    for (int r = threadIdx.y; r < rows; r += 32) s += in[(size_t)r * cols + c];
+  }
+  red[threadIdx.y][threadIdx.x] = s;
+  __syncthreads();
+  for (int h = 16; h >= 1; h >>= 1) {
+    if (threadIdx.y < h) red[threadIdx.y][threadIdx.x] += red[threadIdx.y + h][threadIdx.x];
+    __syncthreads();
+  }
+  if (threadIdx.y == 0 && c < cols) out[c] = red[0][threadIdx.x];
+}
+
+// Weighted GS spot update (one block of 1024 threads):
+//   E^ = |E|/||E||, T^ = T/||T||, w <- w T^/max(E^, 1e-30), w <- w/||w||,
+//   y = w exp(i arg E) (arg 0 -> 0).
+__global__ void __launch_bounds__(1024) k_wgs_update(const float2* __restrict__ E, float* __restrict__ w,
+                                                     const float* __restrict__ T, float2* __restrict__ y, int N) {
+  __shared__ double red[32];
+  double se = 0.0, st = 0.0;
+  for (int n = threadIdx.x; n < N; n += 1024) {
+    const float2 e = E[n];
+    se += (double)e.x * e.x + (double)e.y * e.y;
+    st += (double)T[n] * T[n];
+  }
+  se = block_sum<1024>(se, red);
+  st = block_sum<1024>(st, red);
+  const float inv_e = se > 0.0 ? (float)(1.0 / sqrt(se)) : 0.0f;
+  const float inv_t = (float)(1.0 / sqrt(st));
+  double sw = 0.0;
+  for (int n = threadIdx.x; n < N; n += 1024) {
+    const float2 e = E[n];
+    const float ea = sqrtf(e.x * e.x + e.y * e.y);
+    const float eh = fmaxf(ea * inv_e, 1e-30f);
+    const float wn = w[n] * (T[n] * inv_t) / eh;
+    w[n] = wn;
+    sw += (double)wn * wn;
+  }
+  sw = block_sum<1024>(sw, red);
+  const float inv_w = (float)(1.0 / sqrt(sw));
+  for (int n = threadIdx.x; n < N; n += 1024) {
+    const float wn = w[n] * inv_w;
+    w[n] = wn;
+    const float2 e = E[n];
+    const float ea = sqrtf(e.x * e.x + e.y * e.y);
+    y[n] = ea > 0.0f ? make_float2(wn * (e.x / ea), wn * (e.y / ea)) : make_float2(wn, 0.0f);
+  }
+}
+
+// metrics = {uniformity, efficiency, sum |E|^2, min I^} (one block).
+__global__ void __launch_bounds__(1024) k_metrics(const float2* __restrict__ E, const float* __restrict__ T, int N,
+                                                  const double* __restrict__ sum_a2, double M,
+                                                  float* __restrict__ metrics) {
+  __shared__ double red[32];
+  __shared__ float rmin[32], rmax[32];
+  double se = 0.0;
+  float lo = 3.0e38f, hi = 0.0f;
+  for (int n = threadIdx.x; n < N; n += 1024) {
+    const float2 e = E[n];
+    const float I = e.x * e.x + e.y * e.y;
+    se += (double)I;
+    const float ih = I / (T[n] * T[n]);
+    lo = fminf(lo, ih);
+    hi = fmaxf(hi, ih);
+  }
+  se = block_sum<1024>(se, red);
+  for (int o = 16; o >= 1; o >>= 1) {
+    lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+  if (lane == 0) {
+    rmin[wq] = lo;
+    rmax[wq] = hi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 1; q < 32; ++q) {
+      lo = fminf(lo, rmin[q]);
+      hi = fmaxf(hi, rmax[q]);
+    }
+    lo = fminf(lo, rmin[0]);
+    hi = fmaxf(hi, rmax[0]);
+    metrics[0] = (hi + lo) > 0.0f ? 1.0f - (hi - lo) / (hi + lo) : 0.0f;
+    metrics[1] = (float)(se / (M * (*sum_a2)));
+    metrics[2] = (float)se;
+    metrics[3] = lo;
+  }
+}
+
+}  // namespace ash

@@ -1,0 +1,159 @@
+// Shared device helpers, geometry and kernel parameter blocks.
+//
+// Data layout (HBM):
+//   The SLM grid is cut into 32 x 32 pixel tiles. Each tile is processed by
+//   one CTA of NT = 1024 / P threads; thread t owns P pixels of the tile:
+//   column (t % 32), rows (t / 32) + (NT / 32) * k for k = 0..P-1.
+//   The basis is stored relative to one anchor pixel per tile
+//   (dZ_dm = Z_d(m) - Z_d(anchor)) in a "register image" layout
+//   [tile][t][d][k] (fp32), so that each thread loads its D x P values as
+//   contiguous 16-byte vectors and the whole tile is one contiguous block.
+//   The anchor values are kept per (tile, mode) as Z_d(anchor)/(2 pi) split
+//   into an fp32 hi/lo pair.
+//
+// Phase split (paper Sec. II kernel K_n(m) = exp(-i sum_d C_nd Z_d(m))):
+//   C_n . Z_m = 2 pi * base(n, tile) + C_n . dZ_m
+//   base(n, tile) = sum_d C_nd Z_d(anchor)/(2 pi), reduced exactly modulo 1
+//   with error-free fp32 products; the local phase C_n . dZ_m stays within
+//   a few tens of radians, where sin.approx/cos.approx keep ~1e-5 rad.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ash {
+
+constexpr int kTileX = 32;
+constexpr int kTileY = 32;
+constexpr int kTilePix = kTileX * kTileY;
+constexpr int kMaxModes = 16;
+
+struct Geometry {
+  int nx, ny;          // grid
+  int tiles_x, tiles_y;
+  int T;               // number of tiles
+  int D;               // modes
+  int N;               // spots
+  int P;               // pixels per thread
+  int NT;              // threads per tile CTA (1024 / P)
+};
+
+// Pixels per thread for a given mode count (register budget of the
+// pixel-stationary kernels: P * D basis values live in registers).
+__host__ __device__ constexpr int pixels_per_thread(int D) { return D <= 12 ? 8 : 4; }
+
+// ---------------------------------------------------------------------------
+// Packed fp32x2 arithmetic (Blackwell FFMA2): one instruction, two lanes of
+// work; used for pixel pairs so the phase contraction and complex MAC take
+// half the issue slots.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\t"
+      "mov.b64 rb, {%4, %5};\n\t"
+      "mov.b64 rc, {%6, %7};\n\t"
+      "fma.rn.f32x2 rd, ra, rb, rc;\n\t"
+      "mov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\t"
+      "mov.b64 rb, {%4, %5};\n\t"
+      "mul.rn.f32x2 rd, ra, rb;\n\t"
+      "mov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+
+// Round to nearest integer on the FP32 pipe (|x| < 2^22): adding and
+// subtracting 1.5 * 2^23 leaves the integer part; __fadd_rn keeps the
+// compiler from folding the pair.
+__device__ __forceinline__ float rint_fma_pipe(float x) {
+  return __fsub_rn(__fadd_rn(x, 12582912.0f), 12582912.0f);
+}
+
+// base(n, tile) in turns, reduced to [-1/2, 1/2]:
+//   sum_d c[d] * (hi[d] + lo[d]), with hi + lo = Z_d(anchor) / (2 pi).
+// c[d]*hi[d] = p + e exactly (fma error term); p - rint(p) is exact; the
+// running sum is re-reduced after every mode so it never exceeds ~1 turn.
+template <int D>
+__device__ __forceinline__ float base_turns(const float* c, const float2* anc) {
+  float acc = 0.0f;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const float p = __fmul_rn(c[d], anc[d].x);
+    const float e = __fmaf_rn(c[d], anc[d].x, -p);
+    const float r = __fsub_rn(p, rint_fma_pipe(p));
+    const float t = __fmaf_rn(c[d], anc[d].y, e);
+    acc = __fadd_rn(acc, __fadd_rn(r, t));
+    acc = __fsub_rn(acc, rint_fma_pipe(acc));
+  }
+  return acc;
+}
+
+// exp(i * 2 pi * turns) for |turns| <= 1/2, accurate (sincospif).
+__device__ __forceinline__ float2 cis_turns(float turns) {
+  float s, c;
+  sincospif(2.0f * turns, &s, &c);
+  return make_float2(c, s);
+}
+
+// ---------------------------------------------------------------------------
+// Kernel parameter blocks.
+
+enum FwdSource : int { kSrcPhase = 0, kSrcField = 1 };
+enum AdjEpilogue : int { kEpiField = 1, kEpiPhase = 2, kEpiGradPhase = 4 };
+
+struct FwdParams {
+  Geometry g;
+  const float* dz;        // register-image basis [T][NT][D][P]
+  const float* amp_img;   // register-image amplitude [T][NT][P]
+  const float2* anchors;  // [T][D] (hi, lo) of Z(anchor)/(2 pi)
+  const float* coeff;     // [N][D]
+  const float* phase;     // user layout [ny][nx] (kSrcPhase)
+  const float2* field;    // user layout [ny][nx] complex (kSrcField)
+  int source;
+  float* partial;         // [rows][2N], rows = gridDim.x * (NT/32)
+  int tiles_per_cta;      // static schedule: CTA b handles tiles b, b+G, ...
+};
+
+struct AdjParams {
+  Geometry g;
+  const float* dz;
+  const float* amp_img;
+  const float2* anchors;
+  const float* coeff;
+  const float2* y;        // [N] complex
+  float2* g_out;          // user layout complex or null
+  float* phase_out;       // user layout or null
+  const float* phase_in;  // for kEpiGradPhase: current phase (user layout)
+  float* dphase;          // for kEpiGradPhase
+  int epilogue;
+};
+
+struct GradCParams {
+  Geometry g;
+  const float* dz;
+  const float* amp_img;
+  const float2* anchors;
+  const float* coeff;
+  const float* phase;     // user layout
+  const float2* gradE;    // [N]
+  float* partial;         // [gridDim.x][N][D]
+  int tiles_per_cta;
+};
+
+// Coefficient-gradient kernel shape: threads per CTA, spots per thread.
+constexpr int kGradThreads = 128;
+constexpr int kGradSpots = 4;
+
+// Device-side error word bits.
+constexpr unsigned kErrBadArg = 1u;
+
+}  // namespace ash

@@ -1,0 +1,434 @@
+// Fused spot-kernel transforms: forward E = K f, adjoint g = K^H y, and the
+// coefficient-gradient moments. Never forms K: each term's phase
+// C_n . dZ_m, its sincos and the complex multiply-accumulate happen in
+// registers.
+//
+// Forward / adjoint are pixel-stationary: a CTA owns one 32x32 tile, each
+// thread keeps the basis values of its P pixels in registers, and the CTA
+// streams the spots through shared memory in chunks. Per term:
+//   D packed FMAs (two pixels per instruction) for the local phase,
+//   2 MUFU ops (sin.approx, cos.approx),
+//   2 packed FMAs for the complex multiply-accumulate.
+// The forward reduces each spot's per-thread partial sums across the warp
+// with a transpose reduction (32 values -> one per lane in 5 shuffle stages)
+// and rotates the warp sum by exp(-i 2 pi base(n, tile)).
+#pragma once
+
+#include "common.cuh"
+
+namespace ash {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kSpotChunk = 256;   // spots staged per shared-memory chunk
+constexpr int kBatch = 16;        // spots per warp transpose reduction
+
+__host__ __device__ constexpr int cpair_stride(int D) { return ((2 * D) + 3) & ~3; }
+
+// Shared memory bytes of the pixel-stationary kernels.
+__host__ __device__ constexpr size_t fwd_smem_bytes(int D) {
+  return (size_t)kSpotChunk * cpair_stride(D) * 4 + (size_t)kSpotChunk * 8;
+}
+__host__ __device__ constexpr size_t adj_smem_bytes(int D) {
+  return (size_t)kSpotChunk * cpair_stride(D) * 4 + (size_t)kSpotChunk * 32;
+}
+
+// Lane l returns the sum over the warp of a[l].
+__device__ __forceinline__ float warp_transpose_reduce32(float (&a)[32], int lane) {
+#pragma unroll
+  for (int half = 16; half >= 1; half >>= 1) {
+    const bool up = (lane & half) != 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const float send = up ? a[i] : a[i + half];
+      const float keep = up ? a[i + half] : a[i];
+      a[i] = keep + __shfl_xor_sync(kFull, send, half);
+    }
+  }
+  return a[0];
+}
+
+template <int D, int P>
+__device__ __forceinline__ void load_dz(const float* __restrict__ dz_img, int tile, int t,
+                                        float2 (&dz)[P / 2][D]) {
+  constexpr int NT = kTilePix / P;
+  const float4* src = reinterpret_cast<const float4*>(dz_img + ((size_t)tile * NT + t) * D * P);
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+#pragma unroll
+    for (int q = 0; q < P / 4; ++q) {
+      const float4 v = __ldg(src + d * (P / 4) + q);
+      dz[2 * q][d] = make_float2(v.x, v.y);
+      dz[2 * q + 1][d] = make_float2(v.z, v.w);
+    }
+  }
+}
+
+// Stage one spot: duplicated coefficient pairs into sC row, returns base turns.
+template <int D>
+__device__ __forceinline__ float stage_spot(const float* __restrict__ coeff, const float2* __restrict__ anc,
+                                            int n, float* __restrict__ sCrow) {
+  float c[D];
+  float2 a[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    c[d] = __ldg(coeff + (size_t)n * D + d);
+    a[d] = __ldg(anc + d);
+  }
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    sCrow[2 * d] = c[d];
+    sCrow[2 * d + 1] = c[d];
+  }
+  return base_turns<D>(c, a);
+}
+
+template <int D>
+__device__ __forceinline__ void load_cpairs(const float* __restrict__ sCrow, float2 (&cc)[D]) {
+  const float4* q4 = reinterpret_cast<const float4*>(sCrow);
+#pragma unroll
+  for (int q = 0; q < D / 2; ++q) {
+    const float4 v = q4[q];
+    cc[2 * q] = make_float2(v.x, v.y);
+    cc[2 * q + 1] = make_float2(v.z, v.w);
+  }
+  if (D & 1) {
+    const float2 v = reinterpret_cast<const float2*>(sCrow)[D - 1];
+    cc[D - 1] = v;
+  }
+}
+
+// Local phase of two pixels (one packed lane each) for one spot.
+template <int D>
+__device__ __forceinline__ float2 local_phase(const float2 (&cc)[D], const float2 (&z)[D]) {
+  float2 x = mul2(cc[0], z[0]);
+#pragma unroll
+  for (int d = 1; d < D; ++d) x = fma2(cc[d], z[d], x);
+  return x;
+}
+
+__device__ __forceinline__ void sincos2(float2 x, float2& s, float2& c) {
+  s.x = __sinf(x.x);
+  c.x = __cosf(x.x);
+  s.y = __sinf(x.y);
+  c.y = __cosf(x.y);
+}
+
+// ---------------------------------------------------------------------------
+// Forward: partial[row][2n..2n+1] = sum over this warp's pixels of this
+// CTA's tiles of f_m exp(-i C_n . Z_m). Static persistent schedule.
+template <int D, int P>
+__global__ void __launch_bounds__(kTilePix / P) k_forward(const FwdParams p) {
+  constexpr int NT = kTilePix / P;
+  constexpr int NW = NT / 32;
+  constexpr int RS = NT / 32;
+  constexpr int CPS = cpair_stride(D);
+  extern __shared__ float4 smem4[];
+  float* sC = reinterpret_cast<float*>(smem4);
+  float2* sRot = reinterpret_cast<float2*>(sC + kSpotChunk * CPS);
+
+  const Geometry& G = p.g;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int N = G.N;
+  float* prow = p.partial + (size_t)(blockIdx.x * NW + w) * 2 * N;
+
+  for (int it = 0; it < p.tiles_per_cta; ++it) {
+    const int tile = blockIdx.x + it * gridDim.x;
+    if (tile >= G.T) break;
+    const bool first = (it == 0);
+
+    float2 dz[P / 2][D];
+    load_dz<D, P>(p.dz, tile, t, dz);
+
+    const int tx = tile % G.tiles_x, ty = tile / G.tiles_x;
+    const int i = tx * kTileX + lane;
+    float fr[P], fi[P];
+    {
+      const float4* asrc = reinterpret_cast<const float4*>(p.amp_img + ((size_t)tile * NT + t) * P);
+      float a[P];
+#pragma unroll
+      for (int q = 0; q < P / 4; ++q) {
+        const float4 v = __ldg(asrc + q);
+        a[4 * q] = v.x; a[4 * q + 1] = v.y; a[4 * q + 2] = v.z; a[4 * q + 3] = v.w;
+      }
+#pragma unroll
+      for (int k = 0; k < P; ++k) {
+        const int j = ty * kTileY + w + RS * k;
+        const bool valid = (i < G.nx) && (j < G.ny);
+        const size_t m = (size_t)j * G.nx + i;
+        if (p.source == kSrcPhase) {
+          const float ph = valid ? __ldg(p.phase + m) : 0.0f;
+          float s, c;
+          sincosf(ph, &s, &c);
+          fr[k] = a[k] * c;
+          fi[k] = a[k] * s;
+        } else {
+          const float2 f = valid ? __ldg(p.field + m) : make_float2(0.0f, 0.0f);
+          fr[k] = f.x;
+          fi[k] = f.y;
+        }
+      }
+    }
+    float2 fr2[P / 2], fi2[P / 2], nfr2[P / 2];
+#pragma unroll
+    for (int q = 0; q < P / 2; ++q) {
+      fr2[q] = make_float2(fr[2 * q], fr[2 * q + 1]);
+      fi2[q] = make_float2(fi[2 * q], fi[2 * q + 1]);
+      nfr2[q] = make_float2(-fr[2 * q], -fr[2 * q + 1]);
+    }
+
+    const float2* anc = p.anchors + (size_t)tile * D;
+    for (int n0 = 0; n0 < N; n0 += kSpotChunk) {
+      const int nc = min(kSpotChunk, N - n0);
+      __syncthreads();
+      for (int s = t; s < nc; s += NT) {
+        const float bt = stage_spot<D>(p.coeff, anc, n0 + s, sC + s * CPS);
+        sRot[s] = cis_turns(-bt);
+      }
+      __syncthreads();
+
+      for (int b0 = 0; b0 < nc; b0 += kBatch) {
+        float acc[32];
+#pragma unroll
+        for (int s = 0; s < kBatch; ++s) {
+          float re = 0.0f, im = 0.0f;
+          if (b0 + s < nc) {
+            float2 cc[D];
+            load_cpairs<D>(sC + (b0 + s) * CPS, cc);
+            float2 re2 = make_float2(0.0f, 0.0f), im2 = make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int q = 0; q < P / 2; ++q) {
+              const float2 x = local_phase<D>(cc, dz[q]);
+              float2 sn, cs;
+              sincos2(x, sn, cs);
+              re2 = fma2(fr2[q], cs, re2);
+              re2 = fma2(fi2[q], sn, re2);
+              im2 = fma2(fi2[q], cs, im2);
+              im2 = fma2(nfr2[q], sn, im2);
+            }
+            re = re2.x + re2.y;
+            im = im2.x + im2.y;
+          }
+          acc[2 * s] = re;
+          acc[2 * s + 1] = im;
+        }
+        const float v = warp_transpose_reduce32(acc, lane);
+        const float other = __shfl_xor_sync(kFull, v, 1);
+        const int s = lane >> 1;
+        const bool is_im = (lane & 1) != 0;
+        if (b0 + s < nc) {
+          const float re = is_im ? other : v;
+          const float im = is_im ? v : other;
+          const float2 r = sRot[b0 + s];
+          const float out = is_im ? fmaf(im, r.x, re * r.y) : fmaf(re, r.x, -im * r.y);
+          float* dst = prow + 2 * (n0 + b0) + lane;
+          *dst = first ? out : (*dst + out);
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint: one CTA per tile, g over the tile's pixels, fused epilogue.
+template <int D, int P>
+__global__ void __launch_bounds__(kTilePix / P) k_adjoint(const AdjParams p) {
+  constexpr int NT = kTilePix / P;
+  constexpr int RS = NT / 32;
+  constexpr int CPS = cpair_stride(D);
+  extern __shared__ float4 smem4[];
+  float* sC = reinterpret_cast<float*>(smem4);
+  float4* sY = reinterpret_cast<float4*>(sC + kSpotChunk * CPS);   // [chunk][2] float4
+
+  const Geometry& G = p.g;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int N = G.N;
+  const int tile = blockIdx.x;
+
+  float2 dz[P / 2][D];
+  load_dz<D, P>(p.dz, tile, t, dz);
+  float2 re2[P / 2], im2[P / 2];
+#pragma unroll
+  for (int q = 0; q < P / 2; ++q) {
+    re2[q] = make_float2(0.0f, 0.0f);
+    im2[q] = make_float2(0.0f, 0.0f);
+  }
+
+  const float2* anc = p.anchors + (size_t)tile * D;
+  for (int n0 = 0; n0 < N; n0 += kSpotChunk) {
+    const int nc = min(kSpotChunk, N - n0);
+    __syncthreads();
+    for (int s = t; s < nc; s += NT) {
+      const float bt = stage_spot<D>(p.coeff, anc, n0 + s, sC + s * CPS);
+      const float2 r = cis_turns(bt);
+      const float2 y = __ldg(p.y + n0 + s);
+      const float yr = y.x * r.x - y.y * r.y;
+      const float yi = y.x * r.y + y.y * r.x;
+      sY[2 * s] = make_float4(yr, yr, yi, yi);
+      sY[2 * s + 1] = make_float4(-yi, -yi, 0.0f, 0.0f);
+    }
+    __syncthreads();
+
+#pragma unroll 2
+    for (int s = 0; s < nc; ++s) {
+      float2 cc[D];
+      load_cpairs<D>(sC + s * CPS, cc);
+      const float4 ya = sY[2 * s];
+      const float4 yb = sY[2 * s + 1];
+      const float2 yr2 = make_float2(ya.x, ya.y);
+      const float2 yi2 = make_float2(ya.z, ya.w);
+      const float2 nyi2 = make_float2(yb.x, yb.y);
+#pragma unroll
+      for (int q = 0; q < P / 2; ++q) {
+        const float2 x = local_phase<D>(cc, dz[q]);
+        float2 sn, cs;
+        sincos2(x, sn, cs);
+        re2[q] = fma2(yr2, cs, re2[q]);
+        re2[q] = fma2(nyi2, sn, re2[q]);
+        im2[q] = fma2(yi2, cs, im2[q]);
+        im2[q] = fma2(yr2, sn, im2[q]);
+      }
+    }
+  }
+
+  const int tx = tile % G.tiles_x, ty = tile / G.tiles_x;
+  const int i = tx * kTileX + lane;
+  float a[P];
+  if (p.epilogue & kEpiGradPhase) {
+    const float4* asrc = reinterpret_cast<const float4*>(p.amp_img + ((size_t)tile * NT + t) * P);
+#pragma unroll
+    for (int q = 0; q < P / 4; ++q) {
+      const float4 v = __ldg(asrc + q);
+      a[4 * q] = v.x; a[4 * q + 1] = v.y; a[4 * q + 2] = v.z; a[4 * q + 3] = v.w;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < P; ++k) {
+    const int j = ty * kTileY + w + RS * k;
+    if (i >= G.nx || j >= G.ny) continue;
+    const size_t m = (size_t)j * G.nx + i;
+    const float gr = (k & 1) ? re2[k >> 1].y : re2[k >> 1].x;
+    const float gi = (k & 1) ? im2[k >> 1].y : im2[k >> 1].x;
+    if (p.epilogue & kEpiField) p.g_out[m] = make_float2(gr, gi);
+    if (p.epilogue & kEpiPhase) p.phase_out[m] = (gr == 0.0f && gi == 0.0f) ? 0.0f : atan2f(gi, gr);
+    if (p.epilogue & kEpiGradPhase) {
+      float s, c;
+      sincosf(__ldg(p.phase_in + m), &s, &c);
+      const float fr = a[k] * c, fi = a[k] * s;
+      p.dphase[m] = fr * gi - fi * gr;   // -Im(f conj(h))
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Coefficient gradient (spot-stationary): partial[b][n][d] =
+//   sum over the tiles of CTA column b of Z_d(m) * Im(conj(gradE_n) f_m K_nm).
+// Tiles are staged through shared memory as [pixel][dZ (D), Z (D), fr, fi].
+__host__ __device__ constexpr int gradc_rec(int D) { return ((2 * D + 2) + 3) & ~3; }
+__host__ __device__ constexpr size_t gradc_smem_bytes(int D) { return (size_t)kTilePix * gradc_rec(D) * 4; }
+
+template <int D>
+__global__ void __launch_bounds__(kGradThreads) k_gradc(const GradCParams p) {
+  constexpr int S = kGradSpots;
+  constexpr int REC = gradc_rec(D);
+  extern __shared__ float4 smem4[];
+  float* sP = reinterpret_cast<float*>(smem4);
+  const Geometry& G = p.g;
+  const int P = G.P, NTp = G.NT;   // pixel layout of the register-image arrays
+  const int t = threadIdx.x;
+  const int N = G.N;
+  const int nbase = blockIdx.y * (kGradThreads * S) + t;
+
+  float c[S][D];
+  float mom[S][D];
+  float2 gE[S];
+  bool act[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int n = nbase + s * kGradThreads;
+    act[s] = n < N;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      c[s][d] = act[s] ? __ldg(p.coeff + (size_t)n * D + d) : 0.0f;
+      mom[s][d] = 0.0f;
+    }
+    gE[s] = act[s] ? __ldg(p.gradE + n) : make_float2(0.0f, 0.0f);
+  }
+
+  for (int tile = blockIdx.x; tile < G.T; tile += gridDim.x) {
+    const int tx = tile % G.tiles_x, ty = tile / G.tiles_x;
+    const float2* anc = p.anchors + (size_t)tile * D;
+    __syncthreads();
+    // stage the tile: pixel (tp, k) of the register-image layout -> record
+    for (int e = t; e < kTilePix; e += kGradThreads) {
+      const int tp = e / P, k = e % P;
+      const int lane = tp & 31, wq = tp >> 5;
+      const int i = tx * kTileX + lane;
+      const int j = ty * kTileY + wq + (NTp / 32) * k;
+      const bool valid = (i < G.nx) && (j < G.ny);
+      float* rec = sP + (size_t)e * REC;
+      const float* src = p.dz + ((size_t)tile * NTp + tp) * D * P + k;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const float dzv = __ldg(src + d * P);
+        const float2 a = __ldg(anc + d);
+        rec[d] = dzv;
+        rec[D + d] = dzv + 6.283185307179586f * (a.x + a.y);
+      }
+      float fr = 0.0f, fi = 0.0f;
+      if (valid) {
+        const float amp = __ldg(p.amp_img + ((size_t)tile * NTp + tp) * P + k);
+        float sn, cs;
+        sincosf(__ldg(p.phase + (size_t)j * G.nx + i), &sn, &cs);
+        fr = amp * cs;
+        fi = amp * sn;
+      }
+      rec[2 * D] = fr;
+      rec[2 * D + 1] = fi;
+    }
+    // gamma = conj(gradE) exp(-i 2 pi base)
+    float gr[S], gi[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      float2 a[D];
+#pragma unroll
+      for (int d = 0; d < D; ++d) a[d] = __ldg(anc + d);
+      const float bt = base_turns<D>(c[s], a);
+      const float2 r = cis_turns(-bt);
+      // (gE.x - i gE.y)(r.x + i r.y)
+      gr[s] = gE[s].x * r.x + gE[s].y * r.y;
+      gi[s] = gE[s].x * r.y - gE[s].y * r.x;
+    }
+    __syncthreads();
+    for (int e = 0; e < kTilePix; ++e) {
+      const float* rec = sP + (size_t)e * REC;
+      float z[D], za[D];
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        z[d] = rec[d];
+        za[d] = rec[D + d];
+      }
+      const float fr = rec[2 * D], fi = rec[2 * D + 1];
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        float x = c[s][0] * z[0];
+#pragma unroll
+        for (int d = 1; d < D; ++d) x = fmaf(c[s][d], z[d], x);
+        const float sn = __sinf(x), cs = __cosf(x);
+        const float vr = fmaf(fr, cs, fi * sn);
+        const float vi = fmaf(fi, cs, -fr * sn);
+        const float q = fmaf(gr[s], vi, gi[s] * vr);
+#pragma unroll
+        for (int d = 0; d < D; ++d) mom[s][d] = fmaf(q, za[d], mom[s][d]);
+      }
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int n = nbase + s * kGradThreads;
+    if (!act[s]) continue;
+#pragma unroll
+    for (int d = 0; d < D; ++d) p.partial[((size_t)blockIdx.x * N + n) * D + d] = mom[s][d];
+  }
+}
+
+}  // namespace ash

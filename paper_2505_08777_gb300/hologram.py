@@ -1,0 +1,157 @@
+"""Thin torch-facing binding over the C ABI (include/ash.h).
+
+Argument marshalling only: tensors are checked for device, dtype and
+contiguity, then their device pointers and torch's current CUDA stream are
+handed to libash. Every step of the computation runs in the library's CUDA
+kernels; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+
+__all__ = ["Hologram"]
+
+
+def _stream_ptr(stream=None) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None) -> ctypes.c_void_p:
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _need(t: torch.Tensor, dtype, shape, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+class Hologram:
+    """One hologram: SLM grid (ny, nx), illumination amplitude, basis and the
+    N x D coefficient matrix (paper Sec. II / Methods). Owns a libash handle."""
+
+    def __init__(self, amp: torch.Tensor, coeff: torch.Tensor, noll=None, basis: torch.Tensor | None = None,
+                 stream=None):
+        self._lib = _lib.load()
+        self._h = ctypes.c_void_p(0)
+        if amp.dim() != 2:
+            raise ValueError("amp must be (ny, nx)")
+        self.ny, self.nx = int(amp.shape[0]), int(amp.shape[1])
+        if coeff.dim() != 2:
+            raise ValueError("coeff must be (N, D)")
+        self.N, self.D = int(coeff.shape[0]), int(coeff.shape[1])
+        _need(amp, torch.float32, (self.ny, self.nx), "amp")
+        _need(coeff, torch.float32, (self.N, self.D), "coeff")
+        noll_arr = None
+        if noll is not None:
+            noll = [int(v) for v in noll]
+            if len(noll) != self.D:
+                raise ValueError("noll must list one index per column of coeff")
+            noll_arr = (ctypes.c_int * self.D)(*noll)
+        if basis is not None:
+            _need(basis, torch.float32, (self.D, self.ny, self.nx), "basis")
+        self.noll = noll
+        st = self._lib.ash_hologram_create(ctypes.byref(self._h), self.nx, self.ny, _ptr(amp), self.D,
+                                           noll_arr, _ptr(basis), self.N, _ptr(coeff), _stream_ptr(stream))
+        _lib.check(st, "ash_hologram_create")
+
+    # -- lifetime ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            torch.cuda.current_stream().synchronize()
+            self._lib.ash_hologram_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    @property
+    def M(self) -> int:
+        return self.nx * self.ny
+
+    def workspace_bytes(self) -> int:
+        b = ctypes.c_size_t(0)
+        _lib.check(self._lib.ash_hologram_info(self._h, None, None, None, None, ctypes.byref(b)), "ash_hologram_info")
+        return int(b.value)
+
+    # -- state ------------------------------------------------------------
+    def set_coefficients(self, coeff: torch.Tensor, stream=None):
+        _need(coeff, torch.float32, (self.N, self.D), "coeff")
+        _lib.check(self._lib.ash_set_coefficients(self._h, _ptr(coeff), _stream_ptr(stream)), "ash_set_coefficients")
+
+    def set_amplitude(self, amp: torch.Tensor, stream=None):
+        _need(amp, torch.float32, (self.ny, self.nx), "amp")
+        _lib.check(self._lib.ash_set_amplitude(self._h, _ptr(amp), _stream_ptr(stream)), "ash_set_amplitude")
+
+    # -- transforms -------------------------------------------------------
+    def forward(self, phase: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """E_n = sum_m A_m exp(i phase_m) exp(-i C_n . Z_m) -> complex64 (N,)."""
+        _need(phase, torch.float32, (self.ny, self.nx), "phase")
+        E = out if out is not None else torch.empty(self.N, dtype=torch.complex64, device=phase.device)
+        _need(E, torch.complex64, (self.N,), "out")
+        _lib.check(self._lib.ash_forward(self._h, _ptr(phase), _ptr(E), _stream_ptr(stream)), "ash_forward")
+        return E
+
+    def forward_field(self, field: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """E_n = sum_m field_m exp(-i C_n . Z_m) for a complex64 (ny, nx) field."""
+        _need(field, torch.complex64, (self.ny, self.nx), "field")
+        E = out if out is not None else torch.empty(self.N, dtype=torch.complex64, device=field.device)
+        _need(E, torch.complex64, (self.N,), "out")
+        _lib.check(self._lib.ash_forward_field(self._h, _ptr(field), _ptr(E), _stream_ptr(stream)), "ash_forward_field")
+        return E
+
+    def adjoint(self, y: torch.Tensor, want_field: bool = True, want_phase: bool = False, stream=None):
+        """g_m = sum_n y_n exp(+i C_n . Z_m); returns (g complex64 (ny, nx) or None,
+        phase float32 (ny, nx) or None)."""
+        _need(y, torch.complex64, (self.N,), "y")
+        g = torch.empty((self.ny, self.nx), dtype=torch.complex64, device=y.device) if want_field else None
+        ph = torch.empty((self.ny, self.nx), dtype=torch.float32, device=y.device) if want_phase else None
+        _lib.check(self._lib.ash_adjoint(self._h, _ptr(y), _ptr(g), _ptr(ph), _stream_ptr(stream)), "ash_adjoint")
+        return g, ph
+
+    def wgs(self, phase: torch.Tensor, weights: torch.Tensor, target: torch.Tensor, iters: int,
+            E_out: torch.Tensor | None = None, metrics_out: torch.Tensor | None = None, stream=None):
+        """Weighted GS, in place on (phase, weights). Returns (E, metrics) where
+        metrics = [uniformity, efficiency, sum |E|^2, min |E|^2/T^2]."""
+        _need(phase, torch.float32, (self.ny, self.nx), "phase")
+        _need(weights, torch.float32, (self.N,), "weights")
+        _need(target, torch.float32, (self.N,), "target")
+        E = E_out if E_out is not None else torch.empty(self.N, dtype=torch.complex64, device=phase.device)
+        met = metrics_out if metrics_out is not None else torch.empty(4, dtype=torch.float32, device=phase.device)
+        _lib.check(self._lib.ash_wgs_iterate(self._h, _ptr(phase), _ptr(weights), _ptr(target), int(iters), _ptr(E),
+                                             _ptr(met), _stream_ptr(stream)), "ash_wgs_iterate")
+        return E, met
+
+    def grad(self, phase: torch.Tensor, grad_E: torch.Tensor, want_phase: bool = True, want_coeff: bool = True,
+             stream=None):
+        """(dL/dphase (ny, nx) or None, dL/dC (N, D) or None) from grad_E = dL/dRe E + i dL/dIm E."""
+        _need(phase, torch.float32, (self.ny, self.nx), "phase")
+        _need(grad_E, torch.complex64, (self.N,), "grad_E")
+        dph = torch.empty((self.ny, self.nx), dtype=torch.float32, device=phase.device) if want_phase else None
+        dC = torch.empty((self.N, self.D), dtype=torch.float32, device=phase.device) if want_coeff else None
+        _lib.check(self._lib.ash_grad(self._h, _ptr(phase), _ptr(grad_E), _ptr(dph), _ptr(dC), _stream_ptr(stream)),
+                   "ash_grad")
+        return dph, dC
+
+    def check(self, stream=None):
+        _lib.check(self._lib.ash_hologram_check(self._h, _stream_ptr(stream)), "ash_hologram_check")

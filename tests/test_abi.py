@@ -1,0 +1,94 @@
+"""The C ABI library: loads, exports every symbol include/ash.h declares, and
+rejects bad arguments on the host before touching the GPU (CPU only)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ash.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = set(re.findall(r"\b(ash_[a-z_0-9]+)\s*\(", text))
+    return sorted(n for n in names if not n.endswith("_fn"))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2505_08777_gb300 as P
+    lib_path = os.path.join(ROOT, "paper_2505_08777_gb300", "libash.so")
+    if not os.path.exists(lib_path):
+        P.build()
+    return P.load_library()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    from paper_2505_08777_gb300 import _lib
+    assert set(_lib.SIGNATURES) == set(names)
+
+
+def test_abi_version_and_status_strings(lib):
+    assert lib.ash_abi_version() == 1
+    assert lib.ash_status_string(0) == b"ASH_OK"
+    assert lib.ash_status_string(1) == b"ASH_ERR_INVALID_ARG"
+    assert lib.ash_status_string(99) == b"ASH_ERR_UNKNOWN"
+
+
+def _create(lib, nx, ny, D, N, noll=True, amp=1, coeff=1, basis=0):
+    h = ctypes.c_void_p(0)
+    arr = (ctypes.c_int * max(D, 1))(*([2] * max(D, 1))) if noll else None
+    st = lib.ash_hologram_create(ctypes.byref(h), nx, ny, ctypes.c_void_p(amp), D, arr, ctypes.c_void_p(basis), N,
+                                 ctypes.c_void_p(coeff), None)
+    return st, h
+
+
+def test_invalid_arguments_rejected_without_gpu(lib):
+    # argument checks run before any CUDA call, so they work on a CPU-only host
+    assert _create(lib, 0, 8, 2, 4)[0] == 1
+    assert _create(lib, 8, 20000, 2, 4)[0] == 1
+    assert _create(lib, 8, 8, 0, 4)[0] == 1
+    assert _create(lib, 8, 8, 17, 4)[0] == 1
+    assert _create(lib, 8, 8, 2, 0)[0] == 1
+    assert _create(lib, 8, 8, 2, 4, amp=0)[0] == 1
+    assert _create(lib, 8, 8, 2, 4, noll=False)[0] == 1          # neither noll nor basis
+    assert _create(lib, 8, 8, 2, 4, noll=True, basis=64)[0] == 1  # both
+    assert b"exactly one" in lib.ash_last_error()
+    bad = (ctypes.c_int * 2)(2, 0)
+    h = ctypes.c_void_p(0)
+    st = lib.ash_hologram_create(ctypes.byref(h), 8, 8, ctypes.c_void_p(1), 2, bad, None, 4, ctypes.c_void_p(1), None)
+    assert st == 1 and b"Noll" in lib.ash_last_error()
+    for fn, args in [("ash_forward", (None, None, None, None)), ("ash_adjoint", (None, None, None, None, None)),
+                     ("ash_wgs_iterate", (None, None, None, None, 1, None, None, None)),
+                     ("ash_grad", (None, None, None, None, None, None)), ("ash_hologram_check", (None, None))]:
+        assert getattr(lib, fn)(*args) == 1, fn
+    assert lib.ash_debug_fail_after(-1) == 1
+
+
+def test_fault_injection_counts_calls(lib):
+    # the n-th launching call fails with ASH_ERR_INJECTED; argument errors are not counted
+    assert lib.ash_debug_fail_after(1) == 0
+    st, _ = _create(lib, 8, 8, 2, 4)
+    assert st == 6 and b"injected" in lib.ash_last_error()
+    assert lib.ash_debug_fail_after(0) == 0
+
+
+def test_allocator_hook_validation(lib):
+    from paper_2505_08777_gb300 import _lib
+    alloc = _lib.ALLOC_FN(lambda ctx, n, s: None)
+    assert lib.ash_set_allocator(alloc, _lib.FREE_FN(0), None) == 1
+    assert lib.ash_set_allocator(_lib.ALLOC_FN(0), _lib.FREE_FN(0), None) == 0
+
+
+def test_python_binding_rejects_cpu_tensors():
+    torch = pytest.importorskip("torch")
+    from paper_2505_08777_gb300 import Hologram
+    with pytest.raises(ValueError):
+        Hologram(torch.ones(4, 4), torch.zeros(2, 3), noll=[2, 3, 4])
