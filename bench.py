@@ -1,0 +1,353 @@
+"""Benchmark of the aberration-space holography hot path on GB300.
+
+One step = one complete weighted-GS solve of the anisoplanatic 2D workload
+(1024 x 1024 SLM, N = 400 spots in a 20 x 20 grid over +-0.45 Nyquist,
+50 isoplanatic patches, D = 10 Zernike modes, 50 iterations + the final
+forward and metrics), inputs resident in HBM. The metric counts spot-kernel
+terms (one (spot, pixel) phase + sincos + complex MAC) of the forward and
+adjoint passes: terms/step = (2 * iters + 1) * N * M.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank solves its own independent hologram (weak scaling,
+no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "spot-kernel Gterm/s (N*M phase+sincos+cMAC) fwd+adj; WGS iter/s at 1024^2 x 400"
+UNIT = "Gterm/s"
+L2_FLUSH_BYTES = 256 << 20
+MUFU_PER_CLK_PER_SM = 16          # measured: sin.approx / cos.approx throughput per SM per clock
+MUFU_PER_TERM = 2                 # one sin and one cos per term
+MAX_SM_MHZ = 2070.0
+
+
+def _workload_config(p, iters):
+    return {
+        "workload": f"anisoplanatic 2D tweezer array: SLM {p.nx}x{p.ny}, N={p.N} spots (20x20 grid, +-0.45 Nyquist, "
+                    f"50 isoplanatic patches x 8 modes), D={p.D} (Noll 2-11), {iters} WGS iterations per step",
+        "nx": p.nx, "ny": p.ny, "N": p.N, "D": p.D, "iters_per_step": iters,
+        "terms_per_step": (2 * iters + 1) * p.N * p.M,
+        "l2": "flushed between steps (256 MiB write)",
+        "parallelism": "one independent hologram per GPU",
+    }
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        top = max(sm)
+        loaded = [s for s in sm if s >= 0.5 * top] or sm
+        return {"sm_mhz": float(np.median(loaded)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_sample(p, Z, workers):
+    """One WGS iteration of the workload on the CPU oracle (forward + spot
+    update + adjoint over the full grid and all spots). Returns (terms, s)."""
+    from oracle import transform, wgs
+    A = p.amp.astype(np.float64).ravel()
+    C = p.coeff.astype(np.float64)
+    t0 = time.perf_counter()
+    E = transform.forward(transform.field(A, p.phase0), C, Z, workers=workers)
+    w, y = wgs.weight_update(E, p.target.astype(np.float64), p.target)
+    g = transform.adjoint(y, C, Z, workers=workers)
+    transform.phase_of(g)
+    dt = time.perf_counter() - t0
+    return 2 * p.N * p.M, dt
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    from oracle import zernike
+    from workloads import config_c2
+    p = config_c2(1)
+    Z = zernike.basis(p.nx, p.ny, p.noll)
+    cores = _cpu_cores()
+    for _ in range(args.warmup):
+        oracle_sample(p, Z, cores)
+    terms, secs = 0, 0.0
+    for _ in range(args.steps):
+        t, dt = oracle_sample(p, Z, cores)
+        terms += t
+        secs += dt
+    val = terms / secs / 1e9
+    sample = "one WGS iteration (forward + update + adjoint, full 1024x1024 grid, all 400 spots) per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "config": _workload_config(p, 1) | {"oracle": "numpy complex128, pixel chunks x all spots, thread pool"},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    from paper_2505_08777_gb300 import Hologram
+    from workloads import config_c2
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    p = config_c2(1 + rank)
+    iters = p.iters
+    terms_per_step = (2 * iters + 1) * p.N * p.M
+    stream = torch.cuda.current_stream()
+
+    t0 = time.perf_counter()
+    h = Hologram(torch.from_numpy(p.amp).to(dev), torch.from_numpy(p.coeff).to(dev), noll=p.noll)
+    create_s = time.perf_counter() - t0
+    phase0 = torch.from_numpy(p.phase0).to(dev)
+    target = torch.from_numpy(p.target).to(dev)
+    phase = torch.empty_like(phase0)
+    w = torch.empty_like(target)
+    E = torch.empty(p.N, dtype=torch.complex64, device=dev)
+    met = torch.empty(4, dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step():
+        phase.copy_(phase0)
+        w.copy_(target)
+        h.wgs(phase, w, target, iters, E_out=E, metrics_out=met)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, per-step CUDA events, L2 flushed in between
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        for k in range(args.steps):
+            flush.zero_()
+            phase.copy_(phase0)
+            w.copy_(target)
+            ev[k][0].record(stream)
+            h.wgs(phase, w, target, iters, E_out=E, metrics_out=met)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    uniformity = float(met[0].item())
+    t = torch.tensor([total_ms], device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    total_ms_max = float(t.item())
+    value = world * terms_per_step * args.steps / (total_ms_max * 1e-3) / 1e9
+
+    # ---- end to end through the public API with host buffers
+    ph_host = torch.from_numpy(p.phase0).pin_memory()
+    T_host = torch.from_numpy(p.target).pin_memory()
+    ph_out = torch.empty_like(ph_host).pin_memory()
+    E_out = torch.empty(p.N, dtype=torch.complex64).pin_memory()
+    met_out = torch.empty(4, dtype=torch.float32).pin_memory()
+    e2e_ms = 0.0
+    for k in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        phase.copy_(ph_host, non_blocking=True)
+        target.copy_(T_host, non_blocking=True)
+        w.copy_(target)
+        h.wgs(phase, w, target, iters, E_out=E, metrics_out=met)
+        ph_out.copy_(phase, non_blocking=True)
+        E_out.copy_(E, non_blocking=True)
+        met_out.copy_(met, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        e2e_ms += a.elapsed_time(b)
+    h2d = ph_host.numel() * 4 + T_host.numel() * 4
+    d2h = ph_out.numel() * 4 + E_out.numel() * 8 + 16
+    t = torch.tensor([e2e_ms], device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    e2e_value = world * terms_per_step * args.steps / (float(t.item()) * 1e-3) / 1e9
+
+    # ---- per-kernel timing (same stream, CUDA events around each launch)
+    rng = np.random.default_rng(5)
+    y = torch.from_numpy((rng.normal(size=p.N) + 1j * rng.normal(size=p.N)).astype(np.complex64)).to(dev)
+    g_field = torch.empty((p.ny, p.nx), dtype=torch.complex64, device=dev)
+    gE = y.clone()
+
+    def time_launches(fn, reps=20):
+        fn()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / reps
+
+    lib_ph = torch.empty((p.ny, p.nx), dtype=torch.float32, device=dev)
+    from paper_2505_08777_gb300 import _lib
+    L = _lib.load()
+    import ctypes
+
+    def adj_only():
+        _lib.check(L.ash_adjoint(h.handle, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(0),
+                                 ctypes.c_void_p(lib_ph.data_ptr()), ctypes.c_void_p(stream.cuda_stream)), "adjoint")
+
+    def fwd_only():
+        h.forward(phase0, out=E)
+
+    def grad_both():
+        h.grad(phase0, gE)
+
+    adj_ms = time_launches(adj_only)
+    fwd_ms = time_launches(fwd_only)
+    grad_ms = time_launches(grad_both, reps=5)
+    NM = p.N * p.M
+    adj_gterm = NM / (adj_ms * 1e-3) / 1e9
+    fwd_gterm = NM / (fwd_ms * 1e-3) / 1e9
+    grad_gterm = 2 * NM / (grad_ms * 1e-3) / 1e9
+
+    clk = clocks.summary()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * (MUFU_PER_CLK_PER_SM / MUFU_PER_TERM) * MAX_SM_MHZ * 1e6 / 1e9
+    roofline = {
+        "bound": "alu", "kernel": "k_adjoint<D=10,P=8> (pixel-stationary adjoint, phase epilogue)",
+        "achieved": adj_gterm, "peak": peak, "unit": "Gterm/s", "frac": adj_gterm / peak,
+        "peak_basis": f"MUFU pipe: {MUFU_PER_CLK_PER_SM} sin/cos per clk per SM (measured), 2 per term, "
+                      f"{sms} SMs x {MAX_SM_MHZ:.0f} MHz max clock",
+        "traffic": None,
+        "frac_at_sampled_clock": (adj_gterm / (peak * clk["sm_mhz"] / MAX_SM_MHZ)) if clk.get("sm_mhz") else None,
+    }
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic", "config": _workload_config(p, iters),
+        "wgs_iter_per_s": world * iters * args.steps / (total_ms_max * 1e-3),
+        "final_uniformity": uniformity,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": (4 * iters + 3) * args.steps,
+        "roofline": roofline,
+        "kernels": {"forward_gterm_s": fwd_gterm, "adjoint_gterm_s": adj_gterm, "grad_phase+coeff_gterm_s": grad_gterm,
+                    "forward_ms": fwd_ms, "adjoint_ms": adj_ms, "grad_ms": grad_ms, "create_s": create_s},
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import zernike
+        Z = zernike.basis(p.nx, p.ny, p.noll)
+        cores = _cpu_cores()
+        terms, secs = oracle_sample(p, Z, cores)
+        line["cpu_baseline"] = {"value": terms / secs / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": "one WGS iteration (forward + update + adjoint) over the full 1024x1024 "
+                                          "grid and all 400 spots, numpy complex128 thread pool",
+                                "seconds": secs}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
