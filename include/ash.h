@@ -215,6 +215,38 @@ ash_status ash_grad(ash_hologram *h, const float *phase, const float *grad_E, fl
  */
 ash_status ash_hologram_check(ash_hologram *h, void *stream);
 
+/*
+ * Allocation-free forward transform. The paper has no counterpart: this is
+ * an interface for callers that cannot allocate device memory -- a host
+ * framework that owns all device memory and forbids cudaMalloc once running,
+ * a real-time SLM control loop that must not allocate, a plugin that only
+ * receives pre-allocated buffers. Such callers cannot create a handle, so
+ * every input is passed directly:
+ *   E_n = sum_m amp_m exp(i phase_m) exp(-i coeff_n . basis_m)
+ *   nx, ny  grid, 1 <= nx, ny <= 16384.
+ *   amp, phase  device float[ny*nx] (row-major).
+ *   D       1 <= D <= ASH_MAX_MODES.
+ *   basis   device float[D*ny*nx], row d = Z_d over the grid (row-major).
+ *   N       1 <= N <= 131072.
+ *   coeff   device float[N*D] (row-major).
+ *   E       device float[2*N] (complex64, 8-byte aligned), overwritten.
+ * It calls no cudaMalloc, cudaFree or other allocating routine. Its split-M
+ * partial sums live in a fixed 8 MiB __device__ array inside the library
+ * (every GPU that loads the library holds it until the process exits); N is
+ * limited so that at least one CTA's rows fit, and larger N returns
+ * ASH_ERR_INVALID_ARG. All calls share that array and it keeps the last
+ * call's contents (each call overwrites every row it later reads), so calls
+ * whose kernels overlap on the GPU -- on different streams, or from several
+ * host threads -- race; serialise them. The first call on each device does a
+ * one-time set-up (it looks up the array's device address with that device
+ * current); make that first call before any stream capture. Precision and
+ * results match ash_forward on a handle created with the same basis, to fp32
+ * rounding.
+ */
+ash_status ash_forward_noalloc(int nx, int ny, const float *amp, const float *phase, int D,
+                               const float *basis, int N, const float *coeff, float *E,
+                               void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -57,6 +57,11 @@ cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 }  // namespace
 
+namespace ash {
+// Lets other translation units report through ash_last_error().
+void record_error(const char* msg) { g_last_error = msg; }
+}  // namespace ash
+
 struct ash_hologram {
   Geometry g{};
   int device = 0;
