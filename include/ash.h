@@ -210,6 +210,26 @@ ash_status ash_grad(ash_hologram *h, const float *phase, const float *grad_E, fl
                     float *dcoeff, void *stream);
 
 /*
+ * Number of kernel launches one ash_wgs_iterate call with `iters` iterations
+ * enqueues (transform kernels, reductions, fix-ups, spot updates, metrics);
+ * -1 on a NULL handle.
+ */
+int ash_wgs_launches(const ash_hologram *h, int iters);
+
+/*
+ * Measurement helper: runs each kernel of one WGS iteration once on
+ * `stream`, bracketed by CUDA events recorded on that stream, synchronises
+ * it, and writes the durations in milliseconds to the host array ms_out[6]:
+ *   {forward kernel, forward reduction, adjoint kernel (phase epilogue),
+ *    adjoint fix-up (0 if not needed), spot update, coefficient-gradient
+ *    kernel}.
+ *   phase  device float[ny*nx] (forward input); y device float[2*N]
+ *          (adjoint input and gradient input).
+ * The handle's workspace is used; outputs are discarded.
+ */
+ash_status ash_profile(ash_hologram *h, const float *phase, const float *y, float *ms_out, void *stream);
+
+/*
  * Synchronise `stream` and report device-side errors recorded by the
  * handle's kernels (ASH_ERR_DEVICE / ASH_ERR_TIMEOUT), clearing them.
  */

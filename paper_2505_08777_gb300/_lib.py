@@ -37,6 +37,8 @@ SIGNATURES = {
     "ash_wgs_iterate": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "ash_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "ash_hologram_check": (c_int, [c_void_p, c_void_p]),
+    "ash_wgs_launches": (c_int, [c_void_p, c_int]),
+    "ash_profile": (c_int, [c_void_p, c_void_p, c_void_p, c_float_p, c_void_p]),
     "ash_forward_noalloc": (c_int, [c_int, c_int, c_void_p, c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p,
                                     c_void_p]),
 }

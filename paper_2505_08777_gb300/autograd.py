@@ -1,0 +1,57 @@
+"""torch.autograd.Function over the library's forward transform and its
+hand-written gradient (paper Methods: gradients of the complex farfield
+weights propagated forward and backward through the transform).
+
+    E = spot_field(holo, phase, coeff)      # complex64 (N,)
+
+Backward takes torch's complex gradient convention, grad_E = dL/dRe E +
+i dL/dIm E, and returns dL/dphase (adjoint pass, ash_grad) and dL/dC (moment
+pass with the spot tiles recomputed, ash_grad); nothing of the forward is
+stored besides (phase, coeff).
+"""
+from __future__ import annotations
+
+import torch
+
+from .hologram import Hologram
+
+__all__ = ["SpotField", "spot_field"]
+
+
+class SpotField(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, phase: torch.Tensor, coeff: torch.Tensor, holo: Hologram) -> torch.Tensor:
+        phase = phase.detach().contiguous()
+        coeff = coeff.detach().contiguous()
+        holo.set_coefficients(coeff)
+        E = holo.forward(phase)
+        ctx.save_for_backward(phase, coeff)
+        ctx.holo = holo
+        return E
+
+    @staticmethod
+    def backward(ctx, grad_E: torch.Tensor):
+        phase, coeff = ctx.saved_tensors
+        holo: Hologram = ctx.holo
+        want_phase, want_coeff = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        if not (want_phase or want_coeff):
+            return None, None, None
+        holo.set_coefficients(coeff)
+        dphase, dcoeff = holo.grad(phase, grad_E.contiguous(), want_phase=want_phase, want_coeff=want_coeff)
+        return dphase, dcoeff, None
+
+
+def spot_field(holo: Hologram, phase: torch.Tensor, coeff: torch.Tensor | None = None) -> torch.Tensor:
+    """E_n = sum_m A_m exp(i phase_m) exp(-i coeff_n . Z_m), differentiable in
+    phase and coeff. `coeff` defaults to the handle's current coefficients
+    (then no gradient flows to them)."""
+    if coeff is None:
+        coeff = holo.coefficients()
+    return SpotField.apply(phase, coeff, holo)
+
+
+def spot_intensity_loss(E: torch.Tensor, t: torch.Tensor) -> torch.Tensor:
+    """L = sum_n (|E_n|^2 / mean|E|^2 - t_n)^2 (plain torch on N-vectors)."""
+    I = E.real * E.real + E.imag * E.imag
+    r = I / I.mean() - t
+    return (r * r).sum()

@@ -67,7 +67,9 @@ struct ash_hologram {
   int device = 0;
   cudaStream_t home = nullptr;     // stream the workspace was allocated on
   LaunchInfo li{};
-  int fwd_grid = 0, fwd_rows = 0, tiles_per_cta = 0;
+  Schedule sched{};           // (tile, spot) ranges of the transform kernels
+  bool split_tiles = false;   // some tile's spots span two CTA ranges
+  int fwd_rows = 0;
   int gradc_gx = 0, gradc_gy = 0;
   // workspace
   float* dz = nullptr;
@@ -75,6 +77,7 @@ struct ash_hologram {
   float2* anchors = nullptr;
   float* coeff = nullptr;
   float* partial = nullptr;
+  float2* split = nullptr;
   float* gradc_partial = nullptr;
   float2* E = nullptr;
   float2* y = nullptr;
@@ -183,9 +186,9 @@ ash_status enqueue_forward(ash_hologram* h, int source, const float* phase, cons
   p.phase = phase;
   p.field = field;
   p.source = source;
+  p.sched = h->sched;
   p.partial = h->partial;
-  p.tiles_per_cta = h->tiles_per_cta;
-  cudaError_t e = launch_forward(h->g.D, p, h->fwd_grid, s);
+  cudaError_t e = launch_forward(h->g.D, p, h->sched.G, s);
   if (e != cudaSuccess) return cuda_fail(e, "forward kernel launch");
   const int cols = 2 * h->g.N;
   k_col_reduce<<<(cols + 31) / 32, dim3(32, 32), 0, s>>>(h->partial, h->fwd_rows, cols, reinterpret_cast<float*>(E));
@@ -208,8 +211,15 @@ ash_status enqueue_adjoint(ash_hologram* h, const float2* y, float2* g_out, floa
   p.phase_in = phase_in;
   p.dphase = dphase;
   p.epilogue = epilogue;
-  cudaError_t e = launch_adjoint(h->g.D, p, h->g.T, s);
+  p.sched = h->sched;
+  p.split = h->split;
+  cudaError_t e = launch_adjoint(h->g.D, p, h->sched.G, s);
   if (e != cudaSuccess) return cuda_fail(e, "adjoint kernel launch");
+  if (h->split_tiles) {
+    k_adjoint_fixup<<<h->g.T, h->g.NT, 0, s>>>(p);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint fix-up launch");
+  }
   return ASH_OK;
 }
 
@@ -323,10 +333,22 @@ ash_status ash_hologram_create(ash_hologram** out, int nx, int ny, const float* 
   if (ce != cudaSuccess) return fail(cuda_fail(ce, "kernel preparation"));
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-  const int fwd_slots = sms * (h->li.fwd_ctas_per_sm > 0 ? h->li.fwd_ctas_per_sm : 1);
-  h->fwd_grid = g.T < fwd_slots ? g.T : fwd_slots;
-  h->tiles_per_cta = (g.T + h->fwd_grid - 1) / h->fwd_grid;
-  h->fwd_rows = h->fwd_grid * (g.NT / 32);
+  {
+    // One range of (tile, spot) units per resident CTA; at least min(256, N)
+    // units per CTA so that small problems keep whole tiles together.
+    int per_sm = h->li.fwd_ctas_per_sm < h->li.adj_ctas_per_sm ? h->li.fwd_ctas_per_sm : h->li.adj_ctas_per_sm;
+    if (per_sm < 1) per_sm = 1;
+    const long long W = (long long)g.T * N;
+    const long long umin = N < 256 ? N : 256;
+    long long G = (long long)sms * per_sm;
+    if (G > W / umin) G = W / umin;
+    if (G < 1) G = 1;
+    h->sched.W = W;
+    h->sched.G = (int)G;
+    for (int b = 1; b < h->sched.G; ++b)
+      if (h->sched.begin(b) % N != 0) h->split_tiles = true;
+  }
+  h->fwd_rows = g.T * (g.NT / 32);
   h->gradc_gy = (N + kGradThreads * kGradSpots - 1) / (kGradThreads * kGradSpots);
   {
     const int slots = sms * (h->li.gradc_ctas_per_sm > 0 ? h->li.gradc_ctas_per_sm : 1);
@@ -343,6 +365,7 @@ ash_status ash_hologram_create(ash_hologram** out, int nx, int ny, const float* 
   if ((st = ws(h, &h->anchors, (size_t)g.T * D)) != ASH_OK) return fail(st);
   if ((st = ws(h, &h->coeff, (size_t)N * D)) != ASH_OK) return fail(st);
   if ((st = ws(h, &h->partial, (size_t)h->fwd_rows * 2 * N)) != ASH_OK) return fail(st);
+  if ((st = ws(h, &h->split, (size_t)h->sched.G * 2 * kTilePix)) != ASH_OK) return fail(st);
   if ((st = ws(h, &h->gradc_partial, (size_t)h->gradc_gx * N * D)) != ASH_OK) return fail(st);
   if ((st = ws(h, &h->E, (size_t)N)) != ASH_OK) return fail(st);
   if ((st = ws(h, &h->y, (size_t)N)) != ASH_OK) return fail(st);
@@ -528,6 +551,104 @@ ash_status ash_grad(ash_hologram* h, const float* phase, const float* grad_E, fl
     ASH_CUDA(cudaGetLastError());
   }
   return ASH_OK;
+}
+
+int ash_wgs_launches(const ash_hologram* h, int iters) {
+  if (!h || iters < 0) return -1;
+  const int fwd = 2;                              // transform kernel + reduction
+  const int adj = h->split_tiles ? 2 : 1;         // transform kernel (+ fix-up)
+  return iters * (fwd + 1 + adj) + fwd + 1;       // + final forward and metrics
+}
+
+ash_status ash_profile(ash_hologram* h, const float* phase, const float* y, float* ms_out, void* stream) {
+  if (!h || !phase || !y || !ms_out) return set_error(ASH_ERR_INVALID_ARG, "NULL argument");
+  if (reinterpret_cast<uintptr_t>(y) & 7) return set_error(ASH_ERR_INVALID_ARG, "y must be 8-byte aligned");
+  if (injected_failure()) return set_error(ASH_ERR_INJECTED, "injected failure");
+  cudaStream_t s = as_stream(stream);
+  cudaEvent_t ev[12];
+  for (int q = 0; q < 12; ++q) ASH_CUDA(cudaEventCreate(&ev[q]));
+  const float2* y2 = reinterpret_cast<const float2*>(y);
+  ash_status st = ASH_OK;
+  cudaError_t e = cudaSuccess;
+  // forward kernel, then its reduction
+  FwdParams fp{};
+  fp.g = h->g;
+  fp.sched = h->sched;
+  fp.dz = h->dz;
+  fp.amp_img = h->amp_img;
+  fp.anchors = h->anchors;
+  fp.coeff = h->coeff;
+  fp.phase = phase;
+  fp.source = kSrcPhase;
+  fp.partial = h->partial;
+  const int cols = 2 * h->g.N;
+  cudaEventRecord(ev[0], s);
+  e = launch_forward(h->g.D, fp, h->sched.G, s);
+  cudaEventRecord(ev[1], s);
+  if (e == cudaSuccess) {
+    cudaEventRecord(ev[2], s);
+    k_col_reduce<<<(cols + 31) / 32, dim3(32, 32), 0, s>>>(h->partial, h->fwd_rows, cols,
+                                                            reinterpret_cast<float*>(h->E));
+    e = cudaGetLastError();
+    cudaEventRecord(ev[3], s);
+  }
+  // adjoint kernel (phase epilogue), then the fix-up
+  AdjParams ap{};
+  ap.g = h->g;
+  ap.sched = h->sched;
+  ap.split = h->split;
+  ap.dz = h->dz;
+  ap.amp_img = h->amp_img;
+  ap.anchors = h->anchors;
+  ap.coeff = h->coeff;
+  ap.y = y2;
+  ap.phase_out = h->wgs_phase;
+  ap.epilogue = kEpiPhase;
+  if (e == cudaSuccess) {
+    cudaEventRecord(ev[4], s);
+    e = launch_adjoint(h->g.D, ap, h->sched.G, s);
+    cudaEventRecord(ev[5], s);
+  }
+  if (e == cudaSuccess) {
+    cudaEventRecord(ev[6], s);
+    if (h->split_tiles) {
+      k_adjoint_fixup<<<h->g.T, h->g.NT, 0, s>>>(ap);
+      e = cudaGetLastError();
+    }
+    cudaEventRecord(ev[7], s);
+  }
+  if (e == cudaSuccess) {
+    cudaEventRecord(ev[8], s);
+    k_wgs_update<<<1, 1024, 0, s>>>(h->E, h->wgs_w, reinterpret_cast<const float*>(h->wgs_T), h->y, h->g.N);
+    e = cudaGetLastError();
+    cudaEventRecord(ev[9], s);
+  }
+  if (e == cudaSuccess) {
+    GradCParams gp{};
+    gp.g = h->g;
+    gp.dz = h->dz;
+    gp.amp_img = h->amp_img;
+    gp.anchors = h->anchors;
+    gp.coeff = h->coeff;
+    gp.phase = phase;
+    gp.gradE = y2;
+    gp.partial = h->gradc_partial;
+    cudaEventRecord(ev[10], s);
+    e = launch_gradc(h->g.D, gp, dim3(h->gradc_gx, h->gradc_gy), s);
+    cudaEventRecord(ev[11], s);
+  }
+  if (e != cudaSuccess) st = cuda_fail(e, "profile launch");
+  cudaError_t se = cudaStreamSynchronize(s);
+  if (st == ASH_OK && se != cudaSuccess) st = cuda_fail(se, "profile synchronise");
+  if (st == ASH_OK) {
+    for (int q = 0; q < 6; ++q) {
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, ev[2 * q], ev[2 * q + 1]);
+      ms_out[q] = ms;
+    }
+  }
+  for (int q = 0; q < 12; ++q) cudaEventDestroy(ev[q]);
+  return st;
 }
 
 ash_status ash_hologram_check(ash_hologram* h, void* stream) {

@@ -151,39 +151,83 @@ __global__ void k_col_reduce(const float* __restrict__ in, int rows, int cols, f
   if (threadIdx.y == 0 && c < cols) out[c] = red[0][threadIdx.x];
 }
 
-// Weighted GS spot update (one block of 1024 threads):
+// Deterministic block-wide fp32 sum (fixed shuffle tree, then a fixed tree
+// over the warps); every thread receives the result.
+template <int NTH>
+__device__ __forceinline__ float block_sum_f(float v, float* red) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  float s = lane < NTH / 32 ? red[lane] : 0.0f;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+// Weighted GS spot update (one block of 1024 threads, fp32):
 //   E^ = |E|/||E||, T^ = T/||T||, w <- w T^/max(E^, 1e-30), w <- w/||w||,
 //   y = w exp(i arg E) (arg 0 -> 0).
+// The norms only fix a global scale of w (removed by the renormalisation,
+// and arg g is invariant to it), so fp32 sums are sufficient.
 __global__ void __launch_bounds__(1024) k_wgs_update(const float2* __restrict__ E, float* __restrict__ w,
                                                      const float* __restrict__ T, float2* __restrict__ y, int N) {
-  __shared__ double red[32];
-  double se = 0.0, st = 0.0;
+  __shared__ float red[32];
+  float se = 0.0f, st = 0.0f;
   for (int n = threadIdx.x; n < N; n += 1024) {
     const float2 e = E[n];
-    se += (double)e.x * e.x + (double)e.y * e.y;
-    st += (double)T[n] * T[n];
+    se = fmaf(e.x, e.x, fmaf(e.y, e.y, se));
+    st = fmaf(T[n], T[n], st);
   }
-  se = block_sum<1024>(se, red);
-  st = block_sum<1024>(st, red);
-  const float inv_e = se > 0.0 ? (float)(1.0 / sqrt(se)) : 0.0f;
-  const float inv_t = (float)(1.0 / sqrt(st));
-  double sw = 0.0;
+  se = block_sum_f<1024>(se, red);
+  st = block_sum_f<1024>(st, red);
+  const float ne = sqrtf(se), nt = sqrtf(st);
+  float sw = 0.0f;
   for (int n = threadIdx.x; n < N; n += 1024) {
     const float2 e = E[n];
     const float ea = sqrtf(e.x * e.x + e.y * e.y);
-    const float eh = fmaxf(ea * inv_e, 1e-30f);
-    const float wn = w[n] * (T[n] * inv_t) / eh;
+    const float eh = fmaxf(ea / ne, 1e-30f);
+    const float wn = w[n] * (T[n] / nt) / eh;
     w[n] = wn;
-    sw += (double)wn * wn;
+    sw = fmaf(wn, wn, sw);
   }
-  sw = block_sum<1024>(sw, red);
-  const float inv_w = (float)(1.0 / sqrt(sw));
+  sw = block_sum_f<1024>(sw, red);
+  const float nw = sqrtf(sw);
   for (int n = threadIdx.x; n < N; n += 1024) {
-    const float wn = w[n] * inv_w;
+    const float wn = w[n] / nw;
     w[n] = wn;
     const float2 e = E[n];
     const float ea = sqrtf(e.x * e.x + e.y * e.y);
     y[n] = ea > 0.0f ? make_float2(wn * (e.x / ea), wn * (e.y / ea)) : make_float2(wn, 0.0f);
+  }
+}
+
+// Finishes tiles whose spot range was split between CTAs of k_adjoint: sums
+// the CTAs' partial fields in CTA order and applies the epilogue. One CTA of
+// G.NT threads per tile; tiles owned by a single CTA return at once.
+__global__ void k_adjoint_fixup(const AdjParams p) {
+  const Geometry& G = p.g;
+  const int tile = blockIdx.x, t = threadIdx.x;
+  const long long u_lo = (long long)tile * G.N, u_hi = u_lo + G.N - 1;
+  const int b_lo = p.sched.owner(u_lo), b_hi = p.sched.owner(u_hi);
+  if (b_lo == b_hi) return;
+  const int P = G.P, NT = G.NT;
+  const int tx = tile % G.tiles_x, ty = tile / G.tiles_x;
+  const int i = tx * kTileX + (t & 31);
+  for (int k = 0; k < P; ++k) {
+    float gr = 0.0f, gi = 0.0f;
+    for (int b = b_lo; b <= b_hi; ++b) {
+      const int slot = (p.sched.begin(b) / G.N == tile) ? 0 : 1;
+      const float2 v = p.split[((size_t)b * 2 + slot) * kTilePix + (size_t)k * NT + t];
+      gr += v.x;
+      gi += v.y;
+    }
+    const int j = ty * kTileY + (t >> 5) + (NT / 32) * k;
+    if (i >= G.nx || j >= G.ny) continue;
+    const float a = (p.epilogue & kEpiGradPhase) ? p.amp_img[((size_t)tile * NT + t) * P + k] : 0.0f;
+    adjoint_epilogue(p, (size_t)j * G.nx + i, gr, gi, a);
   }
 }
 

@@ -40,7 +40,18 @@ struct Geometry {
 
 // Pixels per thread for a given mode count (register budget of the
 // pixel-stationary kernels: P * D basis values live in registers).
-__host__ __device__ constexpr int pixels_per_thread(int D) { return D <= 12 ? 8 : 4; }
+#ifndef ASH_P_SMALL_D
+#define ASH_P_SMALL_D 8
+#endif
+__host__ __device__ constexpr int pixels_per_thread(int D) { return D <= 12 ? ASH_P_SMALL_D : 4; }
+
+// Launch bounds of the pixel-stationary kernels: optionally ask the register
+// allocator for ASH_MIN_BLOCKS resident CTAs per SM.
+#ifdef ASH_MIN_BLOCKS
+#define ASH_BOUNDS(P) __launch_bounds__(kTilePix / (P), ASH_MIN_BLOCKS)
+#else
+#define ASH_BOUNDS(P) __launch_bounds__(kTilePix / (P))
+#endif
 
 // ---------------------------------------------------------------------------
 // Packed fp32x2 arithmetic (Blackwell FFMA2): one instruction, two lanes of
@@ -110,8 +121,25 @@ __device__ __forceinline__ float2 cis_turns(float turns) {
 enum FwdSource : int { kSrcPhase = 0, kSrcField = 1 };
 enum AdjEpilogue : int { kEpiField = 1, kEpiPhase = 2, kEpiGradPhase = 4 };
 
+// Balanced static schedule: the T * N (tile, spot) work units, tile-major,
+// are cut into G equal contiguous ranges, one per CTA. A tile whose spots
+// fall into two or more ranges is finished by the adjoint fix-up pass.
+struct Schedule {
+  long long W;   // T * N
+  int G;         // CTAs
+  __host__ __device__ long long begin(int b) const { return ((long long)b * W) / G; }
+  // CTA owning work unit u
+  __host__ __device__ int owner(long long u) const {
+    int b = (int)((u * (long long)G) / W);
+    while (b + 1 < G && begin(b + 1) <= u) ++b;
+    while (b > 0 && begin(b) > u) --b;
+    return b;
+  }
+};
+
 struct FwdParams {
   Geometry g;
+  Schedule sched;
   const float* dz;        // register-image basis [T][NT][D][P]
   const float* amp_img;   // register-image amplitude [T][NT][P]
   const float2* anchors;  // [T][D] (hi, lo) of Z(anchor)/(2 pi)
@@ -119,12 +147,12 @@ struct FwdParams {
   const float* phase;     // user layout [ny][nx] (kSrcPhase)
   const float2* field;    // user layout [ny][nx] complex (kSrcField)
   int source;
-  float* partial;         // [rows][2N], rows = gridDim.x * (NT/32)
-  int tiles_per_cta;      // static schedule: CTA b handles tiles b, b+G, ...
+  float* partial;         // [T * NW][2N]: row (tile, warp), each entry written once
 };
 
 struct AdjParams {
   Geometry g;
+  Schedule sched;
   const float* dz;
   const float* amp_img;
   const float2* anchors;
@@ -134,8 +162,20 @@ struct AdjParams {
   float* phase_out;       // user layout or null
   const float* phase_in;  // for kEpiGradPhase: current phase (user layout)
   float* dphase;          // for kEpiGradPhase
+  float2* split;          // [G][2][kTilePix]: partial g of tiles split between CTAs
   int epilogue;
 };
+
+// Per-pixel adjoint epilogue (m = flat pixel index, a = amplitude there).
+__device__ __forceinline__ void adjoint_epilogue(const AdjParams& p, size_t m, float gr, float gi, float a) {
+  if (p.epilogue & kEpiField) p.g_out[m] = make_float2(gr, gi);
+  if (p.epilogue & kEpiPhase) p.phase_out[m] = (gr == 0.0f && gi == 0.0f) ? 0.0f : atan2f(gi, gr);
+  if (p.epilogue & kEpiGradPhase) {
+    float s, c;
+    sincosf(__ldg(p.phase_in + m), &s, &c);
+    p.dphase[m] = (a * c) * gi - (a * s) * gr;   // -Im(f conj(h)), f = a exp(i phase)
+  }
+}
 
 struct GradCParams {
   Geometry g;
@@ -146,7 +186,6 @@ struct GradCParams {
   const float* phase;     // user layout
   const float2* gradE;    // [N]
   float* partial;         // [gridDim.x][N][D]
-  int tiles_per_cta;
 };
 
 // Coefficient-gradient kernel shape: threads per CTA, spots per thread.

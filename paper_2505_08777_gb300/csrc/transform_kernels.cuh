@@ -100,6 +100,19 @@ __device__ __forceinline__ void load_cpairs(const float* __restrict__ sCrow, flo
 // Local phase of two pixels (one packed lane each) for one spot.
 template <int D>
 __device__ __forceinline__ float2 local_phase(const float2 (&cc)[D], const float2 (&z)[D]) {
+#if defined(ASH_SPLIT_CHAIN)
+  if (D >= 6) {
+    // two independent halves shorten the dependent FMA chain
+    constexpr int H = D / 2;
+    float2 xa = mul2(cc[0], z[0]);
+    float2 xb = mul2(cc[H], z[H]);
+#pragma unroll
+    for (int d = 1; d < H; ++d) xa = fma2(cc[d], z[d], xa);
+#pragma unroll
+    for (int d = H + 1; d < D; ++d) xb = fma2(cc[d], z[d], xb);
+    return make_float2(xa.x + xb.x, xa.y + xb.y);
+  }
+#endif
   float2 x = mul2(cc[0], z[0]);
 #pragma unroll
   for (int d = 1; d < D; ++d) x = fma2(cc[d], z[d], x);
@@ -114,71 +127,78 @@ __device__ __forceinline__ void sincos2(float2 x, float2& s, float2& c) {
 }
 
 // ---------------------------------------------------------------------------
-// Forward: partial[row][2n..2n+1] = sum over this warp's pixels of this
-// CTA's tiles of f_m exp(-i C_n . Z_m). Static persistent schedule.
+// Nearfield pairs f = A exp(i phase) (or a caller field) of a thread's P pixels.
+template <int P>
+__device__ __forceinline__ void load_field(const FwdParams& p, int tile, int t, float2 (&fr2)[P / 2],
+                                           float2 (&fi2)[P / 2], float2 (&nfr2)[P / 2]) {
+  constexpr int NT = kTilePix / P;
+  constexpr int RS = NT / 32;
+  const Geometry& G = p.g;
+  const int lane = t & 31, w = t >> 5;
+  const int tx = tile % G.tiles_x, ty = tile / G.tiles_x;
+  const int i = tx * kTileX + lane;
+  const float4* asrc = reinterpret_cast<const float4*>(p.amp_img + ((size_t)tile * NT + t) * P);
+  float a[P], fr[P], fi[P];
+#pragma unroll
+  for (int q = 0; q < P / 4; ++q) {
+    const float4 v = __ldg(asrc + q);
+    a[4 * q] = v.x; a[4 * q + 1] = v.y; a[4 * q + 2] = v.z; a[4 * q + 3] = v.w;
+  }
+#pragma unroll
+  for (int k = 0; k < P; ++k) {
+    const int j = ty * kTileY + w + RS * k;
+    const bool valid = (i < G.nx) && (j < G.ny);
+    const size_t m = (size_t)j * G.nx + i;
+    if (p.source == kSrcPhase) {
+      const float ph = valid ? __ldg(p.phase + m) : 0.0f;
+      float sn, cs;
+      sincosf(ph, &sn, &cs);
+      fr[k] = a[k] * cs;
+      fi[k] = a[k] * sn;
+    } else {
+      const float2 f = valid ? __ldg(p.field + m) : make_float2(0.0f, 0.0f);
+      fr[k] = f.x;
+      fi[k] = f.y;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < P / 2; ++q) {
+    fr2[q] = make_float2(fr[2 * q], fr[2 * q + 1]);
+    fi2[q] = make_float2(fi[2 * q], fi[2 * q + 1]);
+    nfr2[q] = make_float2(-fr[2 * q], -fr[2 * q + 1]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Forward: partial[(tile, warp)][2n..2n+1] = sum over the warp's pixels of the
+// tile of f_m exp(-i C_n . Z_m), for the (tile, spot) units of this CTA's
+// range. Every entry is written exactly once per launch.
 template <int D, int P>
-__global__ void __launch_bounds__(kTilePix / P) k_forward(const FwdParams p) {
+__global__ void ASH_BOUNDS(P) k_forward(const FwdParams p) {
   constexpr int NT = kTilePix / P;
   constexpr int NW = NT / 32;
-  constexpr int RS = NT / 32;
   constexpr int CPS = cpair_stride(D);
   extern __shared__ float4 smem4[];
   float* sC = reinterpret_cast<float*>(smem4);
   float2* sRot = reinterpret_cast<float2*>(sC + kSpotChunk * CPS);
 
-  const Geometry& G = p.g;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  const int N = G.N;
-  float* prow = p.partial + (size_t)(blockIdx.x * NW + w) * 2 * N;
+  const int N = p.g.N;
+  const long long u0 = p.sched.begin(blockIdx.x), u1 = p.sched.begin(blockIdx.x + 1);
+  const int tf = (int)(u0 / N), tl = (int)((u1 - 1) / N);
 
-  for (int it = 0; it < p.tiles_per_cta; ++it) {
-    const int tile = blockIdx.x + it * gridDim.x;
-    if (tile >= G.T) break;
-    const bool first = (it == 0);
-
+  for (int tile = tf; tile <= tl; ++tile) {
+    const int sb = (tile == tf) ? (int)(u0 - (long long)tile * N) : 0;
+    const int se = (tile == tl) ? (int)(u1 - (long long)tile * N) : N;
     float2 dz[P / 2][D];
     load_dz<D, P>(p.dz, tile, t, dz);
-
-    const int tx = tile % G.tiles_x, ty = tile / G.tiles_x;
-    const int i = tx * kTileX + lane;
-    float fr[P], fi[P];
-    {
-      const float4* asrc = reinterpret_cast<const float4*>(p.amp_img + ((size_t)tile * NT + t) * P);
-      float a[P];
-#pragma unroll
-      for (int q = 0; q < P / 4; ++q) {
-        const float4 v = __ldg(asrc + q);
-        a[4 * q] = v.x; a[4 * q + 1] = v.y; a[4 * q + 2] = v.z; a[4 * q + 3] = v.w;
-      }
-#pragma unroll
-      for (int k = 0; k < P; ++k) {
-        const int j = ty * kTileY + w + RS * k;
-        const bool valid = (i < G.nx) && (j < G.ny);
-        const size_t m = (size_t)j * G.nx + i;
-        if (p.source == kSrcPhase) {
-          const float ph = valid ? __ldg(p.phase + m) : 0.0f;
-          float s, c;
-          sincosf(ph, &s, &c);
-          fr[k] = a[k] * c;
-          fi[k] = a[k] * s;
-        } else {
-          const float2 f = valid ? __ldg(p.field + m) : make_float2(0.0f, 0.0f);
-          fr[k] = f.x;
-          fi[k] = f.y;
-        }
-      }
-    }
     float2 fr2[P / 2], fi2[P / 2], nfr2[P / 2];
-#pragma unroll
-    for (int q = 0; q < P / 2; ++q) {
-      fr2[q] = make_float2(fr[2 * q], fr[2 * q + 1]);
-      fi2[q] = make_float2(fi[2 * q], fi[2 * q + 1]);
-      nfr2[q] = make_float2(-fr[2 * q], -fr[2 * q + 1]);
-    }
-
+    load_field<P>(p, tile, t, fr2, fi2, nfr2);
+    float* prow = p.partial + ((size_t)tile * NW + w) * 2 * N;
     const float2* anc = p.anchors + (size_t)tile * D;
-    for (int n0 = 0; n0 < N; n0 += kSpotChunk) {
-      const int nc = min(kSpotChunk, N - n0);
+
+    for (int n0 = sb; n0 < se; n0 += kSpotChunk) {
+      const int nc = min(kSpotChunk, se - n0);
       __syncthreads();
       for (int s = t; s < nc; s += NT) {
         const float bt = stage_spot<D>(p.coeff, anc, n0 + s, sC + s * CPS);
@@ -219,9 +239,7 @@ __global__ void __launch_bounds__(kTilePix / P) k_forward(const FwdParams p) {
           const float re = is_im ? other : v;
           const float im = is_im ? v : other;
           const float2 r = sRot[b0 + s];
-          const float out = is_im ? fmaf(im, r.x, re * r.y) : fmaf(re, r.x, -im * r.y);
-          float* dst = prow + 2 * (n0 + b0) + lane;
-          *dst = first ? out : (*dst + out);
+          prow[2 * (n0 + b0) + lane] = is_im ? fmaf(im, r.x, re * r.y) : fmaf(re, r.x, -im * r.y);
         }
       }
     }
@@ -229,9 +247,12 @@ __global__ void __launch_bounds__(kTilePix / P) k_forward(const FwdParams p) {
 }
 
 // ---------------------------------------------------------------------------
-// Adjoint: one CTA per tile, g over the tile's pixels, fused epilogue.
+// Adjoint over this CTA's (tile, spot) range. Tiles whose full spot range is
+// owned by the CTA get the epilogue here; the partial sums of tiles split
+// between CTAs go to p.split (slot 0 = first tile of the range, 1 = last)
+// and are finished by k_adjoint_fixup in a fixed CTA order.
 template <int D, int P>
-__global__ void __launch_bounds__(kTilePix / P) k_adjoint(const AdjParams p) {
+__global__ void ASH_BOUNDS(P) k_adjoint(const AdjParams p) {
   constexpr int NT = kTilePix / P;
   constexpr int RS = NT / 32;
   constexpr int CPS = cpair_stride(D);
@@ -242,79 +263,78 @@ __global__ void __launch_bounds__(kTilePix / P) k_adjoint(const AdjParams p) {
   const Geometry& G = p.g;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int N = G.N;
-  const int tile = blockIdx.x;
+  const long long u0 = p.sched.begin(blockIdx.x), u1 = p.sched.begin(blockIdx.x + 1);
+  const int tf = (int)(u0 / N), tl = (int)((u1 - 1) / N);
 
-  float2 dz[P / 2][D];
-  load_dz<D, P>(p.dz, tile, t, dz);
-  float2 re2[P / 2], im2[P / 2];
+  for (int tile = tf; tile <= tl; ++tile) {
+    const int sb = (tile == tf) ? (int)(u0 - (long long)tile * N) : 0;
+    const int se = (tile == tl) ? (int)(u1 - (long long)tile * N) : N;
+    float2 dz[P / 2][D];
+    load_dz<D, P>(p.dz, tile, t, dz);
+    float2 re2[P / 2], im2[P / 2];
 #pragma unroll
-  for (int q = 0; q < P / 2; ++q) {
-    re2[q] = make_float2(0.0f, 0.0f);
-    im2[q] = make_float2(0.0f, 0.0f);
-  }
-
-  const float2* anc = p.anchors + (size_t)tile * D;
-  for (int n0 = 0; n0 < N; n0 += kSpotChunk) {
-    const int nc = min(kSpotChunk, N - n0);
-    __syncthreads();
-    for (int s = t; s < nc; s += NT) {
-      const float bt = stage_spot<D>(p.coeff, anc, n0 + s, sC + s * CPS);
-      const float2 r = cis_turns(bt);
-      const float2 y = __ldg(p.y + n0 + s);
-      const float yr = y.x * r.x - y.y * r.y;
-      const float yi = y.x * r.y + y.y * r.x;
-      sY[2 * s] = make_float4(yr, yr, yi, yi);
-      sY[2 * s + 1] = make_float4(-yi, -yi, 0.0f, 0.0f);
+    for (int q = 0; q < P / 2; ++q) {
+      re2[q] = make_float2(0.0f, 0.0f);
+      im2[q] = make_float2(0.0f, 0.0f);
     }
-    __syncthreads();
+    const float2* anc = p.anchors + (size_t)tile * D;
+    for (int n0 = sb; n0 < se; n0 += kSpotChunk) {
+      const int nc = min(kSpotChunk, se - n0);
+      __syncthreads();
+      for (int s = t; s < nc; s += NT) {
+        const float bt = stage_spot<D>(p.coeff, anc, n0 + s, sC + s * CPS);
+        const float2 r = cis_turns(bt);
+        const float2 y = __ldg(p.y + n0 + s);
+        const float yr = y.x * r.x - y.y * r.y;
+        const float yi = y.x * r.y + y.y * r.x;
+        sY[2 * s] = make_float4(yr, yr, yi, yi);
+        sY[2 * s + 1] = make_float4(-yi, -yi, 0.0f, 0.0f);
+      }
+      __syncthreads();
 
 #pragma unroll 2
-    for (int s = 0; s < nc; ++s) {
-      float2 cc[D];
-      load_cpairs<D>(sC + s * CPS, cc);
-      const float4 ya = sY[2 * s];
-      const float4 yb = sY[2 * s + 1];
-      const float2 yr2 = make_float2(ya.x, ya.y);
-      const float2 yi2 = make_float2(ya.z, ya.w);
-      const float2 nyi2 = make_float2(yb.x, yb.y);
+      for (int s = 0; s < nc; ++s) {
+        float2 cc[D];
+        load_cpairs<D>(sC + s * CPS, cc);
+        const float4 ya = sY[2 * s];
+        const float4 yb = sY[2 * s + 1];
+        const float2 yr2 = make_float2(ya.x, ya.y);
+        const float2 yi2 = make_float2(ya.z, ya.w);
+        const float2 nyi2 = make_float2(yb.x, yb.y);
 #pragma unroll
-      for (int q = 0; q < P / 2; ++q) {
-        const float2 x = local_phase<D>(cc, dz[q]);
-        float2 sn, cs;
-        sincos2(x, sn, cs);
-        re2[q] = fma2(yr2, cs, re2[q]);
-        re2[q] = fma2(nyi2, sn, re2[q]);
-        im2[q] = fma2(yi2, cs, im2[q]);
-        im2[q] = fma2(yr2, sn, im2[q]);
+        for (int q = 0; q < P / 2; ++q) {
+          const float2 x = local_phase<D>(cc, dz[q]);
+          float2 sn, cs;
+          sincos2(x, sn, cs);
+          re2[q] = fma2(yr2, cs, re2[q]);
+          re2[q] = fma2(nyi2, sn, re2[q]);
+          im2[q] = fma2(yi2, cs, im2[q]);
+          im2[q] = fma2(yr2, sn, im2[q]);
+        }
       }
     }
-  }
 
-  const int tx = tile % G.tiles_x, ty = tile / G.tiles_x;
-  const int i = tx * kTileX + lane;
-  float a[P];
-  if (p.epilogue & kEpiGradPhase) {
-    const float4* asrc = reinterpret_cast<const float4*>(p.amp_img + ((size_t)tile * NT + t) * P);
+    if (sb == 0 && se == N) {
+      const int tx = tile % G.tiles_x, ty = tile / G.tiles_x;
+      const int i = tx * kTileX + lane;
+      const float* aimg = p.amp_img + ((size_t)tile * NT + t) * P;
 #pragma unroll
-    for (int q = 0; q < P / 4; ++q) {
-      const float4 v = __ldg(asrc + q);
-      a[4 * q] = v.x; a[4 * q + 1] = v.y; a[4 * q + 2] = v.z; a[4 * q + 3] = v.w;
-    }
-  }
+      for (int k = 0; k < P; ++k) {
+        const int j = ty * kTileY + w + RS * k;
+        if (i >= G.nx || j >= G.ny) continue;
+        const float gr = (k & 1) ? re2[k >> 1].y : re2[k >> 1].x;
+        const float gi = (k & 1) ? im2[k >> 1].y : im2[k >> 1].x;
+        const float a = (p.epilogue & kEpiGradPhase) ? __ldg(aimg + k) : 0.0f;
+        adjoint_epilogue(p, (size_t)j * G.nx + i, gr, gi, a);
+      }
+    } else {
+      float2* dst = p.split + ((size_t)blockIdx.x * 2 + (tile == tf ? 0 : 1)) * kTilePix;
 #pragma unroll
-  for (int k = 0; k < P; ++k) {
-    const int j = ty * kTileY + w + RS * k;
-    if (i >= G.nx || j >= G.ny) continue;
-    const size_t m = (size_t)j * G.nx + i;
-    const float gr = (k & 1) ? re2[k >> 1].y : re2[k >> 1].x;
-    const float gi = (k & 1) ? im2[k >> 1].y : im2[k >> 1].x;
-    if (p.epilogue & kEpiField) p.g_out[m] = make_float2(gr, gi);
-    if (p.epilogue & kEpiPhase) p.phase_out[m] = (gr == 0.0f && gi == 0.0f) ? 0.0f : atan2f(gi, gr);
-    if (p.epilogue & kEpiGradPhase) {
-      float s, c;
-      sincosf(__ldg(p.phase_in + m), &s, &c);
-      const float fr = a[k] * c, fi = a[k] * s;
-      p.dphase[m] = fr * gi - fi * gr;   // -Im(f conj(h))
+      for (int k = 0; k < P; ++k) {
+        const float gr = (k & 1) ? re2[k >> 1].y : re2[k >> 1].x;
+        const float gi = (k & 1) ? im2[k >> 1].y : im2[k >> 1].x;
+        dst[k * NT + t] = make_float2(gr, gi);
+      }
     }
   }
 }

@@ -64,6 +64,7 @@ class Hologram:
         if basis is not None:
             _need(basis, torch.float32, (self.D, self.ny, self.nx), "basis")
         self.noll = noll
+        self._coeff = coeff.detach().clone()
         st = self._lib.ash_hologram_create(ctypes.byref(self._h), self.nx, self.ny, _ptr(amp), self.D,
                                            noll_arr, _ptr(basis), self.N, _ptr(coeff), _stream_ptr(stream))
         _lib.check(st, "ash_hologram_create")
@@ -98,6 +99,12 @@ class Hologram:
     def set_coefficients(self, coeff: torch.Tensor, stream=None):
         _need(coeff, torch.float32, (self.N, self.D), "coeff")
         _lib.check(self._lib.ash_set_coefficients(self._h, _ptr(coeff), _stream_ptr(stream)), "ash_set_coefficients")
+        if coeff.data_ptr() != self._coeff.data_ptr():
+            self._coeff.copy_(coeff.detach())
+
+    def coefficients(self) -> torch.Tensor:
+        """The coefficient matrix the handle currently holds (N, D)."""
+        return self._coeff
 
     def set_amplitude(self, amp: torch.Tensor, stream=None):
         _need(amp, torch.float32, (self.ny, self.nx), "amp")
