@@ -235,6 +235,71 @@ ash_status ash_profile(ash_hologram *h, const float *phase, const float *y, floa
  */
 ash_status ash_hologram_check(ash_hologram *h, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Batched uneven form: many holograms (different grids, spot counts and
+ * mode counts) solved together. Each phase of a WGS iteration (forward,
+ * reduction, spot update, adjoint, fix-up) is ONE launch over the work units
+ * (hologram, tile, spot) of all holograms, cut into equal contiguous ranges
+ * per CTA; the whole loop is one CUDA graph. Not in the paper (which solves
+ * one hologram at a time); results equal the per-hologram path's up to fp32
+ * summation order.
+ */
+typedef struct ash_batch ash_batch;
+
+/* One hologram of a batch: same meaning as the ash_hologram_create
+ * arguments; 1 <= D <= 12. */
+typedef struct {
+  int nx, ny;
+  const float *amp;     /* device float[ny*nx] */
+  int D;
+  const int *noll;      /* host int[D] or NULL */
+  const float *basis;   /* device float[D*ny*nx] or NULL */
+  int N;
+  const float *coeff;   /* device float[N*D] */
+} ash_hologram_desc;
+
+/* Create a batch of `count` holograms (descs: host array). Allocates one
+ * handle workspace per hologram plus the batch's descriptor table and split
+ * scratch; synchronises `stream`. ASH_ERR_UNSUPPORTED if some D > 12. */
+ash_status ash_batch_create(ash_batch **out, int count, const ash_hologram_desc *descs, void *stream);
+
+/* Destroy (synchronises the device first); NULL is ignored. */
+void ash_batch_destroy(ash_batch *b);
+
+/* count, CTAs per transform launch, resident CTAs of the device, and the
+ * total number of (hologram, tile, spot) work units; outputs may be NULL. */
+ash_status ash_batch_info(const ash_batch *b, int *count, int *grid, int *resident_ctas, long long *units);
+
+/* Override the CTA count of the transform launches (clamped to
+ * [1, 4 x resident CTAs]); invalidates captured graphs. */
+ash_status ash_batch_set_grid(ash_batch *b, int grid);
+
+/* Kernel launches one ash_batch_wgs call enqueues for `iters`; -1 if NULL. */
+int ash_batch_wgs_launches(const ash_batch *b, int iters);
+
+/*
+ * Weighted GS on every hologram of the batch (same rule as
+ * ash_wgs_iterate), in place on phases[i] / weights[i]:
+ *   phases, weights, targets  host arrays of `count` device pointers
+ *                             (float[ny_i*nx_i], float[N_i], float[N_i]).
+ *   metrics_out  device float[4*count] or NULL ({uniformity, efficiency,
+ *                sum |E|^2, min I^} per hologram).
+ * The loop runs as one CUDA graph per iteration count (captured on first use).
+ */
+ash_status ash_batch_wgs(ash_batch *b, float *const *phases, float *const *weights, const float *const *targets,
+                         int iters, float *metrics_out, void *stream);
+
+/*
+ * Autotuner of the launch shape: times one batched forward + adjoint for
+ * CTA counts of 0.5x .. 4x the resident CTAs on the given phases, keeps the
+ * fastest, and appends "key grid" to the text file cache_path (NULL: no
+ * cache). A cache line with this batch's key (device SM count and the
+ * hologram shapes) is used without timing. grid_out (host, may be NULL)
+ * receives the chosen CTA count. Synchronises `stream`.
+ */
+ash_status ash_batch_tune(ash_batch *b, const float *const *phases, const char *cache_path, int *grid_out,
+                          void *stream);
+
 /*
  * Allocation-free forward transform. The paper has no counterpart: this is
  * an interface for callers that cannot allocate device memory -- a host

@@ -7,7 +7,7 @@ Hologram does, and fails loudly if it is missing.
 """
 from __future__ import annotations
 
-__all__ = ["Hologram", "build", "load_library"]
+__all__ = ["Hologram", "Batch", "build", "load_library"]
 
 
 def load_library():
@@ -24,6 +24,9 @@ def __getattr__(name):
     if name == "Hologram":
         from .hologram import Hologram
         return Hologram
+    if name == "Batch":
+        from .hologram import Batch
+        return Batch
     if name == "autograd":
         from . import autograd
         return autograd

@@ -39,9 +39,24 @@ SIGNATURES = {
     "ash_hologram_check": (c_int, [c_void_p, c_void_p]),
     "ash_wgs_launches": (c_int, [c_void_p, c_int]),
     "ash_profile": (c_int, [c_void_p, c_void_p, c_void_p, c_float_p, c_void_p]),
+    "ash_batch_create": (c_int, [ctypes.POINTER(c_void_p), c_int, c_void_p, c_void_p]),
+    "ash_batch_destroy": (None, [c_void_p]),
+    "ash_batch_info": (c_int, [c_void_p, c_int_p, c_int_p, c_int_p, ctypes.POINTER(ctypes.c_longlong)]),
+    "ash_batch_set_grid": (c_int, [c_void_p, c_int]),
+    "ash_batch_wgs_launches": (c_int, [c_void_p, c_int]),
+    "ash_batch_wgs": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p]),
+    "ash_batch_tune": (c_int, [c_void_p, c_void_p, ctypes.c_char_p, c_int_p, c_void_p]),
     "ash_forward_noalloc": (c_int, [c_int, c_int, c_void_p, c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p,
                                     c_void_p]),
 }
+
+
+
+class HologramDesc(ctypes.Structure):
+    """ash_hologram_desc (include/ash.h)."""
+    _fields_ = [("nx", c_int), ("ny", c_int), ("amp", c_void_p), ("D", c_int), ("noll", c_int_p),
+                ("basis", c_void_p), ("N", c_int), ("coeff", c_void_p)]
+
 
 _lib = None
 

@@ -11,6 +11,7 @@
 #include "ash.h"
 #include "aux_kernels.cuh"
 #include "basis_host.h"
+#include "handle.h"
 #include "launch.h"
 
 using namespace ash;
@@ -60,41 +61,10 @@ cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 namespace ash {
 // Lets other translation units report through ash_last_error().
 void record_error(const char* msg) { g_last_error = msg; }
+ash_status status_cuda(cudaError_t e, const char* where) { return cuda_fail(e, where); }
+bool consume_injected_failure() { return injected_failure(); }
 }  // namespace ash
 
-struct ash_hologram {
-  Geometry g{};
-  int device = 0;
-  cudaStream_t home = nullptr;     // stream the workspace was allocated on
-  LaunchInfo li{};
-  Schedule sched{};           // (tile, spot) ranges of the transform kernels
-  bool split_tiles = false;   // some tile's spots span two CTA ranges
-  int fwd_rows = 0;
-  int gradc_gx = 0, gradc_gy = 0;
-  // workspace
-  float* dz = nullptr;
-  float* amp_img = nullptr;
-  float2* anchors = nullptr;
-  float* coeff = nullptr;
-  float* partial = nullptr;
-  float2* split = nullptr;
-  float* gradc_partial = nullptr;
-  float2* E = nullptr;
-  float2* y = nullptr;
-  float* wgs_phase = nullptr;
-  float* wgs_w = nullptr;
-  float* wgs_T = nullptr;
-  float2* wgs_E = nullptr;
-  float* wgs_metrics = nullptr;
-  double* sum_a2 = nullptr;
-  MonoTerm* terms = nullptr;
-  int* term_off = nullptr;
-  unsigned* err_word = nullptr;
-  std::vector<void*> allocs;
-  size_t bytes = 0;
-  cudaStream_t capture = nullptr;
-  std::map<int, cudaGraphExec_t> graphs;
-};
 
 namespace {
 
@@ -178,11 +148,7 @@ cudaError_t launch_gradc(int D, const GradCParams& p, dim3 grid, cudaStream_t s)
 ash_status enqueue_forward(ash_hologram* h, int source, const float* phase, const float2* field, float2* E,
                            cudaStream_t s) {
   FwdParams p{};
-  p.g = h->g;
-  p.dz = h->dz;
-  p.amp_img = h->amp_img;
-  p.anchors = h->anchors;
-  p.coeff = h->coeff;
+  p.v = view_of(h);
   p.phase = phase;
   p.field = field;
   p.source = source;
@@ -200,17 +166,13 @@ ash_status enqueue_forward(ash_hologram* h, int source, const float* phase, cons
 ash_status enqueue_adjoint(ash_hologram* h, const float2* y, float2* g_out, float* phase_out, const float* phase_in,
                            float* dphase, int epilogue, cudaStream_t s) {
   AdjParams p{};
-  p.g = h->g;
-  p.dz = h->dz;
-  p.amp_img = h->amp_img;
-  p.anchors = h->anchors;
-  p.coeff = h->coeff;
+  p.v = view_of(h);
   p.y = y;
-  p.g_out = g_out;
-  p.phase_out = phase_out;
-  p.phase_in = phase_in;
-  p.dphase = dphase;
-  p.epilogue = epilogue;
+  p.out.g_out = g_out;
+  p.out.phase_out = phase_out;
+  p.out.phase_in = phase_in;
+  p.out.dphase = dphase;
+  p.out.epilogue = epilogue;
   p.sched = h->sched;
   p.split = h->split;
   cudaError_t e = launch_adjoint(h->g.D, p, h->sched.G, s);
@@ -536,11 +498,7 @@ ash_status ash_grad(ash_hologram* h, const float* phase, const float* grad_E, fl
   }
   if (dcoeff) {
     GradCParams p{};
-    p.g = h->g;
-    p.dz = h->dz;
-    p.amp_img = h->amp_img;
-    p.anchors = h->anchors;
-    p.coeff = h->coeff;
+    p.v = view_of(h);
     p.phase = phase;
     p.gradE = gE;
     p.partial = h->gradc_partial;
@@ -572,12 +530,8 @@ ash_status ash_profile(ash_hologram* h, const float* phase, const float* y, floa
   cudaError_t e = cudaSuccess;
   // forward kernel, then its reduction
   FwdParams fp{};
-  fp.g = h->g;
+  fp.v = view_of(h);
   fp.sched = h->sched;
-  fp.dz = h->dz;
-  fp.amp_img = h->amp_img;
-  fp.anchors = h->anchors;
-  fp.coeff = h->coeff;
   fp.phase = phase;
   fp.source = kSrcPhase;
   fp.partial = h->partial;
@@ -594,16 +548,12 @@ ash_status ash_profile(ash_hologram* h, const float* phase, const float* y, floa
   }
   // adjoint kernel (phase epilogue), then the fix-up
   AdjParams ap{};
-  ap.g = h->g;
+  ap.v = view_of(h);
   ap.sched = h->sched;
   ap.split = h->split;
-  ap.dz = h->dz;
-  ap.amp_img = h->amp_img;
-  ap.anchors = h->anchors;
-  ap.coeff = h->coeff;
   ap.y = y2;
-  ap.phase_out = h->wgs_phase;
-  ap.epilogue = kEpiPhase;
+  ap.out.phase_out = h->wgs_phase;
+  ap.out.epilogue = kEpiPhase;
   if (e == cudaSuccess) {
     cudaEventRecord(ev[4], s);
     e = launch_adjoint(h->g.D, ap, h->sched.G, s);
@@ -625,11 +575,7 @@ ash_status ash_profile(ash_hologram* h, const float* phase, const float* y, floa
   }
   if (e == cudaSuccess) {
     GradCParams gp{};
-    gp.g = h->g;
-    gp.dz = h->dz;
-    gp.amp_img = h->amp_img;
-    gp.anchors = h->anchors;
-    gp.coeff = h->coeff;
+    gp.v = view_of(h);
     gp.phase = phase;
     gp.gradE = y2;
     gp.partial = h->gradc_partial;

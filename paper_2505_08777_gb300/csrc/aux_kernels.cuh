@@ -1,5 +1,8 @@
 // Set-up and N-length kernels: basis materialisation, layout conversion,
 // deterministic column reductions, the weighted-GS spot update and metrics.
+// Kernels have internal linkage (static) so the header can serve several
+// translation units; the *_body device functions are shared with the
+// batched kernels.
 #pragma once
 
 #include "common.cuh"
@@ -36,7 +39,7 @@ __device__ inline double eval_mono(const MonoTerm* __restrict__ terms, int b, in
 constexpr int kMaxOrder = 24;
 
 // One CTA per tile, NT threads; thread t fills its P pixels x D modes.
-__global__ void k_basis(const BasisParams p) {
+static __global__ void k_basis(const BasisParams p) {
   const Geometry& G = p.g;
   const int tile = blockIdx.x, t = threadIdx.x;
   const int P = G.P, NT = G.NT, D = G.D;
@@ -99,7 +102,7 @@ __global__ void k_basis(const BasisParams p) {
 }
 
 // Amplitude into the register-image layout (zero outside the grid).
-__global__ void k_amp_image(Geometry G, const float* __restrict__ amp, float* __restrict__ img) {
+static __global__ void k_amp_image(Geometry G, const float* __restrict__ amp, float* __restrict__ img) {
   const int tile = blockIdx.x, t = threadIdx.x;
   const int tx = tile % G.tiles_x, ty = tile / G.tiles_x;
   const int lane = t & 31, w = t >> 5;
@@ -125,7 +128,7 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 }
 
 // sum_m A_m^2 in fp64 (one block).
-__global__ void k_sum_sq(const float* __restrict__ a, size_t M, double* out) {
+static __global__ void k_sum_sq(const float* __restrict__ a, size_t M, double* out) {
   __shared__ double red[32];
   double s = 0.0;
   for (size_t m = threadIdx.x; m < M; m += blockDim.x) s += (double)a[m] * (double)a[m];
@@ -135,9 +138,10 @@ __global__ void k_sum_sq(const float* __restrict__ a, size_t M, double* out) {
 
 // out[c] = sum_r in[r][c] (r in fixed order). Block (32, 32): 32 columns,
 // 32 row lanes; smem tree over the row lanes.
-__global__ void k_col_reduce(const float* __restrict__ in, int rows, int cols, float* __restrict__ out) {
+__device__ __forceinline__ void col_reduce_body(const float* __restrict__ in, int rows, int cols,
+                                                float* __restrict__ out, int bx) {
   __shared__ float red[32][33];
-  const int c = blockIdx.x * 32 + threadIdx.x;
+  const int c = bx * 32 + threadIdx.x;
   float s = 0.0f;
   if (c < cols) {
     for (int r = threadIdx.y; r < rows; r += 32) s += in[(size_t)r * cols + c];
@@ -172,8 +176,8 @@ __device__ __forceinline__ float block_sum_f(float v, float* red) {
 //   y = w exp(i arg E) (arg 0 -> 0).
 // The norms only fix a global scale of w (removed by the renormalisation,
 // and arg g is invariant to it), so fp32 sums are sufficient.
-__global__ void __launch_bounds__(1024) k_wgs_update(const float2* __restrict__ E, float* __restrict__ w,
-                                                     const float* __restrict__ T, float2* __restrict__ y, int N) {
+__device__ __forceinline__ void wgs_update_body(const float2* __restrict__ E, float* __restrict__ w,
+                                                const float* __restrict__ T, float2* __restrict__ y, int N) {
   __shared__ float red[32];
   float se = 0.0f, st = 0.0f;
   for (int n = threadIdx.x; n < N; n += 1024) {
@@ -204,37 +208,35 @@ __global__ void __launch_bounds__(1024) k_wgs_update(const float2* __restrict__ 
   }
 }
 
-// Finishes tiles whose spot range was split between CTAs of k_adjoint: sums
-// the CTAs' partial fields in CTA order and applies the epilogue. One CTA of
-// G.NT threads per tile; tiles owned by a single CTA return at once.
-__global__ void k_adjoint_fixup(const AdjParams p) {
-  const Geometry& G = p.g;
-  const int tile = blockIdx.x, t = threadIdx.x;
-  const long long u_lo = (long long)tile * G.N, u_hi = u_lo + G.N - 1;
-  const int b_lo = p.sched.owner(u_lo), b_hi = p.sched.owner(u_hi);
-  if (b_lo == b_hi) return;
+// Finishes a tile whose spot range (units [u_lo, u_lo + N)) was split
+// between CTAs b_lo..b_hi of an adjoint launch: sums their partial fields in
+// CTA order and applies the epilogue. slot 0 holds a CTA's first tile.
+__device__ __forceinline__ void fixup_tile_body(const HoloView& v, const AdjOut& out, const float2* __restrict__ split,
+                                                const Schedule& sched, int tile, long long u_lo, int b_lo, int b_hi) {
+  const Geometry& G = v.g;
+  const int t = threadIdx.x;
   const int P = G.P, NT = G.NT;
   const int tx = tile % G.tiles_x, ty = tile / G.tiles_x;
   const int i = tx * kTileX + (t & 31);
   for (int k = 0; k < P; ++k) {
     float gr = 0.0f, gi = 0.0f;
     for (int b = b_lo; b <= b_hi; ++b) {
-      const int slot = (p.sched.begin(b) / G.N == tile) ? 0 : 1;
-      const float2 v = p.split[((size_t)b * 2 + slot) * kTilePix + (size_t)k * NT + t];
-      gr += v.x;
-      gi += v.y;
+      const int slot = (sched.begin(b) >= u_lo) ? 0 : 1;
+      const float2 val = split[((size_t)b * 2 + slot) * kTilePix + (size_t)k * NT + t];
+      gr += val.x;
+      gi += val.y;
     }
     const int j = ty * kTileY + (t >> 5) + (NT / 32) * k;
     if (i >= G.nx || j >= G.ny) continue;
-    const float a = (p.epilogue & kEpiGradPhase) ? p.amp_img[((size_t)tile * NT + t) * P + k] : 0.0f;
-    adjoint_epilogue(p, (size_t)j * G.nx + i, gr, gi, a);
+    const float a = (out.epilogue & kEpiGradPhase) ? v.amp_img[((size_t)tile * NT + t) * P + k] : 0.0f;
+    adjoint_epilogue(out, (size_t)j * G.nx + i, gr, gi, a);
   }
 }
 
 // metrics = {uniformity, efficiency, sum |E|^2, min I^} (one block).
-__global__ void __launch_bounds__(1024) k_metrics(const float2* __restrict__ E, const float* __restrict__ T, int N,
-                                                  const double* __restrict__ sum_a2, double M,
-                                                  float* __restrict__ metrics) {
+__device__ __forceinline__ void metrics_body(const float2* __restrict__ E, const float* __restrict__ T, int N,
+                                             const double* __restrict__ sum_a2, double M,
+                                             float* __restrict__ metrics) {
   __shared__ double red[32];
   __shared__ float rmin[32], rmax[32];
   double se = 0.0;
@@ -270,6 +272,33 @@ __global__ void __launch_bounds__(1024) k_metrics(const float2* __restrict__ E, 
     metrics[2] = (float)se;
     metrics[3] = lo;
   }
+}
+
+// ---------------------------------------------------------------------------
+// Single-hologram wrappers.
+
+static __global__ void k_col_reduce(const float* __restrict__ in, int rows, int cols, float* __restrict__ out) {
+  col_reduce_body(in, rows, cols, out, blockIdx.x);
+}
+
+static __global__ void __launch_bounds__(1024) k_wgs_update(const float2* __restrict__ E, float* __restrict__ w,
+                                                            const float* __restrict__ T, float2* __restrict__ y,
+                                                            int N) {
+  wgs_update_body(E, w, T, y, N);
+}
+
+static __global__ void __launch_bounds__(1024) k_metrics(const float2* __restrict__ E, const float* __restrict__ T,
+                                                         int N, const double* __restrict__ sum_a2, double M,
+                                                         float* __restrict__ metrics) {
+  metrics_body(E, T, N, sum_a2, M, metrics);
+}
+
+// One CTA of G.NT threads per tile; tiles owned by a single CTA return at once.
+static __global__ void k_adjoint_fixup(const AdjParams p) {
+  const long long u_lo = (long long)blockIdx.x * p.v.g.N, u_hi = u_lo + p.v.g.N - 1;
+  const int b_lo = p.sched.owner(u_lo), b_hi = p.sched.owner(u_hi);
+  if (b_lo == b_hi) return;
+  fixup_tile_body(p.v, p.out, p.split, p.sched, blockIdx.x, u_lo, b_lo, b_hi);
 }
 
 }  // namespace ash

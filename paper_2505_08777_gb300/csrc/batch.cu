@@ -1,0 +1,511 @@
+// Batched uneven form: many holograms of different grid sizes, spot counts
+// and mode counts solved together, one persistent launch per phase of the
+// weighted-GS iteration, the whole loop captured in one CUDA graph.
+//
+// Work units are (hologram, tile, spot) triples, hologram-major then
+// tile-major; the G CTAs of a launch get equal contiguous ranges of the
+// global unit sequence, so small and large holograms share the GPU without
+// tail effects. Each tile is dispatched on its hologram's D to the same
+// specialised tile code the single-hologram kernels use. Tiles split between
+// CTAs are finished by a fix-up pass in a fixed CTA order (deterministic).
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "aux_kernels.cuh"
+#include "handle.h"
+#include "transform_kernels.cuh"
+
+namespace {
+
+using namespace ash;
+
+constexpr int kBatchP = 8;                 // pixels per thread (D <= 12)
+constexpr int kBatchNT = kTilePix / kBatchP;
+constexpr int kBatchNW = kBatchNT / 32;
+constexpr int kBatchMaxD = 12;
+constexpr int kGridFactorMax = 4;          // split scratch sized for 4x the resident CTAs
+
+struct BatchHolo {
+  HoloView v;
+  long long unit0;       // first global work unit
+  int tile0;             // first global tile
+  float* partial;        // forward partial rows [T * NW][2N]
+  float2* E;
+  float2* y;
+  float* w;
+  const float* T;
+  float* phase;
+  float* metrics;
+  const double* sum_a2;
+};
+
+struct BatchParams {
+  const BatchHolo* holos;
+  int count;
+  Schedule sched;
+  float2* split;
+};
+
+__device__ __forceinline__ int holo_of_unit(const BatchHolo* __restrict__ hs, int count, long long u) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (hs[mid].unit0 <= u) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int holo_of_tile(const BatchHolo* __restrict__ hs, int count, int gt) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (hs[mid].tile0 <= gt) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+constexpr size_t batch_fwd_smem() { return fwd_smem_bytes(kBatchMaxD); }
+constexpr size_t batch_adj_smem() { return adj_smem_bytes(kBatchMaxD); }
+
+#define ASH_D_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12)
+
+__global__ void ASH_BOUNDS(kBatchP) k_batch_forward(const BatchParams bp) {
+  constexpr int P = kBatchP;
+  extern __shared__ float4 smem4[];
+  float* sC = reinterpret_cast<float*>(smem4);
+  float2* sRot = reinterpret_cast<float2*>(sC + kSpotChunk * cpair_stride(kBatchMaxD));
+  const long long u0 = bp.sched.begin(blockIdx.x), u1 = bp.sched.begin(blockIdx.x + 1);
+  long long u = u0;
+  while (u < u1) {
+    const BatchHolo* H = bp.holos + holo_of_unit(bp.holos, bp.count, u);
+    const HoloView v = H->v;
+    const int N = v.g.N;
+    const int tile = (int)((u - H->unit0) / N);
+    const long long ts = H->unit0 + (long long)tile * N;
+    const long long ue = min(u1, ts + N);
+    const int sb = (int)(u - ts), se = (int)(ue - ts);
+    float* ptile = H->partial + (size_t)tile * kBatchNW * 2 * N;
+    switch (v.g.D) {
+#define FWD_CASE(DD) \
+  case DD: forward_tile<DD, P>(v, kSrcPhase, H->phase, nullptr, tile, sb, se, ptile, sC, sRot); break;
+      ASH_D_CASES(FWD_CASE)
+#undef FWD_CASE
+      default: break;
+    }
+    u = ue;
+  }
+}
+
+__global__ void ASH_BOUNDS(kBatchP) k_batch_adjoint(const BatchParams bp) {
+  constexpr int P = kBatchP;
+  extern __shared__ float4 smem4[];
+  float* sC = reinterpret_cast<float*>(smem4);
+  float4* sY = reinterpret_cast<float4*>(sC + kSpotChunk * cpair_stride(kBatchMaxD));
+  const long long u0 = bp.sched.begin(blockIdx.x), u1 = bp.sched.begin(blockIdx.x + 1);
+  long long u = u0;
+  while (u < u1) {
+    const BatchHolo* H = bp.holos + holo_of_unit(bp.holos, bp.count, u);
+    const HoloView v = H->v;
+    const int N = v.g.N;
+    const int tile = (int)((u - H->unit0) / N);
+    const long long ts = H->unit0 + (long long)tile * N;
+    const long long ue = min(u1, ts + N);
+    const int sb = (int)(u - ts), se = (int)(ue - ts);
+    AdjOut out{};
+    out.phase_out = H->phase;
+    out.epilogue = kEpiPhase;
+    float2* slot = bp.split + ((size_t)blockIdx.x * 2 + (u == u0 ? 0 : 1)) * kTilePix;
+    float2 re2[P / 2], im2[P / 2];
+    switch (v.g.D) {
+#define ADJ_CASE(DD) \
+  case DD: adjoint_tile<DD, P>(v, H->y, tile, sb, se, re2, im2, sC, sY); break;
+      ASH_D_CASES(ADJ_CASE)
+#undef ADJ_CASE
+      default:
+#pragma unroll
+        for (int q = 0; q < P / 2; ++q) re2[q] = im2[q] = make_float2(0.0f, 0.0f);
+        break;
+    }
+    adjoint_finish<P>(v, out, tile, sb == 0 && se == N, slot, re2, im2);
+    u = ue;
+  }
+}
+
+// One CTA per global tile; tiles owned by a single CTA return at once.
+__global__ void k_batch_fixup(const BatchParams bp) {
+  const BatchHolo* H = bp.holos + holo_of_tile(bp.holos, bp.count, blockIdx.x);
+  const int tile = blockIdx.x - H->tile0;
+  const int N = H->v.g.N;
+  const long long u_lo = H->unit0 + (long long)tile * N, u_hi = u_lo + N - 1;
+  const int b_lo = bp.sched.owner(u_lo), b_hi = bp.sched.owner(u_hi);
+  if (b_lo == b_hi) return;
+  AdjOut out{};
+  out.phase_out = H->phase;
+  out.epilogue = kEpiPhase;
+  fixup_tile_body(H->v, out, bp.split, bp.sched, tile, u_lo, b_lo, b_hi);
+}
+
+// grid (max columns / 32, count), block (32, 32)
+__global__ void k_batch_reduce(const BatchParams bp) {
+  const BatchHolo* H = bp.holos + blockIdx.y;
+  const int cols = 2 * H->v.g.N;
+  if ((int)blockIdx.x * 32 >= cols) return;
+  col_reduce_body(H->partial, H->v.g.T * kBatchNW, cols, reinterpret_cast<float*>(H->E), blockIdx.x);
+}
+
+__global__ void __launch_bounds__(1024) k_batch_update(const BatchParams bp) {
+  const BatchHolo* H = bp.holos + blockIdx.x;
+  wgs_update_body(H->E, H->w, H->T, H->y, H->v.g.N);
+}
+
+__global__ void __launch_bounds__(1024) k_batch_metrics(const BatchParams bp) {
+  const BatchHolo* H = bp.holos + blockIdx.x;
+  metrics_body(H->E, H->T, H->v.g.N, H->sum_a2, (double)H->v.g.nx * H->v.g.ny, H->metrics);
+}
+
+ash_status fail(ash_status st, const std::string& msg) {
+  record_error(msg.c_str());
+  return st;
+}
+
+#define BCUDA(call)                                            \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) return status_cuda(e_, #call);      \
+  } while (0)
+
+}  // namespace
+
+struct ash_batch {
+  int count = 0;
+  std::vector<ash_hologram*> holos;
+  std::vector<BatchHolo> host;
+  BatchHolo* dev = nullptr;
+  long long U = 0;
+  int total_tiles = 0;
+  int max_cols = 0;
+  int slots = 0;           // resident CTAs on the device
+  int G = 0;               // CTAs of the transform launches
+  bool split = false;
+  float2* split_buf = nullptr;
+  cudaStream_t capture = nullptr;
+  std::map<int, cudaGraphExec_t> graphs;
+  std::string key;         // autotuner cache key
+};
+
+namespace {
+
+void set_grid(ash_batch* b, int G) {
+  if (G < 1) G = 1;
+  if (G > kGridFactorMax * b->slots) G = kGridFactorMax * b->slots;
+  if ((long long)G > b->U) G = (int)b->U;
+  if (G != b->G) {
+    for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    b->graphs.clear();
+  }
+  b->G = G;
+  Schedule s{b->U, G};
+  b->split = false;
+  // a tile is split iff some CTA boundary falls inside it
+  for (int g = 1; g < G && !b->split; ++g) {
+    const long long u = s.begin(g);
+    for (const BatchHolo& h : b->host) {
+      const long long end = h.unit0 + (long long)h.v.g.T * h.v.g.N;
+      if (u >= h.unit0 && u < end) {
+        if ((u - h.unit0) % h.v.g.N != 0) b->split = true;
+        break;
+      }
+    }
+  }
+}
+
+BatchParams params_of(const ash_batch* b) {
+  BatchParams p{};
+  p.holos = b->dev;
+  p.count = b->count;
+  p.sched = Schedule{b->U, b->G};
+  p.split = b->split_buf;
+  return p;
+}
+
+ash_status enqueue_batch_forward(ash_batch* b, cudaStream_t s) {
+  const BatchParams p = params_of(b);
+  k_batch_forward<<<b->G, kBatchNT, batch_fwd_smem(), s>>>(p);
+  BCUDA(cudaGetLastError());
+  k_batch_reduce<<<dim3((b->max_cols + 31) / 32, b->count), dim3(32, 32), 0, s>>>(p);
+  BCUDA(cudaGetLastError());
+  return ASH_OK;
+}
+
+ash_status enqueue_batch_adjoint(ash_batch* b, cudaStream_t s) {
+  const BatchParams p = params_of(b);
+  k_batch_adjoint<<<b->G, kBatchNT, batch_adj_smem(), s>>>(p);
+  BCUDA(cudaGetLastError());
+  if (b->split) {
+    k_batch_fixup<<<b->total_tiles, kBatchNT, 0, s>>>(p);
+    BCUDA(cudaGetLastError());
+  }
+  return ASH_OK;
+}
+
+ash_status enqueue_batch_body(ash_batch* b, int iters, cudaStream_t s) {
+  const BatchParams p = params_of(b);
+  ash_status st;
+  for (int it = 0; it < iters; ++it) {
+    if ((st = enqueue_batch_forward(b, s)) != ASH_OK) return st;
+    k_batch_update<<<b->count, 1024, 0, s>>>(p);
+    BCUDA(cudaGetLastError());
+    if ((st = enqueue_batch_adjoint(b, s)) != ASH_OK) return st;
+  }
+  if ((st = enqueue_batch_forward(b, s)) != ASH_OK) return st;
+  k_batch_metrics<<<b->count, 1024, 0, s>>>(p);
+  BCUDA(cudaGetLastError());
+  return ASH_OK;
+}
+
+void destroy_batch(ash_batch* b) {
+  cudaDeviceSynchronize();
+  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  b->graphs.clear();
+  if (b->dev) cudaFree(b->dev);
+  if (b->split_buf) cudaFree(b->split_buf);
+  if (b->capture) cudaStreamDestroy(b->capture);
+  for (ash_hologram* h : b->holos) ash_hologram_destroy(h);
+  delete b;
+}
+
+std::string cache_lookup(const char* path, const std::string& key) {
+  if (!path) return "";
+  FILE* f = fopen(path, "r");
+  if (!f) return "";
+  char line[512];
+  std::string found;
+  while (fgets(line, sizeof line, f)) {
+    char k[400];
+    int g = 0;
+    if (sscanf(line, "%399s %d", k, &g) == 2 && key == k) found = std::to_string(g);
+  }
+  fclose(f);
+  return found;
+}
+
+void cache_store(const char* path, const std::string& key, int G) {
+  if (!path) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%s %d\n", key.c_str(), G);
+  fclose(f);
+}
+
+}  // namespace
+
+extern "C" {
+
+ash_status ash_batch_create(ash_batch** out, int count, const ash_hologram_desc* descs, void* stream) {
+  if (!out) return fail(ASH_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (count < 1 || count > 65535 || !descs) return fail(ASH_ERR_INVALID_ARG, "count outside [1, 65535] or NULL descs");
+  for (int i = 0; i < count; ++i)
+    if (descs[i].D < 1 || descs[i].D > kBatchMaxD)
+      return fail(ASH_ERR_UNSUPPORTED, "batched holograms need 1 <= D <= 12 (hologram " + std::to_string(i) + ")");
+  if (consume_injected_failure()) return fail(ASH_ERR_INJECTED, "injected failure");
+  ash_batch* b = new ash_batch();
+  b->count = count;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  auto bail = [&](ash_status st) {
+    destroy_batch(b);
+    return st;
+  };
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  std::string key = "sm" + std::to_string(sms) + "_n" + std::to_string(count);
+  for (int i = 0; i < count; ++i) {
+    const ash_hologram_desc& d = descs[i];
+    ash_hologram* h = nullptr;
+    ash_status st = ash_hologram_create(&h, d.nx, d.ny, d.amp, d.D, d.noll, d.basis, d.N, d.coeff, stream);
+    if (st != ASH_OK) return bail(st);
+    b->holos.push_back(h);
+    BatchHolo bh{};
+    bh.v = view_of(h);
+    bh.unit0 = b->U;
+    bh.tile0 = b->total_tiles;
+    bh.partial = h->partial;
+    bh.E = h->wgs_E;
+    bh.y = h->y;
+    bh.w = h->wgs_w;
+    bh.T = h->wgs_T;
+    bh.phase = h->wgs_phase;
+    bh.metrics = h->wgs_metrics;
+    bh.sum_a2 = h->sum_a2;
+    b->host.push_back(bh);
+    b->U += (long long)h->g.T * h->g.N;
+    b->total_tiles += h->g.T;
+    if (2 * h->g.N > b->max_cols) b->max_cols = 2 * h->g.N;
+    key += "_" + std::to_string(d.nx) + "x" + std::to_string(d.ny) + "n" + std::to_string(d.N) + "d" +
+           std::to_string(d.D);
+    if (key.size() > 300) key = key.substr(0, 300);
+  }
+  b->key = key;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_batch_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_fwd_smem())) !=
+      cudaSuccess)
+    return bail(status_cuda(e, "batch forward attribute"));
+  if ((e = cudaFuncSetAttribute(k_batch_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_adj_smem())) !=
+      cudaSuccess)
+    return bail(status_cuda(e, "batch adjoint attribute"));
+  int occ_f = 0, occ_a = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, k_batch_forward, kBatchNT, batch_fwd_smem());
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, k_batch_adjoint, kBatchNT, batch_adj_smem());
+  int occ = occ_f < occ_a ? occ_f : occ_a;
+  if (occ < 1) occ = 1;
+  b->slots = sms * occ;
+  if ((e = cudaMalloc(&b->dev, sizeof(BatchHolo) * count)) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(ASH_ERR_OOM, "batch descriptor allocation"));
+  }
+  if ((e = cudaMalloc(&b->split_buf, sizeof(float2) * (size_t)kGridFactorMax * b->slots * 2 * kTilePix)) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(ASH_ERR_OOM, "batch split scratch allocation"));
+  }
+  if ((e = cudaMemcpyAsync(b->dev, b->host.data(), sizeof(BatchHolo) * count, cudaMemcpyHostToDevice, s)) !=
+      cudaSuccess)
+    return bail(status_cuda(e, "batch descriptor upload"));
+  if ((e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking)) != cudaSuccess)
+    return bail(status_cuda(e, "batch capture stream"));
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return bail(status_cuda(e, "batch set-up"));
+  set_grid(b, b->slots);
+  *out = b;
+  return ASH_OK;
+}
+
+void ash_batch_destroy(ash_batch* b) {
+  if (b) destroy_batch(b);
+}
+
+ash_status ash_batch_info(const ash_batch* b, int* count, int* grid, int* resident_ctas, long long* units) {
+  if (!b) return fail(ASH_ERR_INVALID_ARG, "batch is NULL");
+  if (count) *count = b->count;
+  if (grid) *grid = b->G;
+  if (resident_ctas) *resident_ctas = b->slots;
+  if (units) *units = b->U;
+  return ASH_OK;
+}
+
+ash_status ash_batch_set_grid(ash_batch* b, int grid) {
+  if (!b || grid < 1) return fail(ASH_ERR_INVALID_ARG, "NULL batch or grid < 1");
+  set_grid(b, grid);
+  return ASH_OK;
+}
+
+int ash_batch_wgs_launches(const ash_batch* b, int iters) {
+  if (!b || iters < 0) return -1;
+  const int fwd = 2, adj = b->split ? 2 : 1;
+  return iters * (fwd + 1 + adj) + fwd + 1;
+}
+
+ash_status ash_batch_wgs(ash_batch* b, float* const* phases, float* const* weights, const float* const* targets,
+                         int iters, float* metrics_out, void* stream) {
+  if (!b || !phases || !weights || !targets) return fail(ASH_ERR_INVALID_ARG, "NULL argument");
+  if (iters < 0 || iters > 1000000) return fail(ASH_ERR_INVALID_ARG, "iters outside [0, 1e6]");
+  for (int i = 0; i < b->count; ++i)
+    if (!phases[i] || !weights[i] || !targets[i]) return fail(ASH_ERR_INVALID_ARG, "NULL per-hologram buffer");
+  if (consume_injected_failure()) return fail(ASH_ERR_INJECTED, "injected failure");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  for (int i = 0; i < b->count; ++i) {
+    const ash_hologram* h = b->holos[i];
+    const size_t M = (size_t)h->g.nx * h->g.ny, N = (size_t)h->g.N;
+    BCUDA(cudaMemcpyAsync(h->wgs_phase, phases[i], M * 4, cudaMemcpyDeviceToDevice, s));
+    BCUDA(cudaMemcpyAsync(h->wgs_w, weights[i], N * 4, cudaMemcpyDeviceToDevice, s));
+    BCUDA(cudaMemcpyAsync(h->wgs_T, targets[i], N * 4, cudaMemcpyDeviceToDevice, s));
+  }
+  auto it = b->graphs.find(iters);
+  cudaGraphExec_t exec = nullptr;
+  if (it != b->graphs.end()) {
+    exec = it->second;
+  } else {
+    cudaGraph_t graph = nullptr;
+    BCUDA(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal));
+    ash_status st = enqueue_batch_body(b, iters, b->capture);
+    cudaError_t ce = cudaStreamEndCapture(b->capture, &graph);
+    if (st != ASH_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (ce != cudaSuccess) return status_cuda(ce, "batch cudaStreamEndCapture");
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return status_cuda(ce, "batch cudaGraphInstantiate");
+    b->graphs[iters] = exec;
+  }
+  BCUDA(cudaGraphLaunch(exec, s));
+  for (int i = 0; i < b->count; ++i) {
+    const ash_hologram* h = b->holos[i];
+    const size_t M = (size_t)h->g.nx * h->g.ny, N = (size_t)h->g.N;
+    BCUDA(cudaMemcpyAsync(phases[i], h->wgs_phase, M * 4, cudaMemcpyDeviceToDevice, s));
+    BCUDA(cudaMemcpyAsync(weights[i], h->wgs_w, N * 4, cudaMemcpyDeviceToDevice, s));
+    if (metrics_out)
+      BCUDA(cudaMemcpyAsync(metrics_out + 4 * i, h->wgs_metrics, 16, cudaMemcpyDeviceToDevice, s));
+  }
+  return ASH_OK;
+}
+
+ash_status ash_batch_tune(ash_batch* b, const float* const* phases, const char* cache_path, int* grid_out,
+                          void* stream) {
+  if (!b || !phases) return fail(ASH_ERR_INVALID_ARG, "NULL argument");
+  const std::string hit = cache_lookup(cache_path, b->key);
+  if (!hit.empty()) {
+    set_grid(b, std::stoi(hit));
+    if (grid_out) *grid_out = b->G;
+    return ASH_OK;
+  }
+  if (consume_injected_failure()) return fail(ASH_ERR_INJECTED, "injected failure");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  for (int i = 0; i < b->count; ++i) {
+    const ash_hologram* h = b->holos[i];
+    BCUDA(cudaMemcpyAsync(h->wgs_phase, phases[i], (size_t)h->g.nx * h->g.ny * 4, cudaMemcpyDeviceToDevice, s));
+    BCUDA(cudaMemsetAsync(h->y, 0, (size_t)h->g.N * sizeof(float2), s));
+  }
+  // candidate launch shapes: fractions and multiples of the resident CTAs
+  const int cands[] = {b->slots / 2, b->slots, (3 * b->slots) / 2, 2 * b->slots, 3 * b->slots, 4 * b->slots};
+  cudaEvent_t e0, e1;
+  BCUDA(cudaEventCreate(&e0));
+  BCUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_g = b->slots;
+  for (int c : cands) {
+    if (c < 1) continue;
+    set_grid(b, c);
+    ash_status st = enqueue_batch_forward(b, s);   // warm-up
+    if (st == ASH_OK) st = enqueue_batch_adjoint(b, s);
+    if (st != ASH_OK) return st;
+    BCUDA(cudaEventRecord(e0, s));
+    for (int r = 0; r < 2 && st == ASH_OK; ++r) {
+      st = enqueue_batch_forward(b, s);
+      if (st == ASH_OK) st = enqueue_batch_adjoint(b, s);
+    }
+    if (st != ASH_OK) return st;
+    BCUDA(cudaEventRecord(e1, s));
+    BCUDA(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    BCUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) {
+      best = ms;
+      best_g = b->G;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  set_grid(b, best_g);
+  cache_store(cache_path, b->key, b->G);
+  if (grid_out) *grid_out = b->G;
+  return ASH_OK;
+}
+
+}  // extern "C"

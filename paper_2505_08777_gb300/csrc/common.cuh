@@ -137,52 +137,54 @@ struct Schedule {
   }
 };
 
-struct FwdParams {
+// Everything a tile computation needs to know about one hologram.
+struct HoloView {
   Geometry g;
-  Schedule sched;
   const float* dz;        // register-image basis [T][NT][D][P]
   const float* amp_img;   // register-image amplitude [T][NT][P]
   const float2* anchors;  // [T][D] (hi, lo) of Z(anchor)/(2 pi)
   const float* coeff;     // [N][D]
+};
+
+struct FwdParams {
+  HoloView v;
+  Schedule sched;
   const float* phase;     // user layout [ny][nx] (kSrcPhase)
   const float2* field;    // user layout [ny][nx] complex (kSrcField)
   int source;
   float* partial;         // [T * NW][2N]: row (tile, warp), each entry written once
 };
 
-struct AdjParams {
-  Geometry g;
-  Schedule sched;
-  const float* dz;
-  const float* amp_img;
-  const float2* anchors;
-  const float* coeff;
-  const float2* y;        // [N] complex
+// Where the adjoint's per-pixel results go.
+struct AdjOut {
   float2* g_out;          // user layout complex or null
   float* phase_out;       // user layout or null
   const float* phase_in;  // for kEpiGradPhase: current phase (user layout)
   float* dphase;          // for kEpiGradPhase
-  float2* split;          // [G][2][kTilePix]: partial g of tiles split between CTAs
   int epilogue;
 };
 
+struct AdjParams {
+  HoloView v;
+  Schedule sched;
+  const float2* y;        // [N] complex
+  AdjOut out;
+  float2* split;          // [G][2][kTilePix]: partial g of tiles split between CTAs
+};
+
 // Per-pixel adjoint epilogue (m = flat pixel index, a = amplitude there).
-__device__ __forceinline__ void adjoint_epilogue(const AdjParams& p, size_t m, float gr, float gi, float a) {
-  if (p.epilogue & kEpiField) p.g_out[m] = make_float2(gr, gi);
-  if (p.epilogue & kEpiPhase) p.phase_out[m] = (gr == 0.0f && gi == 0.0f) ? 0.0f : atan2f(gi, gr);
-  if (p.epilogue & kEpiGradPhase) {
+__device__ __forceinline__ void adjoint_epilogue(const AdjOut& o, size_t m, float gr, float gi, float a) {
+  if (o.epilogue & kEpiField) o.g_out[m] = make_float2(gr, gi);
+  if (o.epilogue & kEpiPhase) o.phase_out[m] = (gr == 0.0f && gi == 0.0f) ? 0.0f : atan2f(gi, gr);
+  if (o.epilogue & kEpiGradPhase) {
     float s, c;
-    sincosf(__ldg(p.phase_in + m), &s, &c);
-    p.dphase[m] = (a * c) * gi - (a * s) * gr;   // -Im(f conj(h)), f = a exp(i phase)
+    sincosf(__ldg(o.phase_in + m), &s, &c);
+    o.dphase[m] = (a * c) * gi - (a * s) * gr;   // -Im(f conj(h)), f = a exp(i phase)
   }
 }
 
 struct GradCParams {
-  Geometry g;
-  const float* dz;
-  const float* amp_img;
-  const float2* anchors;
-  const float* coeff;
+  HoloView v;
   const float* phase;     // user layout
   const float2* gradE;    // [N]
   float* partial;         // [gridDim.x][N][D]

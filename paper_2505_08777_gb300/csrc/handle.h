@@ -1,0 +1,68 @@
+// Internal definition of the hologram handle (shared by the C-ABI
+// translation units; not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <vector>
+
+#include "ash.h"
+#include "common.cuh"
+#include "launch.h"
+#include "mono.h"
+
+struct ash_hologram {
+  ash::Geometry g{};
+  int device = 0;
+  cudaStream_t home = nullptr;     // stream the workspace was allocated on
+  ash::LaunchInfo li{};
+  ash::Schedule sched{};           // (tile, spot) ranges of the transform kernels
+  bool split_tiles = false;   // some tile's spots span two CTA ranges
+  int fwd_rows = 0;
+  int gradc_gx = 0, gradc_gy = 0;
+  // workspace
+  float* dz = nullptr;
+  float* amp_img = nullptr;
+  float2* anchors = nullptr;
+  float* coeff = nullptr;
+  float* partial = nullptr;
+  float2* split = nullptr;
+  float* gradc_partial = nullptr;
+  float2* E = nullptr;
+  float2* y = nullptr;
+  float* wgs_phase = nullptr;
+  float* wgs_w = nullptr;
+  float* wgs_T = nullptr;
+  float2* wgs_E = nullptr;
+  float* wgs_metrics = nullptr;
+  double* sum_a2 = nullptr;
+  ash::MonoTerm* terms = nullptr;
+  int* term_off = nullptr;
+  unsigned* err_word = nullptr;
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  cudaStream_t capture = nullptr;
+  std::map<int, cudaGraphExec_t> graphs;
+};
+
+namespace ash {
+
+// Record a message for ash_last_error() (any translation unit).
+void record_error(const char* msg);
+// Map a CUDA error to ASH_ERR_CUDA with a message.
+ash_status status_cuda(cudaError_t e, const char* where);
+// Host-side fault injection counter (ash_debug_fail_after).
+bool consume_injected_failure();
+
+inline HoloView view_of(const ash_hologram* h) {
+  HoloView v{};
+  v.g = h->g;
+  v.dz = h->dz;
+  v.amp_img = h->amp_img;
+  v.anchors = h->anchors;
+  v.coeff = h->coeff;
+  return v;
+}
+
+}  // namespace ash

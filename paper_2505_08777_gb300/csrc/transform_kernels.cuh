@@ -129,15 +129,16 @@ __device__ __forceinline__ void sincos2(float2 x, float2& s, float2& c) {
 // ---------------------------------------------------------------------------
 // Nearfield pairs f = A exp(i phase) (or a caller field) of a thread's P pixels.
 template <int P>
-__device__ __forceinline__ void load_field(const FwdParams& p, int tile, int t, float2 (&fr2)[P / 2],
-                                           float2 (&fi2)[P / 2], float2 (&nfr2)[P / 2]) {
+__device__ __forceinline__ void load_field(const HoloView& hv, int source, const float* __restrict__ phase,
+                                           const float2* __restrict__ field, int tile, int t,
+                                           float2 (&fr2)[P / 2], float2 (&fi2)[P / 2], float2 (&nfr2)[P / 2]) {
   constexpr int NT = kTilePix / P;
   constexpr int RS = NT / 32;
-  const Geometry& G = p.g;
+  const Geometry& G = hv.g;
   const int lane = t & 31, w = t >> 5;
   const int tx = tile % G.tiles_x, ty = tile / G.tiles_x;
   const int i = tx * kTileX + lane;
-  const float4* asrc = reinterpret_cast<const float4*>(p.amp_img + ((size_t)tile * NT + t) * P);
+  const float4* asrc = reinterpret_cast<const float4*>(hv.amp_img + ((size_t)tile * NT + t) * P);
   float a[P], fr[P], fi[P];
 #pragma unroll
   for (int q = 0; q < P / 4; ++q) {
@@ -149,14 +150,14 @@ __device__ __forceinline__ void load_field(const FwdParams& p, int tile, int t, 
     const int j = ty * kTileY + w + RS * k;
     const bool valid = (i < G.nx) && (j < G.ny);
     const size_t m = (size_t)j * G.nx + i;
-    if (p.source == kSrcPhase) {
-      const float ph = valid ? __ldg(p.phase + m) : 0.0f;
+    if (source == kSrcPhase) {
+      const float ph = valid ? __ldg(phase + m) : 0.0f;
       float sn, cs;
       sincosf(ph, &sn, &cs);
       fr[k] = a[k] * cs;
       fi[k] = a[k] * sn;
     } else {
-      const float2 f = valid ? __ldg(p.field + m) : make_float2(0.0f, 0.0f);
+      const float2 f = valid ? __ldg(field + m) : make_float2(0.0f, 0.0f);
       fr[k] = f.x;
       fi[k] = f.y;
     }
@@ -169,173 +170,198 @@ __device__ __forceinline__ void load_field(const FwdParams& p, int tile, int t, 
   }
 }
 
-// ---------------------------------------------------------------------------
-// Forward: partial[(tile, warp)][2n..2n+1] = sum over the warp's pixels of the
-// tile of f_m exp(-i C_n . Z_m), for the (tile, spot) units of this CTA's
-// range. Every entry is written exactly once per launch.
+// Forward over spots [sb, se) of one tile: ptile[w][2n..2n+1] = sum over
+// warp w's pixels of f_m exp(-i C_n . Z_m). Called uniformly by the CTA.
 template <int D, int P>
-__global__ void ASH_BOUNDS(P) k_forward(const FwdParams p) {
+__device__ __forceinline__ void forward_tile(const HoloView& hv, int source, const float* __restrict__ phase,
+                                             const float2* __restrict__ field, int tile, int sb, int se,
+                                             float* __restrict__ ptile, float* sC, float2* sRot) {
   constexpr int NT = kTilePix / P;
-  constexpr int NW = NT / 32;
   constexpr int CPS = cpair_stride(D);
-  extern __shared__ float4 smem4[];
-  float* sC = reinterpret_cast<float*>(smem4);
-  float2* sRot = reinterpret_cast<float2*>(sC + kSpotChunk * CPS);
-
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  const int N = p.g.N;
-  const long long u0 = p.sched.begin(blockIdx.x), u1 = p.sched.begin(blockIdx.x + 1);
-  const int tf = (int)(u0 / N), tl = (int)((u1 - 1) / N);
+  const int N = hv.g.N;
+  float2 dz[P / 2][D];
+  load_dz<D, P>(hv.dz, tile, t, dz);
+  float2 fr2[P / 2], fi2[P / 2], nfr2[P / 2];
+  load_field<P>(hv, source, phase, field, tile, t, fr2, fi2, nfr2);
+  float* prow = ptile + (size_t)w * 2 * N;
+  const float2* anc = hv.anchors + (size_t)tile * D;
 
-  for (int tile = tf; tile <= tl; ++tile) {
-    const int sb = (tile == tf) ? (int)(u0 - (long long)tile * N) : 0;
-    const int se = (tile == tl) ? (int)(u1 - (long long)tile * N) : N;
-    float2 dz[P / 2][D];
-    load_dz<D, P>(p.dz, tile, t, dz);
-    float2 fr2[P / 2], fi2[P / 2], nfr2[P / 2];
-    load_field<P>(p, tile, t, fr2, fi2, nfr2);
-    float* prow = p.partial + ((size_t)tile * NW + w) * 2 * N;
-    const float2* anc = p.anchors + (size_t)tile * D;
+  for (int n0 = sb; n0 < se; n0 += kSpotChunk) {
+    const int nc = min(kSpotChunk, se - n0);
+    __syncthreads();
+    for (int s = t; s < nc; s += NT) {
+      const float bt = stage_spot<D>(hv.coeff, anc, n0 + s, sC + s * CPS);
+      sRot[s] = cis_turns(-bt);
+    }
+    __syncthreads();
 
-    for (int n0 = sb; n0 < se; n0 += kSpotChunk) {
-      const int nc = min(kSpotChunk, se - n0);
-      __syncthreads();
-      for (int s = t; s < nc; s += NT) {
-        const float bt = stage_spot<D>(p.coeff, anc, n0 + s, sC + s * CPS);
-        sRot[s] = cis_turns(-bt);
-      }
-      __syncthreads();
-
-      for (int b0 = 0; b0 < nc; b0 += kBatch) {
-        float acc[32];
+    for (int b0 = 0; b0 < nc; b0 += kBatch) {
+      float acc[32];
 #pragma unroll
-        for (int s = 0; s < kBatch; ++s) {
-          float re = 0.0f, im = 0.0f;
-          if (b0 + s < nc) {
-            float2 cc[D];
-            load_cpairs<D>(sC + (b0 + s) * CPS, cc);
-            float2 re2 = make_float2(0.0f, 0.0f), im2 = make_float2(0.0f, 0.0f);
-#pragma unroll
-            for (int q = 0; q < P / 2; ++q) {
-              const float2 x = local_phase<D>(cc, dz[q]);
-              float2 sn, cs;
-              sincos2(x, sn, cs);
-              re2 = fma2(fr2[q], cs, re2);
-              re2 = fma2(fi2[q], sn, re2);
-              im2 = fma2(fi2[q], cs, im2);
-              im2 = fma2(nfr2[q], sn, im2);
-            }
-            re = re2.x + re2.y;
-            im = im2.x + im2.y;
-          }
-          acc[2 * s] = re;
-          acc[2 * s + 1] = im;
-        }
-        const float v = warp_transpose_reduce32(acc, lane);
-        const float other = __shfl_xor_sync(kFull, v, 1);
-        const int s = lane >> 1;
-        const bool is_im = (lane & 1) != 0;
+      for (int s = 0; s < kBatch; ++s) {
+        float re = 0.0f, im = 0.0f;
         if (b0 + s < nc) {
-          const float re = is_im ? other : v;
-          const float im = is_im ? v : other;
-          const float2 r = sRot[b0 + s];
-          prow[2 * (n0 + b0) + lane] = is_im ? fmaf(im, r.x, re * r.y) : fmaf(re, r.x, -im * r.y);
+          float2 cc[D];
+          load_cpairs<D>(sC + (b0 + s) * CPS, cc);
+          float2 re2 = make_float2(0.0f, 0.0f), im2 = make_float2(0.0f, 0.0f);
+#pragma unroll
+          for (int q = 0; q < P / 2; ++q) {
+            const float2 x = local_phase<D>(cc, dz[q]);
+            float2 sn, cs;
+            sincos2(x, sn, cs);
+            re2 = fma2(fr2[q], cs, re2);
+            re2 = fma2(fi2[q], sn, re2);
+            im2 = fma2(fi2[q], cs, im2);
+            im2 = fma2(nfr2[q], sn, im2);
+          }
+          re = re2.x + re2.y;
+          im = im2.x + im2.y;
         }
+        acc[2 * s] = re;
+        acc[2 * s + 1] = im;
+      }
+      const float v = warp_transpose_reduce32(acc, lane);
+      const float other = __shfl_xor_sync(kFull, v, 1);
+      const int s = lane >> 1;
+      const bool is_im = (lane & 1) != 0;
+      if (b0 + s < nc) {
+        const float re = is_im ? other : v;
+        const float im = is_im ? v : other;
+        const float2 r = sRot[b0 + s];
+        prow[2 * (n0 + b0) + lane] = is_im ? fmaf(im, r.x, re * r.y) : fmaf(re, r.x, -im * r.y);
       }
     }
   }
 }
 
-// ---------------------------------------------------------------------------
-// Adjoint over this CTA's (tile, spot) range. Tiles whose full spot range is
-// owned by the CTA get the epilogue here; the partial sums of tiles split
-// between CTAs go to p.split (slot 0 = first tile of the range, 1 = last)
-// and are finished by k_adjoint_fixup in a fixed CTA order.
+// Adjoint over spots [sb, se) of one tile into per-thread accumulators.
 template <int D, int P>
-__global__ void ASH_BOUNDS(P) k_adjoint(const AdjParams p) {
+__device__ __forceinline__ void adjoint_tile(const HoloView& hv, const float2* __restrict__ y, int tile, int sb,
+                                             int se, float2 (&re2)[P / 2], float2 (&im2)[P / 2], float* sC,
+                                             float4* sY) {
+  constexpr int NT = kTilePix / P;
+  constexpr int CPS = cpair_stride(D);
+  const int t = threadIdx.x;
+  float2 dz[P / 2][D];
+  load_dz<D, P>(hv.dz, tile, t, dz);
+#pragma unroll
+  for (int q = 0; q < P / 2; ++q) {
+    re2[q] = make_float2(0.0f, 0.0f);
+    im2[q] = make_float2(0.0f, 0.0f);
+  }
+  const float2* anc = hv.anchors + (size_t)tile * D;
+  for (int n0 = sb; n0 < se; n0 += kSpotChunk) {
+    const int nc = min(kSpotChunk, se - n0);
+    __syncthreads();
+    for (int s = t; s < nc; s += NT) {
+      const float bt = stage_spot<D>(hv.coeff, anc, n0 + s, sC + s * CPS);
+      const float2 r = cis_turns(bt);
+      const float2 yv = __ldg(y + n0 + s);
+      const float yr = yv.x * r.x - yv.y * r.y;
+      const float yi = yv.x * r.y + yv.y * r.x;
+      sY[2 * s] = make_float4(yr, yr, yi, yi);
+      sY[2 * s + 1] = make_float4(-yi, -yi, 0.0f, 0.0f);
+    }
+    __syncthreads();
+
+#pragma unroll 2
+    for (int s = 0; s < nc; ++s) {
+      float2 cc[D];
+      load_cpairs<D>(sC + s * CPS, cc);
+      const float4 ya = sY[2 * s];
+      const float4 yb = sY[2 * s + 1];
+      const float2 yr2 = make_float2(ya.x, ya.y);
+      const float2 yi2 = make_float2(ya.z, ya.w);
+      const float2 nyi2 = make_float2(yb.x, yb.y);
+#pragma unroll
+      for (int q = 0; q < P / 2; ++q) {
+        const float2 x = local_phase<D>(cc, dz[q]);
+        float2 sn, cs;
+        sincos2(x, sn, cs);
+        re2[q] = fma2(yr2, cs, re2[q]);
+        re2[q] = fma2(nyi2, sn, re2[q]);
+        im2[q] = fma2(yi2, cs, im2[q]);
+        im2[q] = fma2(yr2, sn, im2[q]);
+      }
+    }
+  }
+}
+
+// After adjoint_tile: epilogue for a tile whose whole spot range this CTA
+// owns, else the partial field into the CTA's split slot.
+template <int P>
+__device__ __forceinline__ void adjoint_finish(const HoloView& hv, const AdjOut& out, int tile, bool full,
+                                               float2* __restrict__ slot, const float2 (&re2)[P / 2],
+                                               const float2 (&im2)[P / 2]) {
   constexpr int NT = kTilePix / P;
   constexpr int RS = NT / 32;
+  const Geometry& G = hv.g;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  if (full) {
+    const int tx = tile % G.tiles_x, ty = tile / G.tiles_x;
+    const int i = tx * kTileX + lane;
+    const float* aimg = hv.amp_img + ((size_t)tile * NT + t) * P;
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      const int j = ty * kTileY + w + RS * k;
+      if (i >= G.nx || j >= G.ny) continue;
+      const float gr = (k & 1) ? re2[k >> 1].y : re2[k >> 1].x;
+      const float gi = (k & 1) ? im2[k >> 1].y : im2[k >> 1].x;
+      const float a = (out.epilogue & kEpiGradPhase) ? __ldg(aimg + k) : 0.0f;
+      adjoint_epilogue(out, (size_t)j * G.nx + i, gr, gi, a);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      const float gr = (k & 1) ? re2[k >> 1].y : re2[k >> 1].x;
+      const float gi = (k & 1) ? im2[k >> 1].y : im2[k >> 1].x;
+      slot[k * NT + t] = make_float2(gr, gi);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Forward: partial[(tile, warp)][2n..2n+1] over this CTA's (tile, spot) range;
+// every entry is written exactly once per launch.
+template <int D, int P>
+__global__ void ASH_BOUNDS(P) k_forward(const FwdParams p) {
+  constexpr int NW = kTilePix / P / 32;
   constexpr int CPS = cpair_stride(D);
   extern __shared__ float4 smem4[];
   float* sC = reinterpret_cast<float*>(smem4);
-  float4* sY = reinterpret_cast<float4*>(sC + kSpotChunk * CPS);   // [chunk][2] float4
-
-  const Geometry& G = p.g;
-  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  const int N = G.N;
+  float2* sRot = reinterpret_cast<float2*>(sC + kSpotChunk * CPS);
+  const int N = p.v.g.N;
   const long long u0 = p.sched.begin(blockIdx.x), u1 = p.sched.begin(blockIdx.x + 1);
   const int tf = (int)(u0 / N), tl = (int)((u1 - 1) / N);
-
   for (int tile = tf; tile <= tl; ++tile) {
     const int sb = (tile == tf) ? (int)(u0 - (long long)tile * N) : 0;
     const int se = (tile == tl) ? (int)(u1 - (long long)tile * N) : N;
-    float2 dz[P / 2][D];
-    load_dz<D, P>(p.dz, tile, t, dz);
+    forward_tile<D, P>(p.v, p.source, p.phase, p.field, tile, sb, se, p.partial + (size_t)tile * NW * 2 * N, sC,
+                       sRot);
+  }
+}
+
+// Adjoint over this CTA's (tile, spot) range. Tiles whose full spot range is
+// owned by the CTA get the epilogue here; tiles split between CTAs leave
+// their partial sums in p.split (slot 0 = first tile of the range, 1 = last)
+// for k_adjoint_fixup, which adds them in CTA order.
+template <int D, int P>
+__global__ void ASH_BOUNDS(P) k_adjoint(const AdjParams p) {
+  constexpr int CPS = cpair_stride(D);
+  extern __shared__ float4 smem4[];
+  float* sC = reinterpret_cast<float*>(smem4);
+  float4* sY = reinterpret_cast<float4*>(sC + kSpotChunk * CPS);
+  const int N = p.v.g.N;
+  const long long u0 = p.sched.begin(blockIdx.x), u1 = p.sched.begin(blockIdx.x + 1);
+  const int tf = (int)(u0 / N), tl = (int)((u1 - 1) / N);
+  for (int tile = tf; tile <= tl; ++tile) {
+    const int sb = (tile == tf) ? (int)(u0 - (long long)tile * N) : 0;
+    const int se = (tile == tl) ? (int)(u1 - (long long)tile * N) : N;
     float2 re2[P / 2], im2[P / 2];
-#pragma unroll
-    for (int q = 0; q < P / 2; ++q) {
-      re2[q] = make_float2(0.0f, 0.0f);
-      im2[q] = make_float2(0.0f, 0.0f);
-    }
-    const float2* anc = p.anchors + (size_t)tile * D;
-    for (int n0 = sb; n0 < se; n0 += kSpotChunk) {
-      const int nc = min(kSpotChunk, se - n0);
-      __syncthreads();
-      for (int s = t; s < nc; s += NT) {
-        const float bt = stage_spot<D>(p.coeff, anc, n0 + s, sC + s * CPS);
-        const float2 r = cis_turns(bt);
-        const float2 y = __ldg(p.y + n0 + s);
-        const float yr = y.x * r.x - y.y * r.y;
-        const float yi = y.x * r.y + y.y * r.x;
-        sY[2 * s] = make_float4(yr, yr, yi, yi);
-        sY[2 * s + 1] = make_float4(-yi, -yi, 0.0f, 0.0f);
-      }
-      __syncthreads();
-
-#pragma unroll 2
-      for (int s = 0; s < nc; ++s) {
-        float2 cc[D];
-        load_cpairs<D>(sC + s * CPS, cc);
-        const float4 ya = sY[2 * s];
-        const float4 yb = sY[2 * s + 1];
-        const float2 yr2 = make_float2(ya.x, ya.y);
-        const float2 yi2 = make_float2(ya.z, ya.w);
-        const float2 nyi2 = make_float2(yb.x, yb.y);
-#pragma unroll
-        for (int q = 0; q < P / 2; ++q) {
-          const float2 x = local_phase<D>(cc, dz[q]);
-          float2 sn, cs;
-          sincos2(x, sn, cs);
-          re2[q] = fma2(yr2, cs, re2[q]);
-          re2[q] = fma2(nyi2, sn, re2[q]);
-          im2[q] = fma2(yi2, cs, im2[q]);
-          im2[q] = fma2(yr2, sn, im2[q]);
-        }
-      }
-    }
-
-    if (sb == 0 && se == N) {
-      const int tx = tile % G.tiles_x, ty = tile / G.tiles_x;
-      const int i = tx * kTileX + lane;
-      const float* aimg = p.amp_img + ((size_t)tile * NT + t) * P;
-#pragma unroll
-      for (int k = 0; k < P; ++k) {
-        const int j = ty * kTileY + w + RS * k;
-        if (i >= G.nx || j >= G.ny) continue;
-        const float gr = (k & 1) ? re2[k >> 1].y : re2[k >> 1].x;
-        const float gi = (k & 1) ? im2[k >> 1].y : im2[k >> 1].x;
-        const float a = (p.epilogue & kEpiGradPhase) ? __ldg(aimg + k) : 0.0f;
-        adjoint_epilogue(p, (size_t)j * G.nx + i, gr, gi, a);
-      }
-    } else {
-      float2* dst = p.split + ((size_t)blockIdx.x * 2 + (tile == tf ? 0 : 1)) * kTilePix;
-#pragma unroll
-      for (int k = 0; k < P; ++k) {
-        const float gr = (k & 1) ? re2[k >> 1].y : re2[k >> 1].x;
-        const float gi = (k & 1) ? im2[k >> 1].y : im2[k >> 1].x;
-        dst[k * NT + t] = make_float2(gr, gi);
-      }
-    }
+    adjoint_tile<D, P>(p.v, p.y, tile, sb, se, re2, im2, sC, sY);
+    float2* slot = p.split + ((size_t)blockIdx.x * 2 + (tile == tf ? 0 : 1)) * kTilePix;
+    adjoint_finish<P>(p.v, p.out, tile, sb == 0 && se == N, slot, re2, im2);
   }
 }
 
@@ -352,7 +378,7 @@ __global__ void __launch_bounds__(kGradThreads) k_gradc(const GradCParams p) {
   constexpr int REC = gradc_rec(D);
   extern __shared__ float4 smem4[];
   float* sP = reinterpret_cast<float*>(smem4);
-  const Geometry& G = p.g;
+  const Geometry& G = p.v.g;
   const int P = G.P, NTp = G.NT;   // pixel layout of the register-image arrays
   const int t = threadIdx.x;
   const int N = G.N;
@@ -368,7 +394,7 @@ __global__ void __launch_bounds__(kGradThreads) k_gradc(const GradCParams p) {
     act[s] = n < N;
 #pragma unroll
     for (int d = 0; d < D; ++d) {
-      c[s][d] = act[s] ? __ldg(p.coeff + (size_t)n * D + d) : 0.0f;
+      c[s][d] = act[s] ? __ldg(p.v.coeff + (size_t)n * D + d) : 0.0f;
       mom[s][d] = 0.0f;
     }
     gE[s] = act[s] ? __ldg(p.gradE + n) : make_float2(0.0f, 0.0f);
@@ -376,7 +402,7 @@ __global__ void __launch_bounds__(kGradThreads) k_gradc(const GradCParams p) {
 
   for (int tile = blockIdx.x; tile < G.T; tile += gridDim.x) {
     const int tx = tile % G.tiles_x, ty = tile / G.tiles_x;
-    const float2* anc = p.anchors + (size_t)tile * D;
+    const float2* anc = p.v.anchors + (size_t)tile * D;
     __syncthreads();
     // stage the tile: pixel (tp, k) of the register-image layout -> record
     for (int e = t; e < kTilePix; e += kGradThreads) {
@@ -386,7 +412,7 @@ __global__ void __launch_bounds__(kGradThreads) k_gradc(const GradCParams p) {
       const int j = ty * kTileY + wq + (NTp / 32) * k;
       const bool valid = (i < G.nx) && (j < G.ny);
       float* rec = sP + (size_t)e * REC;
-      const float* src = p.dz + ((size_t)tile * NTp + tp) * D * P + k;
+      const float* src = p.v.dz + ((size_t)tile * NTp + tp) * D * P + k;
 #pragma unroll
       for (int d = 0; d < D; ++d) {
         const float dzv = __ldg(src + d * P);
@@ -396,7 +422,7 @@ __global__ void __launch_bounds__(kGradThreads) k_gradc(const GradCParams p) {
       }
       float fr = 0.0f, fi = 0.0f;
       if (valid) {
-        const float amp = __ldg(p.amp_img + ((size_t)tile * NTp + tp) * P + k);
+        const float amp = __ldg(p.v.amp_img + ((size_t)tile * NTp + tp) * P + k);
         float sn, cs;
         sincosf(__ldg(p.phase + (size_t)j * G.nx + i), &sn, &cs);
         fr = amp * cs;

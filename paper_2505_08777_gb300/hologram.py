@@ -13,7 +13,7 @@ import torch
 
 from . import _lib
 
-__all__ = ["Hologram"]
+__all__ = ["Hologram", "Batch"]
 
 
 def _stream_ptr(stream=None) -> ctypes.c_void_p:
@@ -162,3 +162,83 @@ class Hologram:
 
     def check(self, stream=None):
         _lib.check(self._lib.ash_hologram_check(self._h, _stream_ptr(stream)), "ash_hologram_check")
+
+
+class Batch:
+    """Many holograms solved together (ash_batch_*): one launch per WGS phase
+    over all holograms' (tile, spot) work units, the loop as one CUDA graph."""
+
+    def __init__(self, problems, stream=None):
+        """problems: list of (amp (ny, nx), coeff (N, D), noll list) CUDA tensors / lists."""
+        self._lib = _lib.load()
+        self._b = ctypes.c_void_p(0)
+        self.shapes = []
+        self._keep = []
+        descs = (_lib.HologramDesc * len(problems))()
+        for i, (amp, coeff, noll) in enumerate(problems):
+            ny, nx = int(amp.shape[0]), int(amp.shape[1])
+            N, D = int(coeff.shape[0]), int(coeff.shape[1])
+            _need(amp, torch.float32, (ny, nx), "amp")
+            _need(coeff, torch.float32, (N, D), "coeff")
+            arr = (ctypes.c_int * D)(*[int(v) for v in noll])
+            self._keep.append(arr)
+            descs[i] = _lib.HologramDesc(nx, ny, amp.data_ptr(), D, ctypes.cast(arr, _lib.c_int_p), None, N,
+                                         coeff.data_ptr())
+            self.shapes.append((ny, nx, N, D))
+        _lib.check(self._lib.ash_batch_create(ctypes.byref(self._b), len(problems), descs, _stream_ptr(stream)),
+                   "ash_batch_create")
+
+    def close(self):
+        if getattr(self, "_b", None) is not None and self._b.value:
+            torch.cuda.current_stream().synchronize()
+            self._lib.ash_batch_destroy(self._b)
+            self._b = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def count(self) -> int:
+        return len(self.shapes)
+
+    def info(self) -> dict:
+        c, g, r = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        u = ctypes.c_longlong()
+        _lib.check(self._lib.ash_batch_info(self._b, ctypes.byref(c), ctypes.byref(g), ctypes.byref(r),
+                                            ctypes.byref(u)), "ash_batch_info")
+        return {"count": c.value, "grid": g.value, "resident_ctas": r.value, "units": u.value}
+
+    def set_grid(self, grid: int):
+        _lib.check(self._lib.ash_batch_set_grid(self._b, int(grid)), "ash_batch_set_grid")
+
+    def launches(self, iters: int) -> int:
+        return int(self._lib.ash_batch_wgs_launches(self._b, int(iters)))
+
+    def _ptrs(self, tensors, dtype, shapes, name):
+        if len(tensors) != self.count:
+            raise ValueError(f"{name}: need {self.count} tensors")
+        for t, shp in zip(tensors, shapes):
+            _need(t, dtype, shp, name)
+        return (ctypes.c_void_p * self.count)(*[t.data_ptr() for t in tensors])
+
+    def wgs(self, phases, weights, targets, iters: int, metrics_out: torch.Tensor | None = None, stream=None):
+        """In place on phases / weights; returns metrics (count, 4)."""
+        ph = self._ptrs(phases, torch.float32, [(s[0], s[1]) for s in self.shapes], "phases")
+        w = self._ptrs(weights, torch.float32, [(s[2],) for s in self.shapes], "weights")
+        T = self._ptrs(targets, torch.float32, [(s[2],) for s in self.shapes], "targets")
+        met = metrics_out if metrics_out is not None else torch.empty((self.count, 4), dtype=torch.float32,
+                                                                       device=phases[0].device)
+        _need(met, torch.float32, (self.count, 4), "metrics_out")
+        _lib.check(self._lib.ash_batch_wgs(self._b, ph, w, T, int(iters), _ptr(met), _stream_ptr(stream)),
+                   "ash_batch_wgs")
+        return met
+
+    def tune(self, phases, cache_path: str | None = None, stream=None) -> int:
+        ph = self._ptrs(phases, torch.float32, [(s[0], s[1]) for s in self.shapes], "phases")
+        g = ctypes.c_int()
+        path = cache_path.encode() if cache_path else None
+        _lib.check(self._lib.ash_batch_tune(self._b, ph, path, ctypes.byref(g), _stream_ptr(stream)), "ash_batch_tune")
+        return g.value

@@ -51,7 +51,7 @@ def test_autograd_matches_oracle_and_torch_reference():
     I = E64.abs() ** 2
     r = I / I.mean() - torch.from_numpy(p.target.astype(np.float64)).cuda()
     (r * r).sum().backward()
-    assert _rel(phase.grad.double().cpu().numpy().ravel(), ph64.grad.cpu().numpy()) <= GRAD_TOL
+    assert _rel(phase.grad.double().cpu().numpy().ravel(), ph64.grad.cpu().numpy().ravel()) <= GRAD_TOL
     assert _rel(coeff.grad.double().cpu().numpy(), C64.grad.cpu().numpy()) <= GRAD_TOL
 
 
