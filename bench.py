@@ -36,10 +36,17 @@ MUFU_PER_TERM = 2                 # one sin and one cos per term
 MAX_SM_MHZ = 2070.0
 
 
-def _workload_config(p, iters):
+WORKLOAD_TEXT = {
+    "c2": "anisoplanatic 2D tweezer array: SLM {nx}x{ny}, N={N} spots (20x20 grid, +-0.45 Nyquist, "
+          "50 isoplanatic patches x 8 modes), D={D} (Noll 2-11), {iters} WGS iterations per step",
+    "c3": "3D volumetric spots: SLM {nx}x{ny} flat-top, N={N} spots (20x20x5 lattice, defocus in [-20, 20] rad), "
+          "D={D} (Noll 2-12), {iters} WGS iterations per step",
+}
+
+
+def _workload_config(p, iters, cfg="c2"):
     return {
-        "workload": f"anisoplanatic 2D tweezer array: SLM {p.nx}x{p.ny}, N={p.N} spots (20x20 grid, +-0.45 Nyquist, "
-                    f"50 isoplanatic patches x 8 modes), D={p.D} (Noll 2-11), {iters} WGS iterations per step",
+        "workload": WORKLOAD_TEXT[cfg].format(nx=p.nx, ny=p.ny, N=p.N, D=p.D, iters=iters),
         "nx": p.nx, "ny": p.ny, "N": p.N, "D": p.D, "iters_per_step": iters,
         "terms_per_step": (2 * iters + 1) * p.N * p.M,
         "l2": "flushed between steps (256 MiB write)",
@@ -54,6 +61,9 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5"],
+                    help="c2 (default, the headline): anisoplanatic 2D WGS; c3: 3D volume WGS; "
+                         "c4: autograd + Adam on 8 holograms; c5: 64 uneven holograms, batched vs looped")
     return ap.parse_args()
 
 
@@ -177,10 +187,14 @@ def main():
     args = _args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.config == "c4":
+        return bench_autograd(args)
+    if args.config == "c5":
+        return bench_batch(args)
     import torch
 
     from paper_2505_08777_gb300 import Hologram
-    from workloads import config_c2
+    from workloads import config_c2, config_c3
 
     rank, world, local = _dist()
     torch.cuda.set_device(local)
@@ -188,7 +202,7 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    p = config_c2(1 + rank)
+    p = (config_c2 if args.config == "c2" else config_c3)(1 + rank)
     iters = p.iters
     terms_per_step = (2 * iters + 1) * p.N * p.M
     stream = torch.cuda.current_stream()
@@ -292,8 +306,9 @@ def main():
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = sms * (MUFU_PER_CLK_PER_SM / MUFU_PER_TERM) * MAX_SM_MHZ * 1e6 / 1e9
     dom = "forward" if kms["forward"] >= kms["adjoint"] else "adjoint"
-    kernel_names = {"forward": f"k_forward<D={p.D},P=8> (pixel-stationary forward, warp transpose reduction)",
-                    "adjoint": f"k_adjoint<D={p.D},P=8> (pixel-stationary adjoint, arg epilogue)"}
+    P = 8 if p.D <= 12 else 4
+    kernel_names = {"forward": f"k_forward<D={p.D},P={P}> (pixel-stationary forward, warp transpose reduction)",
+                    "adjoint": f"k_adjoint<D={p.D},P={P}> (pixel-stationary adjoint, arg epilogue)"}
     achieved = gterm[dom]
     roofline = {
         "bound": "alu", "kernel": kernel_names[dom],
@@ -307,7 +322,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic", "config": _workload_config(p, iters),
+        "dtype": "f32", "data": "synthetic", "config": _workload_config(p, iters, args.config),
         "wgs_iter_per_s": world * iters * args.steps / (total_ms_max * 1e-3),
         "final_uniformity": uniformity,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -316,7 +331,9 @@ def main():
         "kernels": {"ms": kms, "gterm_s": gterm, "create_s": create_s},
         "clocks": clk,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if args.config != "c2":
+        line["metric"] = f"spot-kernel Gterm/s (N*M phase+sincos+cMAC) fwd+adj; WGS iter/s, workload {args.config}"
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.config == "c2":
         from oracle import zernike
         Z = zernike.basis(p.nx, p.ny, p.noll)
         cores = _cpu_cores()
@@ -329,6 +346,152 @@ def main():
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
+    return 0
+
+
+def _peak_gterm(torch, dev):
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    return sms * (MUFU_PER_CLK_PER_SM / MUFU_PER_TERM) * MAX_SM_MHZ * 1e6 / 1e9
+
+
+def bench_autograd(args):
+    """c4: gradient descent (Adam) on the spot-intensity loss for a batch of 8
+    holograms (1024^2, N=1024, D=10), gradients w.r.t. phase and C through the
+    hand-written adjoint. One step = forward + backward for all 8 + Adam."""
+    import torch
+
+    from paper_2505_08777_gb300 import Hologram
+    from paper_2505_08777_gb300.autograd import spot_field, spot_intensity_loss
+    from workloads import config_c4
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    ps = [config_c4(s) for s in range(1, 9)]
+    hs = [Hologram(torch.from_numpy(p.amp).to(dev), torch.from_numpy(p.coeff).to(dev), noll=p.noll) for p in ps]
+    phases = [torch.from_numpy(p.phase0).to(dev).requires_grad_(True) for p in ps]
+    coeffs = [torch.from_numpy(p.coeff).to(dev).requires_grad_(True) for p in ps]
+    targets = [torch.from_numpy(p.target).to(dev) for p in ps]
+    opt = torch.optim.Adam(phases + coeffs, lr=0.01)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        opt.zero_grad(set_to_none=False)
+        total = 0.0
+        for h, ph, c, t in zip(hs, phases, coeffs, targets):
+            loss = spot_intensity_loss(spot_field(h, ph, c), t)
+            loss.backward()
+            total = total + loss.detach()
+        opt.step()
+        return total
+
+    first = step()
+    for _ in range(max(args.warmup, 3) - 1):
+        step()
+    torch.cuda.synchronize()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    ms = 0.0
+    with ClockSampler(0) as clocks:
+        for _ in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            last = step()
+            b.record(stream)
+            b.synchronize()
+            ms += a.elapsed_time(b)
+    terms = sum(3 * p.N * p.M for p in ps)     # forward + adjoint (dphase) + moment pass (dC)
+    value = terms * args.steps / (ms * 1e-3) / 1e9
+    line = {"metric": "autograd spot-kernel Gterm/s (fwd + dphase adjoint + dC moments), Adam steps/s, workload c4",
+            "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "8 holograms 1024x1024, N=1024 (32x32 grid), D=10; loss sum (I/mean I - t)^2, "
+                                   "t ~ U[0.5, 1.5]; Adam lr 0.01 on phase and C; one step = 8 x (fwd + bwd) + Adam",
+                       "l2": "flushed between steps (256 MiB write)"},
+            "adam_steps_per_s": args.steps / (ms * 1e-3),
+            "loss_first_step": float(first.item()), "loss_last_step": float(last.item()),
+            "gpu_launches": None, "clocks": clocks.summary()}
+    print(json.dumps(line))
+    return 0
+
+
+def bench_batch(args):
+    """c5: 64 uneven holograms (512^2 / 1024^2 / 1920x1152, N log-uniform in
+    [10, 5000], D in {5, 10, 11}), 50 WGS iterations each: the batched form
+    (one launch per phase for all holograms, one CUDA graph) against looping
+    the per-hologram path. One step = the whole batch solved once."""
+    import torch
+
+    from paper_2505_08777_gb300 import Batch, Hologram
+    from workloads import config_c5
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    ps = config_c5(1, count=64)
+    iters = ps[0].iters
+    amps = [torch.from_numpy(p.amp).to(dev) for p in ps]
+    coeffs = [torch.from_numpy(p.coeff).to(dev) for p in ps]
+    b = Batch([(a, c, p.noll) for a, c, p in zip(amps, coeffs, ps)])
+    hs = [Hologram(a, c, noll=p.noll) for a, c, p in zip(amps, coeffs, ps)]
+    ph0 = [torch.from_numpy(p.phase0).to(dev) for p in ps]
+    T = [torch.from_numpy(p.target).to(dev) for p in ps]
+    ph = [x.clone() for x in ph0]
+    w = [t.clone() for t in T]
+    tuned = b.tune(ph0, os.path.join(ROOT, "gpurun_out", "ash_tune.txt"))
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def reset():
+        for x, y in zip(ph, ph0):
+            x.copy_(y)
+        for x, y in zip(w, T):
+            x.copy_(y)
+
+    def batched():
+        b.wgs(ph, w, T, iters)
+
+    def looped():
+        for h, x, y, t in zip(hs, ph, w, T):
+            h.wgs(x, y, t, iters)
+
+    def timed(fn, reps):
+        for _ in range(max(args.warmup, 3)):
+            reset()
+            fn()
+        tot = 0.0
+        for _ in range(reps):
+            reset()
+            flush.zero_()
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            e.record(stream)
+            e.synchronize()
+            tot += a.elapsed_time(e)
+        return tot / reps
+
+    with ClockSampler(0) as clocks:
+        ms_b = timed(batched, args.steps)
+        ms_l = timed(looped, args.steps)
+    met = b.wgs([x.clone() for x in ph0], [t.clone() for t in T], T, iters).cpu().numpy()
+    terms = sum((2 * iters + 1) * p.N * p.M for p in ps)
+    info = b.info()
+    line = {"metric": "spot-kernel Gterm/s fwd+adj, batched uneven WGS (64 holograms x 50 iterations), workload c5",
+            "value": terms / (ms_b * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "64 holograms, sizes {512^2, 1024^2, 1920x1152}, N log-uniform [10, 5000], "
+                                   "D in {5, 10, 11}, 50 WGS iterations each; one step = the whole batch",
+                       "terms_per_step": terms, "l2": "flushed between steps (256 MiB write)",
+                       "tuned_grid": tuned, "resident_ctas": info["resident_ctas"]},
+            "looped_gterm_s": terms / (ms_l * 1e-3) / 1e9, "looped_ms_per_step": ms_l,
+            "batched_speedup_vs_loop": ms_l / ms_b,
+            "gpu_launches": b.launches(iters) * args.steps,
+            "looped_gpu_launches": sum(int(h._lib.ash_wgs_launches(h.handle, iters)) for h in hs) * args.steps,
+            "uniformity_min": float(met[:, 0].min()), "uniformity_median": float(np.median(met[:, 0])),
+            "frac_of_peak": terms / (ms_b * 1e-3) / 1e9 / _peak_gterm(torch, dev),
+            "clocks": clocks.summary()}
+    print(json.dumps(line))
     return 0
 
 

@@ -74,8 +74,33 @@ constexpr size_t batch_adj_smem() { return adj_smem_bytes(kBatchMaxD); }
 
 #define ASH_D_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12)
 
+// Out-of-line per-D tile bodies: each is register-allocated on its own, so
+// the batched kernels cost about as many registers as the single-hologram
+// kernel of the largest D instead of the sum of all inlined cases.
+template <int D>
+__device__ __noinline__ void batch_forward_tile(const BatchHolo* __restrict__ H, int tile, int sb, int se,
+                                                float* sC, float2* sRot) {
+  const HoloView v = H->v;
+  forward_tile<D, kBatchP>(v, kSrcPhase, H->phase, nullptr, tile, sb, se,
+                           H->partial + (size_t)tile * kBatchNW * 2 * v.g.N, sC, sRot);
+}
+
+template <int D>
+__device__ __noinline__ void batch_adjoint_tile(const BatchHolo* __restrict__ H, int tile, int sb, int se,
+                                                float2* slot, float* sC, float4* sY) {
+  const HoloView v = H->v;
+  float2 re2[kBatchP / 2], im2[kBatchP / 2];
+  adjoint_tile<D, kBatchP>(v, H->y, tile, sb, se, re2, im2, sC, sY);
+  AdjOut out{};
+  out.phase_out = H->phase;
+  out.epilogue = kEpiPhase;
+  adjoint_finish<kBatchP>(v, out, tile, sb == 0 && se == v.g.N, slot, re2, im2);
+}
+
+// DMAX: largest mode count of the batch; only cases up to DMAX are reachable,
+// so the kernel's register count is that of the largest case present.
+template <int DMAX>
 __global__ void ASH_BOUNDS(kBatchP) k_batch_forward(const BatchParams bp) {
-  constexpr int P = kBatchP;
   extern __shared__ float4 smem4[];
   float* sC = reinterpret_cast<float*>(smem4);
   float2* sRot = reinterpret_cast<float2*>(sC + kSpotChunk * cpair_stride(kBatchMaxD));
@@ -89,10 +114,9 @@ __global__ void ASH_BOUNDS(kBatchP) k_batch_forward(const BatchParams bp) {
     const long long ts = H->unit0 + (long long)tile * N;
     const long long ue = min(u1, ts + N);
     const int sb = (int)(u - ts), se = (int)(ue - ts);
-    float* ptile = H->partial + (size_t)tile * kBatchNW * 2 * N;
     switch (v.g.D) {
 #define FWD_CASE(DD) \
-  case DD: forward_tile<DD, P>(v, kSrcPhase, H->phase, nullptr, tile, sb, se, ptile, sC, sRot); break;
+  case DD: if constexpr (DD <= DMAX) batch_forward_tile<DD>(H, tile, sb, se, sC, sRot); break;
       ASH_D_CASES(FWD_CASE)
 #undef FWD_CASE
       default: break;
@@ -101,8 +125,8 @@ __global__ void ASH_BOUNDS(kBatchP) k_batch_forward(const BatchParams bp) {
   }
 }
 
+template <int DMAX>
 __global__ void ASH_BOUNDS(kBatchP) k_batch_adjoint(const BatchParams bp) {
-  constexpr int P = kBatchP;
   extern __shared__ float4 smem4[];
   float* sC = reinterpret_cast<float*>(smem4);
   float4* sY = reinterpret_cast<float4*>(sC + kSpotChunk * cpair_stride(kBatchMaxD));
@@ -116,22 +140,14 @@ __global__ void ASH_BOUNDS(kBatchP) k_batch_adjoint(const BatchParams bp) {
     const long long ts = H->unit0 + (long long)tile * N;
     const long long ue = min(u1, ts + N);
     const int sb = (int)(u - ts), se = (int)(ue - ts);
-    AdjOut out{};
-    out.phase_out = H->phase;
-    out.epilogue = kEpiPhase;
     float2* slot = bp.split + ((size_t)blockIdx.x * 2 + (u == u0 ? 0 : 1)) * kTilePix;
-    float2 re2[P / 2], im2[P / 2];
     switch (v.g.D) {
 #define ADJ_CASE(DD) \
-  case DD: adjoint_tile<DD, P>(v, H->y, tile, sb, se, re2, im2, sC, sY); break;
+  case DD: if constexpr (DD <= DMAX) batch_adjoint_tile<DD>(H, tile, sb, se, slot, sC, sY); break;
       ASH_D_CASES(ADJ_CASE)
 #undef ADJ_CASE
-      default:
-#pragma unroll
-        for (int q = 0; q < P / 2; ++q) re2[q] = im2[q] = make_float2(0.0f, 0.0f);
-        break;
+      default: break;
     }
-    adjoint_finish<P>(v, out, tile, sb == 0 && se == N, slot, re2, im2);
     u = ue;
   }
 }
@@ -173,6 +189,32 @@ ash_status fail(ash_status st, const std::string& msg) {
   return st;
 }
 
+// Max-D classes with their own kernel instantiations.
+constexpr int kDClasses[] = {4, 6, 8, 10, 11, 12};
+using BatchKernel = void (*)(BatchParams);
+
+BatchKernel fwd_kernel(int dmax) {
+  switch (dmax) {
+    case 4: return k_batch_forward<4>;
+    case 6: return k_batch_forward<6>;
+    case 8: return k_batch_forward<8>;
+    case 10: return k_batch_forward<10>;
+    case 11: return k_batch_forward<11>;
+    default: return k_batch_forward<12>;
+  }
+}
+
+BatchKernel adj_kernel(int dmax) {
+  switch (dmax) {
+    case 4: return k_batch_adjoint<4>;
+    case 6: return k_batch_adjoint<6>;
+    case 8: return k_batch_adjoint<8>;
+    case 10: return k_batch_adjoint<10>;
+    case 11: return k_batch_adjoint<11>;
+    default: return k_batch_adjoint<12>;
+  }
+}
+
 #define BCUDA(call)                                            \
   do {                                                         \
     cudaError_t e_ = (call);                                   \
@@ -190,6 +232,8 @@ struct ash_batch {
   int total_tiles = 0;
   int max_cols = 0;
   int slots = 0;           // resident CTAs on the device
+  int dclass = 12;         // kernel instantiation: max D of the batch, rounded up to a class
+  BatchKernel fwd = nullptr, adj = nullptr;
   int G = 0;               // CTAs of the transform launches
   bool split = false;
   float2* split_buf = nullptr;
@@ -235,7 +279,7 @@ BatchParams params_of(const ash_batch* b) {
 
 ash_status enqueue_batch_forward(ash_batch* b, cudaStream_t s) {
   const BatchParams p = params_of(b);
-  k_batch_forward<<<b->G, kBatchNT, batch_fwd_smem(), s>>>(p);
+  b->fwd<<<b->G, kBatchNT, batch_fwd_smem(), s>>>(p);
   BCUDA(cudaGetLastError());
   k_batch_reduce<<<dim3((b->max_cols + 31) / 32, b->count), dim3(32, 32), 0, s>>>(p);
   BCUDA(cudaGetLastError());
@@ -244,7 +288,7 @@ ash_status enqueue_batch_forward(ash_batch* b, cudaStream_t s) {
 
 ash_status enqueue_batch_adjoint(ash_batch* b, cudaStream_t s) {
   const BatchParams p = params_of(b);
-  k_batch_adjoint<<<b->G, kBatchNT, batch_adj_smem(), s>>>(p);
+  b->adj<<<b->G, kBatchNT, batch_adj_smem(), s>>>(p);
   BCUDA(cudaGetLastError());
   if (b->split) {
     k_batch_fixup<<<b->total_tiles, kBatchNT, 0, s>>>(p);
@@ -352,16 +396,25 @@ ash_status ash_batch_create(ash_batch** out, int count, const ash_hologram_desc*
     if (key.size() > 300) key = key.substr(0, 300);
   }
   b->key = key;
+  int dmax = 1;
+  for (int i = 0; i < count; ++i) dmax = descs[i].D > dmax ? descs[i].D : dmax;
+  for (int c : kDClasses)
+    if (c >= dmax) {
+      b->dclass = c;
+      break;
+    }
+  b->fwd = fwd_kernel(b->dclass);
+  b->adj = adj_kernel(b->dclass);
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_batch_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_fwd_smem())) !=
+  if ((e = cudaFuncSetAttribute(b->fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_fwd_smem())) !=
       cudaSuccess)
     return bail(status_cuda(e, "batch forward attribute"));
-  if ((e = cudaFuncSetAttribute(k_batch_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_adj_smem())) !=
+  if ((e = cudaFuncSetAttribute(b->adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_adj_smem())) !=
       cudaSuccess)
     return bail(status_cuda(e, "batch adjoint attribute"));
   int occ_f = 0, occ_a = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, k_batch_forward, kBatchNT, batch_fwd_smem());
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, k_batch_adjoint, kBatchNT, batch_adj_smem());
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, b->fwd, kBatchNT, batch_fwd_smem());
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, b->adj, kBatchNT, batch_adj_smem());
   int occ = occ_f < occ_a ? occ_f : occ_a;
   if (occ < 1) occ = 1;
   b->slots = sms * occ;

@@ -45,13 +45,13 @@ struct Geometry {
 #endif
 __host__ __device__ constexpr int pixels_per_thread(int D) { return D <= 12 ? ASH_P_SMALL_D : 4; }
 
-// Launch bounds of the pixel-stationary kernels: optionally ask the register
-// allocator for ASH_MIN_BLOCKS resident CTAs per SM.
-#ifdef ASH_MIN_BLOCKS
-#define ASH_BOUNDS(P) __launch_bounds__(kTilePix / (P), ASH_MIN_BLOCKS)
-#else
-#define ASH_BOUNDS(P) __launch_bounds__(kTilePix / (P))
+// Launch bounds of the pixel-stationary kernels: with P = 8 (128 threads)
+// ask the register allocator for 3 resident CTAs per SM (<= 170 registers,
+// which the D <= 12 kernels meet with at most a few bytes of spill).
+#ifndef ASH_MIN_BLOCKS
+#define ASH_MIN_BLOCKS 3
 #endif
+#define ASH_BOUNDS(P) __launch_bounds__(kTilePix / (P), ((P) == 8 ? ASH_MIN_BLOCKS : 1))
 
 // ---------------------------------------------------------------------------
 // Packed fp32x2 arithmetic (Blackwell FFMA2): one instruction, two lanes of
