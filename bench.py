@@ -307,7 +307,11 @@ def main():
     peak = sms * (MUFU_PER_CLK_PER_SM / MUFU_PER_TERM) * MAX_SM_MHZ * 1e6 / 1e9
     dom = "forward" if kms["forward"] >= kms["adjoint"] else "adjoint"
     P = 8 if p.D <= 12 else 4
-    kernel_names = {"forward": f"k_forward<D={p.D},P={P}> (pixel-stationary forward, warp transpose reduction)",
+    linfo = h.launch_info()
+    fwd_tc = bool(linfo["adjoint_variant"] & 4)
+    kernel_names = {"forward": (f"k_tc_forward<D={p.D}> (tcgen05 split-tf32 phase contraction into TMEM, "
+                                f"sincos + packed complex MAC, warp transpose reduction)") if fwd_tc else
+                               f"k_forward<D={p.D},P={P}> (pixel-stationary forward, warp transpose reduction)",
                     "adjoint": f"k_adjoint<D={p.D},P={P}> (pixel-stationary adjoint, arg epilogue)"}
     achieved = gterm[dom]
     roofline = {
@@ -328,7 +332,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(L.ash_wgs_launches(h.handle, iters)) * args.steps,
         "roofline": roofline,
-        "kernels": {"ms": kms, "gterm_s": gterm, "create_s": create_s},
+        "kernels": {"ms": kms, "gterm_s": gterm, "create_s": create_s, "launch_info": linfo},
         "clocks": clk,
     }
     if args.config != "c2":

@@ -210,6 +210,28 @@ ash_status ash_grad(ash_hologram *h, const float *phase, const float *grad_E, fl
                     float *dcoeff, void *stream);
 
 /*
+ * Launch shapes chosen for the handle, written to the host array out[8]:
+ *   {CTAs of the FMA-pipe transform launches, their resident CTAs per SM
+ *    (forward), (adjoint), CTAs of the tensor-core adjoint (0 if not
+ *    available), its resident CTAs per SM, split flags (bit 0: FMA schedule
+ *    splits tiles, bit 1: tensor-core schedule splits sub-tiles), kernels in
+ *    use (adjoint: 1 FMA or 2 tensor core, plus 4 if the forward uses the
+ *    tensor core), pixels per thread}.
+ */
+ash_status ash_hologram_launch_info(const ash_hologram *h, int *out);
+
+/*
+ * Kernel variant of the forward and adjoint transforms: 0 = automatic
+ * (the faster measured family per transform: tensor-core forward for
+ * D <= 10, FMA-pipe adjoint), 1 = FMA-pipe kernels, 2 = tensor-core kernels
+ * (ASH_ERR_UNSUPPORTED if D > 12). Both
+ * compute the same sums; the tensor-core variant forms the phases
+ * C_n . dZ_m with split-tf32 tcgen05 MMAs into tensor memory. Drops the
+ * handle's captured graphs.
+ */
+ash_status ash_set_kernel_variant(ash_hologram *h, int variant);
+
+/*
  * Number of kernel launches one ash_wgs_iterate call with `iters` iterations
  * enqueues (transform kernels, reductions, fix-ups, spot updates, metrics);
  * -1 on a NULL handle.

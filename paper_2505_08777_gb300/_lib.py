@@ -38,6 +38,8 @@ SIGNATURES = {
     "ash_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "ash_hologram_check": (c_int, [c_void_p, c_void_p]),
     "ash_wgs_launches": (c_int, [c_void_p, c_int]),
+    "ash_set_kernel_variant": (c_int, [c_void_p, c_int]),
+    "ash_hologram_launch_info": (c_int, [c_void_p, c_int_p]),
     "ash_profile": (c_int, [c_void_p, c_void_p, c_void_p, c_float_p, c_void_p]),
     "ash_batch_create": (c_int, [ctypes.POINTER(c_void_p), c_int, c_void_p, c_void_p]),
     "ash_batch_destroy": (None, [c_void_p]),

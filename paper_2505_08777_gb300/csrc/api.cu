@@ -13,6 +13,7 @@
 #include "basis_host.h"
 #include "handle.h"
 #include "launch.h"
+#include "tc_kernels.cuh"
 
 using namespace ash;
 
@@ -134,6 +135,49 @@ cudaError_t launch_adjoint(int D, const AdjParams& p, int grid, cudaStream_t s) 
   return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_tc_adjoint(int D, const TcAdjParams& p, int grid, cudaStream_t s) {
+  switch (range_of(D)) {
+    case 0: return launch_tc_adjoint_r0(D, p, grid, s);
+    case 1: return launch_tc_adjoint_r1(D, p, grid, s);
+    case 2: return launch_tc_adjoint_r2(D, p, grid, s);
+    case 3: return launch_tc_adjoint_r3(D, p, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_tc_forward(int D, const TcFwdParams& p, int grid, cudaStream_t s) {
+  switch (range_of(D)) {
+    case 0: return launch_tc_forward_r0(D, p, grid, s);
+    case 1: return launch_tc_forward_r1(D, p, grid, s);
+    case 2: return launch_tc_forward_r2(D, p, grid, s);
+    case 3: return launch_tc_forward_r3(D, p, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Kernel choice per transform. Automatic: the tensor-core forward where its
+// K fits one 128-byte atom (D <= 10) -- it was measured faster than the FMA
+// forward there -- and the FMA-pipe adjoint (measured faster than the
+// tensor-core adjoint at every D). Variant 1 / 2 force one family.
+bool use_tc(const ash_hologram* h) { return h->tc_ok && h->variant == 2; }
+bool use_tc_forward(const ash_hologram* h) {
+  if (!h->tc_ok || h->variant == 1) return false;
+  return h->variant == 2 || tc_kp(h->g.D) == 32;
+}
+int tc_rows(const ash_hologram* h) { return h->g.T * tc_sub(h->g.D) * 4; }
+
+cudaError_t enqueue_split_coeff(ash_hologram* h, cudaStream_t s) {
+  if (!h->tc_ok) return cudaSuccess;
+  const int KP = tc_kp(h->g.D);
+  const long long n = (long long)h->g.N * KP;
+  k_tc_split_coeff<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(h->coeff, h->g.N, h->g.D, KP, h->cz);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long long nr = (long long)h->g.N * h->g.T;
+  k_tile_rotations<<<(unsigned)((nr + 255) / 256), 256, 0, s>>>(h->coeff, h->anchors, h->g.N, h->g.D, h->g.T, h->rot);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gradc(int D, const GradCParams& p, dim3 grid, cudaStream_t s) {
   switch (range_of(D)) {
     case 0: return launch_gradc_r0(D, p, grid, s);
@@ -147,6 +191,25 @@ cudaError_t launch_gradc(int D, const GradCParams& p, dim3 grid, cudaStream_t s)
 // forward transform into E (device complex [N]).
 ash_status enqueue_forward(ash_hologram* h, int source, const float* phase, const float2* field, float2* E,
                            cudaStream_t s) {
+  if (use_tc_forward(h)) {
+    TcFwdParams tp{};
+    tp.v = view_of(h);
+    tp.sched = h->tsched;
+    tp.cz = h->cz;
+    tp.rot = h->rot;
+    tp.phase = phase;
+    tp.field = field;
+    tp.source = source;
+    tp.partial = h->partial;
+    tp.err = h->err_word;
+    cudaError_t e = launch_tc_forward(h->g.D, tp, h->tsched.G, s);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core forward launch");
+    const int cols = 2 * h->g.N;
+    k_col_reduce<<<(cols + 31) / 32, dim3(32, 32), 0, s>>>(h->partial, tc_rows(h), cols, reinterpret_cast<float*>(E));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "forward reduce launch");
+    return ASH_OK;
+  }
   FwdParams p{};
   p.v = view_of(h);
   p.phase = phase;
@@ -173,6 +236,25 @@ ash_status enqueue_adjoint(ash_hologram* h, const float2* y, float2* g_out, floa
   p.out.phase_in = phase_in;
   p.out.dphase = dphase;
   p.out.epilogue = epilogue;
+  if (use_tc(h)) {
+    TcAdjParams tp{};
+    tp.v = p.v;
+    tp.sched = h->tsched;
+    tp.cz = h->cz;
+    tp.rot = h->rot;
+    tp.y = y;
+    tp.out = p.out;
+    tp.split = h->split;
+    tp.err = h->err_word;
+    cudaError_t e = launch_tc_adjoint(h->g.D, tp, h->tsched.G, s);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core adjoint launch");
+    if (h->tsplit) {
+      k_tc_adjoint_fixup<<<h->g.T * tc_sub(h->g.D), kTcThreads, 0, s>>>(tp, tc_mb(h->g.D));
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return cuda_fail(e, "tensor-core adjoint fix-up launch");
+    }
+    return ASH_OK;
+  }
   p.sched = h->sched;
   p.split = h->split;
   cudaError_t e = launch_adjoint(h->g.D, p, h->sched.G, s);
@@ -311,6 +393,22 @@ ash_status ash_hologram_create(ash_hologram** out, int nx, int ny, const float* 
       if (h->sched.begin(b) % N != 0) h->split_tiles = true;
   }
   h->fwd_rows = g.T * (g.NT / 32);
+  if (D <= 12 && h->li.tc_adj_ctas_per_sm > 0 && h->li.tc_fwd_ctas_per_sm > 0) {
+    // tensor-core adjoint: units (sub-tile, spot) with sub-tiles of 128 x MB pixels
+    h->tc_ok = true;
+    const long long W = (long long)g.T * tc_sub(D) * N;
+    const long long umin = N < 256 ? N : 256;
+    const int per_sm = h->li.tc_adj_ctas_per_sm < h->li.tc_fwd_ctas_per_sm ? h->li.tc_adj_ctas_per_sm
+                                                                           : h->li.tc_fwd_ctas_per_sm;
+    long long G = (long long)sms * per_sm;
+    if (G > W / umin) G = W / umin;
+    if (G < 1) G = 1;
+    if (G > h->sched.G) G = h->sched.G;   // the split scratch is sized for sched.G CTAs
+    h->tsched.W = W;
+    h->tsched.G = (int)G;
+    for (int b = 1; b < h->tsched.G; ++b)
+      if (h->tsched.begin(b) % N != 0) h->tsplit = true;
+  }
   h->gradc_gy = (N + kGradThreads * kGradSpots - 1) / (kGradThreads * kGradSpots);
   {
     const int slots = sms * (h->li.gradc_ctas_per_sm > 0 ? h->li.gradc_ctas_per_sm : 1);
@@ -326,8 +424,13 @@ ash_status ash_hologram_create(ash_hologram** out, int nx, int ny, const float* 
   if ((st = ws(h, &h->amp_img, pix)) != ASH_OK) return fail(st);
   if ((st = ws(h, &h->anchors, (size_t)g.T * D)) != ASH_OK) return fail(st);
   if ((st = ws(h, &h->coeff, (size_t)N * D)) != ASH_OK) return fail(st);
-  if ((st = ws(h, &h->partial, (size_t)h->fwd_rows * 2 * N)) != ASH_OK) return fail(st);
+  {
+    const size_t rows = h->tc_ok && tc_rows(h) > h->fwd_rows ? (size_t)tc_rows(h) : (size_t)h->fwd_rows;
+    if ((st = ws(h, &h->partial, rows * 2 * N)) != ASH_OK) return fail(st);
+  }
   if ((st = ws(h, &h->split, (size_t)h->sched.G * 2 * kTilePix)) != ASH_OK) return fail(st);
+  if (h->tc_ok && (st = ws(h, &h->cz, (size_t)N * tc_kp(D))) != ASH_OK) return fail(st);
+  if (h->tc_ok && (st = ws(h, &h->rot, (size_t)N * g.T)) != ASH_OK) return fail(st);
   if ((st = ws(h, &h->gradc_partial, (size_t)h->gradc_gx * N * D)) != ASH_OK) return fail(st);
   if ((st = ws(h, &h->E, (size_t)N)) != ASH_OK) return fail(st);
   if ((st = ws(h, &h->y, (size_t)N)) != ASH_OK) return fail(st);
@@ -366,6 +469,7 @@ ash_status ash_hologram_create(ash_hologram** out, int nx, int ny, const float* 
   bp.anchors = h->anchors;
   k_basis<<<g.T, g.NT, 0, s>>>(bp);
   CREATE_CUDA(cudaGetLastError());
+  CREATE_CUDA(enqueue_split_coeff(h, s));
   k_amp_image<<<g.T, g.NT, 0, s>>>(g, amp, h->amp_img);
   CREATE_CUDA(cudaGetLastError());
   k_sum_sq<<<1, 1024, 0, s>>>(amp, M, h->sum_a2);
@@ -401,6 +505,7 @@ ash_status ash_set_coefficients(ash_hologram* h, const float* coeff, void* strea
   if (injected_failure()) return set_error(ASH_ERR_INJECTED, "injected failure");
   ASH_CUDA(cudaMemcpyAsync(h->coeff, coeff, (size_t)h->g.N * h->g.D * sizeof(float), cudaMemcpyDeviceToDevice,
                            as_stream(stream)));
+  ASH_CUDA(enqueue_split_coeff(h, as_stream(stream)));
   return ASH_OK;
 }
 
@@ -511,10 +616,34 @@ ash_status ash_grad(ash_hologram* h, const float* phase, const float* grad_E, fl
   return ASH_OK;
 }
 
+ash_status ash_hologram_launch_info(const ash_hologram* h, int* out) {
+  if (!h || !out) return set_error(ASH_ERR_INVALID_ARG, "NULL argument");
+  out[0] = h->sched.G;
+  out[1] = h->li.fwd_ctas_per_sm;
+  out[2] = h->li.adj_ctas_per_sm;
+  out[3] = h->tc_ok ? h->tsched.G : 0;
+  out[4] = h->li.tc_adj_ctas_per_sm < h->li.tc_fwd_ctas_per_sm ? h->li.tc_adj_ctas_per_sm : h->li.tc_fwd_ctas_per_sm;
+  out[5] = (h->split_tiles ? 1 : 0) | (h->tsplit ? 2 : 0);
+  out[6] = (use_tc(h) ? 2 : 1) | (use_tc_forward(h) ? 4 : 0);
+  out[7] = h->g.P;
+  return ASH_OK;
+}
+
+ash_status ash_set_kernel_variant(ash_hologram* h, int variant) {
+  if (!h || variant < 0 || variant > 2) return set_error(ASH_ERR_INVALID_ARG, "variant must be 0, 1 or 2");
+  if (variant == 2 && !h->tc_ok)
+    return set_error(ASH_ERR_UNSUPPORTED, "tensor-core kernels need D <= 12 (D = %d)", h->g.D);
+  h->variant = variant;
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  h->graphs.clear();
+  return ASH_OK;
+}
+
 int ash_wgs_launches(const ash_hologram* h, int iters) {
   if (!h || iters < 0) return -1;
   const int fwd = 2;                              // transform kernel + reduction
-  const int adj = h->split_tiles ? 2 : 1;         // transform kernel (+ fix-up)
+  const bool split = use_tc(h) ? h->tsplit : h->split_tiles;
+  const int adj = split ? 2 : 1;                  // transform kernel (+ fix-up)
   return iters * (fwd + 1 + adj) + fwd + 1;       // + final forward and metrics
 }
 
@@ -536,12 +665,21 @@ ash_status ash_profile(ash_hologram* h, const float* phase, const float* y, floa
   fp.source = kSrcPhase;
   fp.partial = h->partial;
   const int cols = 2 * h->g.N;
+  TcFwdParams tf{};
+  tf.v = fp.v;
+  tf.sched = h->tsched;
+  tf.cz = h->cz;
+  tf.rot = h->rot;
+  tf.phase = phase;
+  tf.source = kSrcPhase;
+  tf.partial = h->partial;
+  tf.err = h->err_word;
   cudaEventRecord(ev[0], s);
-  e = launch_forward(h->g.D, fp, h->sched.G, s);
+  e = use_tc_forward(h) ? launch_tc_forward(h->g.D, tf, h->tsched.G, s) : launch_forward(h->g.D, fp, h->sched.G, s);
   cudaEventRecord(ev[1], s);
   if (e == cudaSuccess) {
     cudaEventRecord(ev[2], s);
-    k_col_reduce<<<(cols + 31) / 32, dim3(32, 32), 0, s>>>(h->partial, h->fwd_rows, cols,
+    k_col_reduce<<<(cols + 31) / 32, dim3(32, 32), 0, s>>>(h->partial, use_tc_forward(h) ? tc_rows(h) : h->fwd_rows, cols,
                                                             reinterpret_cast<float*>(h->E));
     e = cudaGetLastError();
     cudaEventRecord(ev[3], s);
@@ -554,14 +692,26 @@ ash_status ash_profile(ash_hologram* h, const float* phase, const float* y, floa
   ap.y = y2;
   ap.out.phase_out = h->wgs_phase;
   ap.out.epilogue = kEpiPhase;
+  TcAdjParams tp{};
+  tp.v = ap.v;
+  tp.sched = h->tsched;
+  tp.cz = h->cz;
+  tp.rot = h->rot;
+  tp.y = y2;
+  tp.out = ap.out;
+  tp.split = h->split;
+  tp.err = h->err_word;
   if (e == cudaSuccess) {
     cudaEventRecord(ev[4], s);
-    e = launch_adjoint(h->g.D, ap, h->sched.G, s);
+    e = use_tc(h) ? launch_tc_adjoint(h->g.D, tp, h->tsched.G, s) : launch_adjoint(h->g.D, ap, h->sched.G, s);
     cudaEventRecord(ev[5], s);
   }
   if (e == cudaSuccess) {
     cudaEventRecord(ev[6], s);
-    if (h->split_tiles) {
+    if (use_tc(h) && h->tsplit) {
+      k_tc_adjoint_fixup<<<h->g.T * tc_sub(h->g.D), kTcThreads, 0, s>>>(tp, tc_mb(h->g.D));
+      e = cudaGetLastError();
+    } else if (!use_tc(h) && h->split_tiles) {
       k_adjoint_fixup<<<h->g.T, h->g.NT, 0, s>>>(ap);
       e = cudaGetLastError();
     }

@@ -27,6 +27,13 @@ struct ash_hologram {
   float2* anchors = nullptr;
   float* coeff = nullptr;
   float* partial = nullptr;
+  // tensor-core path (D <= 12): split coefficients, sub-tile schedule
+  int variant = 0;              // 0 auto, 1 FMA-pipe kernels, 2 tensor-core kernels
+  bool tc_ok = false;
+  ash::Schedule tsched{};
+  bool tsplit = false;
+  float* cz = nullptr;
+  float2* rot = nullptr;        // [T][N] per-(tile, spot) anchor phase rotations
   float2* split = nullptr;
   float* gradc_partial = nullptr;
   float2* E = nullptr;

@@ -160,6 +160,17 @@ class Hologram:
                    "ash_grad")
         return dph, dC
 
+    def launch_info(self) -> dict:
+        out = (ctypes.c_int * 8)()
+        _lib.check(self._lib.ash_hologram_launch_info(self._h, out), "ash_hologram_launch_info")
+        keys = ["grid", "fwd_ctas_per_sm", "adj_ctas_per_sm", "tc_grid", "tc_ctas_per_sm", "split_flags",
+                "adjoint_variant", "pixels_per_thread"]
+        return dict(zip(keys, list(out)))
+
+    def set_variant(self, variant: int):
+        """0 = automatic, 1 = FMA-pipe kernels, 2 = tensor-core phase contraction (D <= 12)."""
+        _lib.check(self._lib.ash_set_kernel_variant(self._h, int(variant)), "ash_set_kernel_variant")
+
     def check(self, stream=None):
         _lib.check(self._lib.ash_hologram_check(self._h, _stream_ptr(stream)), "ash_hologram_check")
 

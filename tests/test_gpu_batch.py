@@ -61,6 +61,7 @@ def test_batch_one_iteration_equals_single_path():
     b.wgs(ph, w, T, 1)
     for k, p in enumerate(ps):
         h = Hologram(torch.from_numpy(p.amp).cuda(), torch.from_numpy(p.coeff).cuda(), noll=p.noll)
+        h.set_variant(1)   # the batched kernels use the FMA-pipe arithmetic: same forward sums, bit for bit
         ph1 = torch.from_numpy(p.phase0).cuda().clone()
         w1 = torch.from_numpy(p.target).cuda().clone()
         h.wgs(ph1, w1, T[k], 1)

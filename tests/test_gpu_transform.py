@@ -168,3 +168,44 @@ def test_full_size_sampled(make):
     pix = np.sort(rng.choice(p.M, size=4096, replace=False))
     g_ref = transform.adjoint(y.astype(np.complex128), p.coeff.astype(np.float64), basis_at(p, pix))
     assert_close(g[pix], g_ref, what="adjoint sampled")
+
+
+@pytest.mark.parametrize("nx,ny,N,noll,dmax", [(97, 61, 37, list(range(2, 12)), 5.0), (160, 128, 300, list(range(2, 13)), 20.0),
+                                                (64, 40, 17, [2, 3, 4, 5, 6], 10.0), (33, 70, 5, [4], 20.0),
+                                                (256, 256, 400, list(range(2, 12)), 8.0)])
+def test_adjoint_kernel_variants_agree_with_oracle(nx, ny, N, noll, dmax):
+    """FMA-pipe adjoint (variant 1) and tensor-core adjoint (variant 2, split-tf32
+    phase contraction) against the oracle, on the same inputs."""
+    p = random_problem(200 + nx + N, nx, ny, N, noll, defocus_max=dmax)
+    h = _holo(p)
+    Z, C, _ = oracle_inputs(p)
+    rng = np.random.default_rng(N)
+    y = _rand_complex(rng, N)
+    g_ref = transform.adjoint(y.astype(np.complex128), C, Z)
+    errs = {}
+    for variant in (1, 2):
+        h.set_variant(variant)
+        g, ph = h.adjoint(torch.from_numpy(y).cuda(), want_field=True, want_phase=True)
+        errs[variant] = assert_close(g.cpu().numpy(), g_ref, what=f"adjoint variant {variant}")
+    print("adjoint normwise/max-guard errors by variant:", errs)
+
+
+@pytest.mark.parametrize("nx,ny,N,noll,dmax", [(97, 61, 37, list(range(2, 12)), 5.0), (160, 128, 300, list(range(2, 13)), 20.0),
+                                                (64, 40, 17, [2, 3, 4, 5, 6], 10.0), (33, 70, 5, [4], 20.0),
+                                                (256, 256, 400, list(range(2, 12)), 8.0)])
+def test_forward_kernel_variants_agree_with_oracle(nx, ny, N, noll, dmax):
+    """FMA-pipe forward (variant 1) and tensor-core forward (variant 2) against
+    the oracle, for phase-only and general complex nearfields."""
+    p = random_problem(300 + nx + N, nx, ny, N, noll, defocus_max=dmax)
+    h = _holo(p)
+    Z, C, A = oracle_inputs(p)
+    rng = np.random.default_rng(N + 1)
+    x = _rand_complex(rng, (p.ny, p.nx))
+    E_ref = transform.forward(transform.field(A, p.phase0), C, Z)
+    Ef_ref = transform.forward(x.ravel().astype(np.complex128), C, Z)
+    for variant in (1, 2):
+        h.set_variant(variant)
+        E = h.forward(torch.from_numpy(p.phase0).cuda()).cpu().numpy()
+        assert_close(E, E_ref, what=f"forward variant {variant}")
+        Ef = h.forward_field(torch.from_numpy(x).cuda()).cpu().numpy()
+        assert_close(Ef, Ef_ref, what=f"forward_field variant {variant}")
