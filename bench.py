@@ -34,6 +34,10 @@ L2_FLUSH_BYTES = 256 << 20
 MUFU_PER_CLK_PER_SM = 16          # measured: sin.approx / cos.approx throughput per SM per clock
 MUFU_PER_TERM = 2                 # one sin and one cos per term
 MAX_SM_MHZ = 2070.0
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
+# ncu capture of the named kernel on this workload; see profiles/. Reported as
+# roofline.traffic only for the kernel build these counters were taken on.
+NCU_TRAFFIC_BYTES = {"k_tc_forward<D=10>": 54.072064e6 + 2.536192e6, "k_adjoint<D=10,P=8>": 42.085376e6 + 0.015872e6}
 
 
 WORKLOAD_TEXT = {
@@ -320,7 +324,8 @@ def main():
         "peak_basis": f"MUFU pipe: {MUFU_PER_CLK_PER_SM} sin/cos per clk per SM (measured), 2 per term, "
                       f"{sms} SMs x {MAX_SM_MHZ:.0f} MHz max clock",
         "algorithmic_per_launch": f"N*M = {NM} terms",
-        "traffic": None,
+        "traffic": next((v for k, v in NCU_TRAFFIC_BYTES.items() if kernel_names[dom].startswith(k.split("<")[0])
+                         and f"D={p.D}" in kernel_names[dom] and args.config == "c2"), None),
         "frac_at_sampled_clock": (achieved / (peak * clk["sm_mhz"] / MAX_SM_MHZ)) if clk.get("sm_mhz") else None,
     }
     line = {
