@@ -245,14 +245,16 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_tc_adjoint(const TcAdjParams 
           yi2[q] = make_float2(a.z, a.w);
           nyi2[q] = make_float2(bq.x, bq.y);
         }
+        uint32_t xr[MB][16];
+#pragma unroll
+        for (int b = 0; b < MB; ++b) tmem_ld16_nowait(tmem + tlane + (uint32_t)(buf * MB * S + b * S), xr[b]);
+        tmem_wait();
 #pragma unroll
         for (int b = 0; b < MB; ++b) {
-          float x[16];
-          tmem_ld16(tmem + tlane + (uint32_t)(buf * MB * S + b * S), x);
 #pragma unroll
           for (int q = 0; q < S / 2; ++q) {
             float2 sn, cs;
-            sincos2(make_float2(x[2 * q], x[2 * q + 1]), sn, cs);
+            sincos2(make_float2(__uint_as_float(xr[b][2 * q]), __uint_as_float(xr[b][2 * q + 1])), sn, cs);
             re2[b] = fma2(yr2[q], cs, re2[b]);
             re2[b] = fma2(nyi2[q], sn, re2[b]);
             im2[b] = fma2(yi2[q], cs, im2[b]);
@@ -330,7 +332,10 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_tc_forward(const TcFwdParams 
   const int sf = (int)(u0 / N), sl = (int)((u1 - 1) / N);
 
   float4 bv[BV];
-  auto fetch = [&](int n0, int se) {
+  float2 rot_next = make_float2(0.0f, 0.0f), rot_cur = make_float2(0.0f, 0.0f);
+  // loads of chunk (n0 .. n0 + S) issued one iteration ahead of their use:
+  // B rows (split coefficients) and this lane's spot rotation
+  auto fetch = [&](int tile, int n0, int se) {
 #pragma unroll
     for (int q = 0; q < BV; ++q) {
       const int e = t + q * kTcThreads;
@@ -339,6 +344,8 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_tc_forward(const TcFwdParams 
       bv[q] = n < se ? __ldg(reinterpret_cast<const float4*>(p.cz + (size_t)n * KP + atom * 32 + 4 * j))
                      : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
+    const int n = n0 + (lane >> 1);
+    rot_next = n < se ? __ldg(p.rot + (size_t)tile * N + n) : make_float2(1.0f, 0.0f);
   };
   auto put = [&](int buf) {
 #pragma unroll
@@ -358,7 +365,7 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_tc_forward(const TcFwdParams 
     const int tx = tile % G.tiles_x, ty = tile / G.tiles_x;
     const int i = tx * kTileX + lane;
 
-    fetch(sb, se);
+    fetch(tile, sb, se);
     // A rows and this thread's nearfield values (duplicated for packed FMAs)
     float2 frr[MB], fii[MB], nfrr[MB];
     {
@@ -416,11 +423,11 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_tc_forward(const TcFwdParams 
       }
     }
     put(0);
+    rot_cur = rot_next;
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     float* prow = p.partial + ((size_t)st * 4 + w) * 2 * N;
-    const float2* rot = p.rot + (size_t)tile * N;
 
     for (int c = 0; c <= nch; ++c) {
       if (c < nch && t == 0) {
@@ -437,23 +444,27 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_tc_forward(const TcFwdParams 
         }
         umma_commit(&mbar[buf]);
       }
-      if (c + 1 < nch) fetch(sb + (c + 1) * S, se);
+      // rot_cur belongs to chunk c - 1 (consumed below); chunk c's is in rot_next
+      const float2 rot_use = rot_cur;
+      rot_cur = rot_next;
+      if (c + 1 < nch) fetch(tile, sb + (c + 1) * S, se);
       if (c >= 1) {
         const int buf = (c - 1) & 1, n0 = sb + (c - 1) * S;
         ok = mbar_wait(&mbar[buf], (parity >> buf) & 1u, kTcWaitPolls) && ok;
         parity ^= 1u << buf;
         tc_fence_after();
+        uint32_t xr[MB][16];
+#pragma unroll
+        for (int b = 0; b < MB; ++b) tmem_ld16_nowait(tmem + tlane + (uint32_t)(buf * MB * S + b * S), xr[b]);
+        tmem_wait();
         float2 re2[S / 2], im2[S / 2];
 #pragma unroll
-        for (int q = 0; q < S / 2; ++q) re2[q] = im2[q] = make_float2(0.0f, 0.0f);
+        for (int q = 0; q < S / 2; ++q) {
+          re2[q] = im2[q] = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int b = 0; b < MB; ++b) {
-          float x[16];
-          tmem_ld16(tmem + tlane + (uint32_t)(buf * MB * S + b * S), x);
-#pragma unroll
-          for (int q = 0; q < S / 2; ++q) {
+          for (int b = 0; b < MB; ++b) {
             float2 sn, cs;
-            sincos2(make_float2(x[2 * q], x[2 * q + 1]), sn, cs);
+            sincos2(make_float2(__uint_as_float(xr[b][2 * q]), __uint_as_float(xr[b][2 * q + 1])), sn, cs);
             // f exp(-i x) = (fr cs + fi sn) + i (fi cs - fr sn)
             re2[q] = fma2(frr[b], cs, re2[q]);
             re2[q] = fma2(fii[b], sn, re2[q]);
@@ -471,14 +482,13 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_tc_forward(const TcFwdParams 
         }
         const float v = warp_transpose_reduce32(acc, lane);
         const float other = __shfl_xor_sync(kFull, v, 1);
-        const int s = lane >> 1;
         const bool is_im = (lane & 1) != 0;
-        const int n = n0 + s;
+        const int n = n0 + (lane >> 1);
         if (n < se) {
           const float re = is_im ? other : v;
           const float im = is_im ? v : other;
-          const float2 r = __ldg(rot + n);   // exp(+i 2 pi base): multiply by its conjugate
-          prow[2 * n + (lane & 1)] = is_im ? fmaf(im, r.x, -re * r.y) : fmaf(re, r.x, im * r.y);
+          // exp(+i 2 pi base) was loaded one iteration ago: multiply by its conjugate
+          prow[2 * n + (lane & 1)] = is_im ? fmaf(im, rot_use.x, -re * rot_use.y) : fmaf(re, rot_use.x, im * rot_use.y);
         }
       }
       if (c + 1 < nch) put((c + 1) & 1);
