@@ -37,7 +37,7 @@ MAX_SM_MHZ = 2070.0
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
 # ncu capture of the named kernel on this workload; see profiles/. Reported as
 # roofline.traffic only for the kernel build these counters were taken on.
-NCU_TRAFFIC_BYTES = {"k_tc_forward<D=10>": 54.072064e6 + 2.536192e6, "k_adjoint<D=10,P=8>": 42.085376e6 + 0.015872e6}
+NCU_TRAFFIC_BYTES = {}
 
 
 WORKLOAD_TEXT = {
@@ -313,10 +313,14 @@ def main():
     P = 8 if p.D <= 12 else 4
     linfo = h.launch_info()
     fwd_tc = bool(linfo["adjoint_variant"] & 4)
-    kernel_names = {"forward": (f"k_tc_forward<D={p.D}> (tcgen05 split-tf32 phase contraction into TMEM, "
-                                f"sincos + packed complex MAC, warp transpose reduction)") if fwd_tc else
+    adj_tc = bool(linfo["adjoint_variant"] & 2)
+    NA = 1 if 3 * p.D <= 32 else 2
+    kernel_names = {"forward": (f"k_tc_forward<{NA}> (spot-stationary: tcgen05 split-tf32 MMA of 128 spots x 64 "
+                                f"pixels into TMEM, sincos + packed complex MAC)") if fwd_tc else
                                f"k_forward<D={p.D},P={P}> (pixel-stationary forward, warp transpose reduction)",
-                    "adjoint": f"k_adjoint<D={p.D},P={P}> (pixel-stationary adjoint, arg epilogue)"}
+                    "adjoint": (f"k_tc_adjoint<{NA}> (pixel-stationary: tcgen05 split-tf32 MMA of 128 pixels x 64 "
+                                f"spots into TMEM, sincos + packed complex MAC, arg epilogue)") if adj_tc else
+                               f"k_adjoint<D={p.D},P={P}> (pixel-stationary adjoint, arg epilogue)"}
     achieved = gterm[dom]
     roofline = {
         "bound": "alu", "kernel": kernel_names[dom],
@@ -324,8 +328,7 @@ def main():
         "peak_basis": f"MUFU pipe: {MUFU_PER_CLK_PER_SM} sin/cos per clk per SM (measured), 2 per term, "
                       f"{sms} SMs x {MAX_SM_MHZ:.0f} MHz max clock",
         "algorithmic_per_launch": f"N*M = {NM} terms",
-        "traffic": next((v for k, v in NCU_TRAFFIC_BYTES.items() if kernel_names[dom].startswith(k.split("<")[0])
-                         and f"D={p.D}" in kernel_names[dom] and args.config == "c2"), None),
+        "traffic": NCU_TRAFFIC_BYTES.get(kernel_names[dom].split(" ")[0]) if args.config == "c2" else None,
         "frac_at_sampled_clock": (achieved / (peak * clk["sm_mhz"] / MAX_SM_MHZ)) if clk.get("sm_mhz") else None,
     }
     line = {

@@ -13,7 +13,7 @@
 #include "basis_host.h"
 #include "handle.h"
 #include "launch.h"
-#include "tc_kernels.cuh"
+#include "tc_launch.h"
 
 using namespace ash;
 
@@ -135,47 +135,61 @@ cudaError_t launch_adjoint(int D, const AdjParams& p, int grid, cudaStream_t s) 
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_tc_adjoint(int D, const TcAdjParams& p, int grid, cudaStream_t s) {
-  switch (range_of(D)) {
-    case 0: return launch_tc_adjoint_r0(D, p, grid, s);
-    case 1: return launch_tc_adjoint_r1(D, p, grid, s);
-    case 2: return launch_tc_adjoint_r2(D, p, grid, s);
-    case 3: return launch_tc_adjoint_r3(D, p, grid, s);
-  }
-  return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_tc_forward(int D, const TcFwdParams& p, int grid, cudaStream_t s) {
-  switch (range_of(D)) {
-    case 0: return launch_tc_forward_r0(D, p, grid, s);
-    case 1: return launch_tc_forward_r1(D, p, grid, s);
-    case 2: return launch_tc_forward_r2(D, p, grid, s);
-    case 3: return launch_tc_forward_r3(D, p, grid, s);
-  }
-  return cudaErrorInvalidValue;
-}
-
-// Kernel choice per transform. Automatic: the tensor-core forward where its
-// K fits one 128-byte atom (D <= 10) -- it was measured faster than the FMA
-// forward there -- and the FMA-pipe adjoint (measured faster than the
-// tensor-core adjoint at every D). Variant 1 / 2 force one family.
-bool use_tc(const ash_hologram* h) { return h->tc_ok && h->variant == 2; }
-bool use_tc_forward(const ash_hologram* h) {
+// Kernel family per transform. Automatic: the tensor-core kernels where an
+// operand row fits one 128-byte K-atom (D <= 10) and there are enough spots
+// for their chunks of 64 (measured on GB300: the tensor-core forward is
+// faster from N = 64, the tensor-core adjoint from N = 256 -- below that a
+// partial last spot chunk costs it more than the FMA kernel); the FMA-pipe
+// kernels otherwise. Variant 1 / 2 force one family (2 needs D <= 21).
+constexpr int kTcFwdMinSpots = 64, kTcAdjMinSpots = 256;
+bool use_tc_fwd(const ash_hologram* h) {
   if (!h->tc_ok || h->variant == 1) return false;
-  return h->variant == 2 || tc_kp(h->g.D) == 32;
+  return h->variant == 2 || (h->tc_na == 1 && h->g.N >= kTcFwdMinSpots);
 }
-int tc_rows(const ash_hologram* h) { return h->g.T * tc_sub(h->g.D) * 4; }
+bool use_tc_adj(const ash_hologram* h) {
+  if (!h->tc_ok || h->variant == 1) return false;
+  return h->variant == 2 || (h->tc_na == 1 && h->g.N >= kTcAdjMinSpots);
+}
 
-cudaError_t enqueue_split_coeff(ash_hologram* h, cudaStream_t s) {
+// Source of a forward: a phase or a complex field in user layout, or the
+// tc-layout nearfield the previous tensor-core adjoint wrote (kEpiFimg).
+constexpr int kSrcImg = 2;
+
+cudaError_t enqueue_tc_coeff(ash_hologram* h, cudaStream_t s) {
   if (!h->tc_ok) return cudaSuccess;
-  const int KP = tc_kp(h->g.D);
-  const long long n = (long long)h->g.N * KP;
-  k_tc_split_coeff<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(h->coeff, h->g.N, h->g.D, KP, h->cz);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  const long long nr = (long long)h->g.N * h->g.T;
-  k_tile_rotations<<<(unsigned)((nr + 255) / 256), 256, 0, s>>>(h->coeff, h->anchors, h->g.N, h->g.D, h->g.T, h->rot);
-  return cudaGetLastError();
+  return tc_build_coeff(h->g, h->coeff, h->anchors, h->czs, h->rot, s);
+}
+
+TcFwdParams tc_fwd_params(const ash_hologram* h, float2* E) {
+  TcFwdParams p{};
+  p.g = h->g;
+  p.zs = h->zs;
+  p.czs = h->czs;
+  p.rot = h->rot;
+  p.fimg = h->fimg;
+  p.sched = h->tfwd;
+  p.begin = h->tfwd_begin;
+  p.E = E;
+  p.part = h->tc_part;
+  p.err = h->err_word;
+  return p;
+}
+
+TcAdjParams tc_adj_params(const ash_hologram* h, const float2* y, const AdjOut& out) {
+  TcAdjParams p{};
+  p.g = h->g;
+  p.zs = h->zs;
+  p.czs = h->czs;
+  p.rot = h->rot;
+  p.y = y;
+  p.amp_img = h->amp_img;
+  p.out = out;
+  p.fimg = h->fimg;
+  p.sched = h->tadj;
+  p.split = h->tc_split;
+  p.split_groups = h->tadj_groups;
+  p.err = h->err_word;
+  return p;
 }
 
 cudaError_t launch_gradc(int D, const GradCParams& p, dim3 grid, cudaStream_t s) {
@@ -191,23 +205,19 @@ cudaError_t launch_gradc(int D, const GradCParams& p, dim3 grid, cudaStream_t s)
 // forward transform into E (device complex [N]).
 ash_status enqueue_forward(ash_hologram* h, int source, const float* phase, const float2* field, float2* E,
                            cudaStream_t s) {
-  if (use_tc_forward(h)) {
-    TcFwdParams tp{};
-    tp.v = view_of(h);
-    tp.sched = h->tsched;
-    tp.cz = h->cz;
-    tp.rot = h->rot;
-    tp.phase = phase;
-    tp.field = field;
-    tp.source = source;
-    tp.partial = h->partial;
-    tp.err = h->err_word;
-    cudaError_t e = launch_tc_forward(h->g.D, tp, h->tsched.G, s);
+  if (use_tc_fwd(h)) {
+    cudaError_t e = cudaSuccess;
+    if (source != kSrcImg) {
+      e = tc_field_img(h->g, h->amp_img, source == kSrcPhase ? phase : nullptr, field, h->fimg, s);
+      if (e != cudaSuccess) return cuda_fail(e, "nearfield image launch");
+    }
+    const TcFwdParams tp = tc_fwd_params(h, E);
+    e = tc_launch_forward(h->tc_na, tp, h->tfwd.G, s);
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core forward launch");
-    const int cols = 2 * h->g.N;
-    k_col_reduce<<<(cols + 31) / 32, dim3(32, 32), 0, s>>>(h->partial, tc_rows(h), cols, reinterpret_cast<float*>(E));
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "forward reduce launch");
+    if (h->tfwd_split) {
+      e = tc_launch_forward_reduce(tp, s);
+      if (e != cudaSuccess) return cuda_fail(e, "tensor-core forward reduce launch");
+    }
     return ASH_OK;
   }
   FwdParams p{};
@@ -236,21 +246,12 @@ ash_status enqueue_adjoint(ash_hologram* h, const float2* y, float2* g_out, floa
   p.out.phase_in = phase_in;
   p.out.dphase = dphase;
   p.out.epilogue = epilogue;
-  if (use_tc(h)) {
-    TcAdjParams tp{};
-    tp.v = p.v;
-    tp.sched = h->tsched;
-    tp.cz = h->cz;
-    tp.rot = h->rot;
-    tp.y = y;
-    tp.out = p.out;
-    tp.split = h->split;
-    tp.err = h->err_word;
-    cudaError_t e = launch_tc_adjoint(h->g.D, tp, h->tsched.G, s);
+  if (use_tc_adj(h)) {
+    const TcAdjParams tp = tc_adj_params(h, y, p.out);
+    cudaError_t e = tc_launch_adjoint(h->tc_na, tp, h->tadj.G, s);
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core adjoint launch");
-    if (h->tsplit) {
-      k_tc_adjoint_fixup<<<h->g.T * tc_sub(h->g.D), kTcThreads, 0, s>>>(tp, tc_mb(h->g.D));
-      e = cudaGetLastError();
+    if (h->tadj_split) {
+      e = tc_launch_adjoint_fixup(tp, h->tadj_nsplit, s);
       if (e != cudaSuccess) return cuda_fail(e, "tensor-core adjoint fix-up launch");
     }
     return ASH_OK;
@@ -267,19 +268,26 @@ ash_status enqueue_adjoint(ash_hologram* h, const float2* y, float2* g_out, floa
   return ASH_OK;
 }
 
+// iters x (forward, spot update, adjoint), then a final forward and the
+// metrics. When both transforms run on the tensor cores the adjoint also
+// writes the next forward's nearfield (kEpiFimg), so only the first forward
+// converts a phase.
+bool wgs_fused_field(const ash_hologram* h) { return use_tc_fwd(h) && use_tc_adj(h); }
+
 ash_status enqueue_wgs_body(ash_hologram* h, int iters, cudaStream_t s) {
-  ash_status st;
+  const bool tc = wgs_fused_field(h);
+  const int adj_epi = tc ? (kEpiPhase | kEpiFimg) : kEpiPhase;
+  ash_status st = enqueue_forward(h, kSrcPhase, h->wgs_phase, nullptr, h->wgs_E, s);
+  if (st != ASH_OK) return st;
   for (int it = 0; it < iters; ++it) {
-    st = enqueue_forward(h, kSrcPhase, h->wgs_phase, nullptr, h->wgs_E, s);
-    if (st != ASH_OK) return st;
     k_wgs_update<<<1, 1024, 0, s>>>(h->wgs_E, h->wgs_w, h->wgs_T, h->y, h->g.N);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "wgs update launch");
-    st = enqueue_adjoint(h, h->y, nullptr, h->wgs_phase, nullptr, nullptr, kEpiPhase, s);
+    st = enqueue_adjoint(h, h->y, nullptr, h->wgs_phase, nullptr, nullptr, adj_epi, s);
+    if (st != ASH_OK) return st;
+    st = enqueue_forward(h, tc ? kSrcImg : kSrcPhase, h->wgs_phase, nullptr, h->wgs_E, s);
     if (st != ASH_OK) return st;
   }
-  st = enqueue_forward(h, kSrcPhase, h->wgs_phase, nullptr, h->wgs_E, s);
-  if (st != ASH_OK) return st;
   k_metrics<<<1, 1024, 0, s>>>(h->wgs_E, h->wgs_T, h->g.N, h->sum_a2, (double)h->g.nx * h->g.ny, h->wgs_metrics);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "metrics launch");
@@ -393,21 +401,40 @@ ash_status ash_hologram_create(ash_hologram** out, int nx, int ny, const float* 
       if (h->sched.begin(b) % N != 0) h->split_tiles = true;
   }
   h->fwd_rows = g.T * (g.NT / 32);
-  if (D <= 12 && h->li.tc_adj_ctas_per_sm > 0 && h->li.tc_fwd_ctas_per_sm > 0) {
-    // tensor-core adjoint: units (sub-tile, spot) with sub-tiles of 128 x MB pixels
+  std::vector<int> tadj_groups;
+  std::vector<long long> tfwd_begin;
+  if (D <= kTcMaxModes) {
+    // tensor-core path: one range of units per resident CTA, at least two
+    // MMA chunks per CTA
+    h->tc_na = tc_na(D);
+    ce = tc_prepare(h->tc_na, &h->li.tc_adj_ctas_per_sm, &h->li.tc_fwd_ctas_per_sm);
+    if (ce != cudaSuccess) return fail(cuda_fail(ce, "tensor-core kernel preparation"));
     h->tc_ok = true;
-    const long long W = (long long)g.T * tc_sub(D) * N;
-    const long long umin = N < 256 ? N : 256;
-    const int per_sm = h->li.tc_adj_ctas_per_sm < h->li.tc_fwd_ctas_per_sm ? h->li.tc_adj_ctas_per_sm
-                                                                           : h->li.tc_fwd_ctas_per_sm;
-    long long G = (long long)sms * per_sm;
-    if (G > W / umin) G = W / umin;
-    if (G < 1) G = 1;
-    if (G > h->sched.G) G = h->sched.G;   // the split scratch is sized for sched.G CTAs
-    h->tsched.W = W;
-    h->tsched.G = (int)G;
-    for (int b = 1; b < h->tsched.G; ++b)
-      if (h->tsched.begin(b) % N != 0) h->tsplit = true;
+    const int nch = (N + kTcChunk - 1) / kTcChunk;
+    const long long Wa = (long long)g.T * kTcGroupsPerTile * nch;
+    long long Ga = (long long)sms * h->li.tc_adj_ctas_per_sm;
+    if (Ga > Wa / 2) Ga = Wa / 2;
+    if (Ga < 1) Ga = 1;
+    h->tadj.W = Wa;
+    h->tadj.G = (int)Ga;
+    for (int b = 1; b < h->tadj.G; ++b) {
+      const long long u = h->tadj.begin(b);
+      if (u % nch == 0) continue;
+      const int grp = (int)(u / nch);
+      if (tadj_groups.empty() || tadj_groups.back() != grp) tadj_groups.push_back(grp);
+    }
+    h->tadj_split = !tadj_groups.empty();
+    h->tadj_nsplit = (int)tadj_groups.size();
+    TcFwdSched& f = h->tfwd;
+    f.nb = (N + kTcRows - 1) / kTcRows;
+    f.nq = g.T * kTcChunksPerTile;
+    long long Gf = (long long)sms * h->li.tc_fwd_ctas_per_sm;
+    if (Gf > f.units() / 2) Gf = f.units() / 2;
+    if (Gf < 1) Gf = 1;
+    f.G = (int)Gf;
+    for (int b = 0; b <= f.G; ++b) tfwd_begin.push_back(f.begin(b));
+    for (int b = 1; b < f.G; ++b)
+      if (tfwd_begin[b] % f.nq != 0) h->tfwd_split = true;
   }
   h->gradc_gy = (N + kGradThreads * kGradSpots - 1) / (kGradThreads * kGradSpots);
   {
@@ -424,13 +451,18 @@ ash_status ash_hologram_create(ash_hologram** out, int nx, int ny, const float* 
   if ((st = ws(h, &h->amp_img, pix)) != ASH_OK) return fail(st);
   if ((st = ws(h, &h->anchors, (size_t)g.T * D)) != ASH_OK) return fail(st);
   if ((st = ws(h, &h->coeff, (size_t)N * D)) != ASH_OK) return fail(st);
-  {
-    const size_t rows = h->tc_ok && tc_rows(h) > h->fwd_rows ? (size_t)tc_rows(h) : (size_t)h->fwd_rows;
-    if ((st = ws(h, &h->partial, rows * 2 * N)) != ASH_OK) return fail(st);
-  }
+  if ((st = ws(h, &h->partial, (size_t)h->fwd_rows * 2 * N)) != ASH_OK) return fail(st);
   if ((st = ws(h, &h->split, (size_t)h->sched.G * 2 * kTilePix)) != ASH_OK) return fail(st);
-  if (h->tc_ok && (st = ws(h, &h->cz, (size_t)N * tc_kp(D))) != ASH_OK) return fail(st);
-  if (h->tc_ok && (st = ws(h, &h->rot, (size_t)N * g.T)) != ASH_OK) return fail(st);
+  if (h->tc_ok) {
+    if ((st = ws(h, &h->zs, tc_zs_floats(g))) != ASH_OK) return fail(st);
+    if ((st = ws(h, &h->czs, tc_czs_floats(N, D))) != ASH_OK) return fail(st);
+    if ((st = ws(h, &h->fimg, tc_fimg_float4s(g))) != ASH_OK) return fail(st);
+    if ((st = ws(h, &h->rot, (size_t)N * g.T)) != ASH_OK) return fail(st);
+    if ((st = ws(h, &h->tc_split, (size_t)h->tadj.G * 2 * kTcRows)) != ASH_OK) return fail(st);
+    if ((st = ws(h, &h->tc_part, (size_t)h->tfwd.G * 2 * kTcRows)) != ASH_OK) return fail(st);
+    if ((st = ws(h, &h->tfwd_begin, tfwd_begin.size())) != ASH_OK) return fail(st);
+    if ((st = ws(h, &h->tadj_groups, tadj_groups.size() + 1)) != ASH_OK) return fail(st);
+  }
   if ((st = ws(h, &h->gradc_partial, (size_t)h->gradc_gx * N * D)) != ASH_OK) return fail(st);
   if ((st = ws(h, &h->E, (size_t)N)) != ASH_OK) return fail(st);
   if ((st = ws(h, &h->y, (size_t)N)) != ASH_OK) return fail(st);
@@ -469,7 +501,17 @@ ash_status ash_hologram_create(ash_hologram** out, int nx, int ny, const float* 
   bp.anchors = h->anchors;
   k_basis<<<g.T, g.NT, 0, s>>>(bp);
   CREATE_CUDA(cudaGetLastError());
-  CREATE_CUDA(enqueue_split_coeff(h, s));
+  if (h->tc_ok) {
+    CREATE_CUDA(cudaMemcpyAsync(h->tfwd_begin, tfwd_begin.data(), tfwd_begin.size() * sizeof(long long),
+                                cudaMemcpyHostToDevice, s));
+    if (!tadj_groups.empty())
+      CREATE_CUDA(cudaMemcpyAsync(h->tadj_groups, tadj_groups.data(), tadj_groups.size() * sizeof(int),
+                                  cudaMemcpyHostToDevice, s));
+    CREATE_CUDA(tc_build_zs(g, h->dz, h->zs, s));
+    // pixels outside the grid stay 0 in every nearfield image
+    CREATE_CUDA(cudaMemsetAsync(h->fimg, 0, tc_fimg_float4s(g) * sizeof(float4), s));
+  }
+  CREATE_CUDA(enqueue_tc_coeff(h, s));
   k_amp_image<<<g.T, g.NT, 0, s>>>(g, amp, h->amp_img);
   CREATE_CUDA(cudaGetLastError());
   k_sum_sq<<<1, 1024, 0, s>>>(amp, M, h->sum_a2);
@@ -505,7 +547,7 @@ ash_status ash_set_coefficients(ash_hologram* h, const float* coeff, void* strea
   if (injected_failure()) return set_error(ASH_ERR_INJECTED, "injected failure");
   ASH_CUDA(cudaMemcpyAsync(h->coeff, coeff, (size_t)h->g.N * h->g.D * sizeof(float), cudaMemcpyDeviceToDevice,
                            as_stream(stream)));
-  ASH_CUDA(enqueue_split_coeff(h, as_stream(stream)));
+  ASH_CUDA(enqueue_tc_coeff(h, as_stream(stream)));
   return ASH_OK;
 }
 
@@ -621,10 +663,10 @@ ash_status ash_hologram_launch_info(const ash_hologram* h, int* out) {
   out[0] = h->sched.G;
   out[1] = h->li.fwd_ctas_per_sm;
   out[2] = h->li.adj_ctas_per_sm;
-  out[3] = h->tc_ok ? h->tsched.G : 0;
-  out[4] = h->li.tc_adj_ctas_per_sm < h->li.tc_fwd_ctas_per_sm ? h->li.tc_adj_ctas_per_sm : h->li.tc_fwd_ctas_per_sm;
-  out[5] = (h->split_tiles ? 1 : 0) | (h->tsplit ? 2 : 0);
-  out[6] = (use_tc(h) ? 2 : 1) | (use_tc_forward(h) ? 4 : 0);
+  out[3] = h->tc_ok ? h->tadj.G : 0;
+  out[4] = h->tc_ok ? h->tfwd.G : 0;
+  out[5] = (h->split_tiles ? 1 : 0) | (h->tadj_split ? 2 : 0) | (h->tfwd_split ? 4 : 0);
+  out[6] = (use_tc_adj(h) ? 2 : 1) | (use_tc_fwd(h) ? 4 : 0);
   out[7] = h->g.P;
   return ASH_OK;
 }
@@ -632,7 +674,7 @@ ash_status ash_hologram_launch_info(const ash_hologram* h, int* out) {
 ash_status ash_set_kernel_variant(ash_hologram* h, int variant) {
   if (!h || variant < 0 || variant > 2) return set_error(ASH_ERR_INVALID_ARG, "variant must be 0, 1 or 2");
   if (variant == 2 && !h->tc_ok)
-    return set_error(ASH_ERR_UNSUPPORTED, "tensor-core kernels need D <= 12 (D = %d)", h->g.D);
+    return set_error(ASH_ERR_UNSUPPORTED, "tensor-core kernels need D <= %d (D = %d)", kTcMaxModes, h->g.D);
   h->variant = variant;
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
   h->graphs.clear();
@@ -641,10 +683,13 @@ ash_status ash_set_kernel_variant(ash_hologram* h, int variant) {
 
 int ash_wgs_launches(const ash_hologram* h, int iters) {
   if (!h || iters < 0) return -1;
-  const int fwd = 2;                              // transform kernel + reduction
-  const bool split = use_tc(h) ? h->tsplit : h->split_tiles;
-  const int adj = split ? 2 : 1;                  // transform kernel (+ fix-up)
-  return iters * (fwd + 1 + adj) + fwd + 1;       // + final forward and metrics
+  // forward: tensor-core (nearfield image unless fused, kernel, reduce if
+  // split) or FMA (kernel, reduction); adjoint: kernel (+ fix-up)
+  const bool fused = wgs_fused_field(h);
+  const int fwd_first = use_tc_fwd(h) ? 2 + (h->tfwd_split ? 1 : 0) : 2;
+  const int fwd = use_tc_fwd(h) ? (fused ? 1 : 2) + (h->tfwd_split ? 1 : 0) : 2;
+  const int adj = use_tc_adj(h) ? 1 + (h->tadj_split ? 1 : 0) : 1 + (h->split_tiles ? 1 : 0);
+  return fwd_first + iters * (1 + adj + fwd) + 1;   // + metrics
 }
 
 ash_status ash_profile(ash_hologram* h, const float* phase, const float* y, float* ms_out, void* stream) {
@@ -665,23 +710,20 @@ ash_status ash_profile(ash_hologram* h, const float* phase, const float* y, floa
   fp.source = kSrcPhase;
   fp.partial = h->partial;
   const int cols = 2 * h->g.N;
-  TcFwdParams tf{};
-  tf.v = fp.v;
-  tf.sched = h->tsched;
-  tf.cz = h->cz;
-  tf.rot = h->rot;
-  tf.phase = phase;
-  tf.source = kSrcPhase;
-  tf.partial = h->partial;
-  tf.err = h->err_word;
+  const bool tc = use_tc_fwd(h), tca = use_tc_adj(h);
+  const TcFwdParams tf = tc_fwd_params(h, h->E);
+  if (tc) e = tc_field_img(h->g, h->amp_img, phase, nullptr, h->fimg, s);
   cudaEventRecord(ev[0], s);
-  e = use_tc_forward(h) ? launch_tc_forward(h->g.D, tf, h->tsched.G, s) : launch_forward(h->g.D, fp, h->sched.G, s);
+  if (e == cudaSuccess) e = tc ? tc_launch_forward(h->tc_na, tf, h->tfwd.G, s) : launch_forward(h->g.D, fp, h->sched.G, s);
   cudaEventRecord(ev[1], s);
   if (e == cudaSuccess) {
     cudaEventRecord(ev[2], s);
-    k_col_reduce<<<(cols + 31) / 32, dim3(32, 32), 0, s>>>(h->partial, use_tc_forward(h) ? tc_rows(h) : h->fwd_rows, cols,
-                                                            reinterpret_cast<float*>(h->E));
-    e = cudaGetLastError();
+    if (!tc) {
+      k_col_reduce<<<(cols + 31) / 32, dim3(32, 32), 0, s>>>(h->partial, h->fwd_rows, cols, reinterpret_cast<float*>(h->E));
+      e = cudaGetLastError();
+    } else if (h->tfwd_split) {
+      e = tc_launch_forward_reduce(tf, s);
+    }
     cudaEventRecord(ev[3], s);
   }
   // adjoint kernel (phase epilogue), then the fix-up
@@ -692,26 +734,17 @@ ash_status ash_profile(ash_hologram* h, const float* phase, const float* y, floa
   ap.y = y2;
   ap.out.phase_out = h->wgs_phase;
   ap.out.epilogue = kEpiPhase;
-  TcAdjParams tp{};
-  tp.v = ap.v;
-  tp.sched = h->tsched;
-  tp.cz = h->cz;
-  tp.rot = h->rot;
-  tp.y = y2;
-  tp.out = ap.out;
-  tp.split = h->split;
-  tp.err = h->err_word;
+  const TcAdjParams tp = tc_adj_params(h, y2, ap.out);
   if (e == cudaSuccess) {
     cudaEventRecord(ev[4], s);
-    e = use_tc(h) ? launch_tc_adjoint(h->g.D, tp, h->tsched.G, s) : launch_adjoint(h->g.D, ap, h->sched.G, s);
+    e = tca ? tc_launch_adjoint(h->tc_na, tp, h->tadj.G, s) : launch_adjoint(h->g.D, ap, h->sched.G, s);
     cudaEventRecord(ev[5], s);
   }
   if (e == cudaSuccess) {
     cudaEventRecord(ev[6], s);
-    if (use_tc(h) && h->tsplit) {
-      k_tc_adjoint_fixup<<<h->g.T * tc_sub(h->g.D), kTcThreads, 0, s>>>(tp, tc_mb(h->g.D));
-      e = cudaGetLastError();
-    } else if (!use_tc(h) && h->split_tiles) {
+    if (tca && h->tadj_split) {
+      e = tc_launch_adjoint_fixup(tp, h->tadj_nsplit, s);
+    } else if (!tca && h->split_tiles) {
       k_adjoint_fixup<<<h->g.T, h->g.NT, 0, s>>>(ap);
       e = cudaGetLastError();
     }

@@ -119,7 +119,18 @@ __device__ __forceinline__ float2 cis_turns(float turns) {
 // Kernel parameter blocks.
 
 enum FwdSource : int { kSrcPhase = 0, kSrcField = 1 };
-enum AdjEpilogue : int { kEpiField = 1, kEpiPhase = 2, kEpiGradPhase = 4 };
+// kEpiFimg (tensor-core adjoint only): also write f = A exp(i arg g) in the
+// forward's tc layout, so the next WGS forward needs no sincos of its own.
+enum AdjEpilogue : int { kEpiField = 1, kEpiPhase = 2, kEpiGradPhase = 4, kEpiFimg = 8 };
+
+// sin and cos of two local phases on the MUFU pipe (the phases are kept
+// small by the tile anchoring, where sin.approx / cos.approx are accurate).
+__device__ __forceinline__ void sincos2(float2 x, float2& s, float2& c) {
+  s.x = __sinf(x.x);
+  c.x = __cosf(x.x);
+  s.y = __sinf(x.y);
+  c.y = __cosf(x.y);
+}
 
 // Balanced static schedule: the T * N (tile, spot) work units, tile-major,
 // are cut into G equal contiguous ranges, one per CTA. A tile whose spots

@@ -11,6 +11,7 @@
 #include "common.cuh"
 #include "launch.h"
 #include "mono.h"
+#include "tc_launch.h"
 
 struct ash_hologram {
   ash::Geometry g{};
@@ -27,13 +28,23 @@ struct ash_hologram {
   float2* anchors = nullptr;
   float* coeff = nullptr;
   float* partial = nullptr;
-  // tensor-core path (D <= 12): split coefficients, sub-tile schedule
+  // tensor-core path (D <= 21): operand images, schedules, split buffers
   int variant = 0;              // 0 auto, 1 FMA-pipe kernels, 2 tensor-core kernels
   bool tc_ok = false;
-  ash::Schedule tsched{};
-  bool tsplit = false;
-  float* cz = nullptr;
+  int tc_na = 0;                // K-atoms per operand row
+  ash::Schedule tadj{};         // adjoint units (group, spot chunk)
+  bool tadj_split = false;      // some group's spots span two CTA ranges
+  ash::TcFwdSched tfwd{};       // forward units (spot block, pixel chunk)
+  bool tfwd_split = false;      // some spot block's pixels span two CTA ranges
+  float* zs = nullptr;
+  float* czs = nullptr;
+  float4* fimg = nullptr;
   float2* rot = nullptr;        // [T][N] per-(tile, spot) anchor phase rotations
+  float2* tc_split = nullptr;   // [tadj.G][2][128]
+  float2* tc_part = nullptr;    // [tfwd.G][2][128]
+  long long* tfwd_begin = nullptr;   // [tfwd.G + 1] CTA range starts of the forward
+  int* tadj_groups = nullptr;   // groups split between adjoint CTA ranges
+  int tadj_nsplit = 0;
   float2* split = nullptr;
   float* gradc_partial = nullptr;
   float2* E = nullptr;

@@ -7,18 +7,13 @@
 #include "common.cuh"
 
 namespace ash {
-struct TcAdjParams;
-struct TcFwdParams;
-}
-
-namespace ash {
 
 struct LaunchInfo {
   int threads;        // CTA size of the pixel-stationary kernels
   int fwd_ctas_per_sm;
   int adj_ctas_per_sm;
   int gradc_ctas_per_sm;
-  int tc_adj_ctas_per_sm;   // 0 if the tensor-core adjoint is not available for this D
+  int tc_adj_ctas_per_sm;   // 0 if the tensor-core path is not available for this D
   int tc_fwd_ctas_per_sm;
 };
 
@@ -27,9 +22,7 @@ struct LaunchInfo {
   cudaError_t prepare_r##R(int D, LaunchInfo* info);                                          \
   cudaError_t launch_forward_r##R(int D, const FwdParams& p, int grid, cudaStream_t s);       \
   cudaError_t launch_adjoint_r##R(int D, const AdjParams& p, int grid, cudaStream_t s);       \
-  cudaError_t launch_gradc_r##R(int D, const GradCParams& p, dim3 grid, cudaStream_t s);           \
-  cudaError_t launch_tc_adjoint_r##R(int D, const TcAdjParams& p, int grid, cudaStream_t s);         \
-  cudaError_t launch_tc_forward_r##R(int D, const TcFwdParams& p, int grid, cudaStream_t s);
+  cudaError_t launch_gradc_r##R(int D, const GradCParams& p, dim3 grid, cudaStream_t s);
 ASH_DECLARE_RANGE(0)
 ASH_DECLARE_RANGE(1)
 ASH_DECLARE_RANGE(2)

@@ -1,0 +1,109 @@
+// Launchers of the tensor-core transform path (one instantiation per number
+// of K-atoms, NA = 1 for D <= 10 and NA = 2 for D <= 21).
+#include "tc_kernels.cuh"
+
+namespace ash {
+
+namespace {
+
+// Resident CTAs per SM from the kernel's registers, shared memory and TMEM
+// columns (the runtime's occupancy query does not account for TMEM).
+cudaError_t ctas_per_sm(const void* fn, size_t smem, int tmem_cols, int* out) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+  if (e != cudaSuccess) return e;
+  int dev = 0, smem_sm = 0, regs_sm = 0, reserved = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  const int warps = kTcThreads / 32;
+  const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
+  const int by_regs = regs_sm / (regs_warp * warps);
+  const int by_smem = (int)((size_t)smem_sm / (smem + fa.sharedSizeBytes + (size_t)reserved));
+  const int by_tmem = 512 / tmem_cols;
+  int n = by_regs < by_smem ? by_regs : by_smem;
+  n = n < by_tmem ? n : by_tmem;
+  *out = n < 1 ? 1 : n;
+  return cudaSuccess;
+}
+
+template <int NA>
+cudaError_t prepare_na(int* adj, int* fwd) {
+  const void* ka = (const void*)k_tc_adjoint<NA>;
+  const void* kf = (const void*)k_tc_forward<NA>;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcAdjShape<NA>::SMEM)))
+    return e;
+  if ((e = cudaFuncSetAttribute(ka, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared)))
+    return e;
+  if ((e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwdShape<NA>::SMEM)))
+    return e;
+  if ((e = cudaFuncSetAttribute(kf, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared)))
+    return e;
+  if ((e = ctas_per_sm(ka, TcAdjShape<NA>::SMEM, 2 * kTcChunk, adj))) return e;
+  return ctas_per_sm(kf, TcFwdShape<NA>::SMEM, 2 * kTcChunk, fwd);
+}
+
+unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+}  // namespace
+
+cudaError_t tc_prepare(int NA, int* adj_ctas_per_sm, int* fwd_ctas_per_sm) {
+  if (NA == 1) return prepare_na<1>(adj_ctas_per_sm, fwd_ctas_per_sm);
+  if (NA == 2) return prepare_na<2>(adj_ctas_per_sm, fwd_ctas_per_sm);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t tc_launch_adjoint(int NA, const TcAdjParams& p, int grid, cudaStream_t s) {
+  if (NA == 1) k_tc_adjoint<1><<<grid, kTcThreads, TcAdjShape<1>::SMEM, s>>>(p);
+  else if (NA == 2) k_tc_adjoint<2><<<grid, kTcThreads, TcAdjShape<2>::SMEM, s>>>(p);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t tc_launch_adjoint_fixup(const TcAdjParams& p, int n_split_groups, cudaStream_t s) {
+  if (n_split_groups <= 0) return cudaSuccess;
+  k_tc_adjoint_fixup<<<n_split_groups, kTcThreads, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_launch_forward(int NA, const TcFwdParams& p, int grid, cudaStream_t s) {
+  if (NA == 1) k_tc_forward<1><<<grid, kTcThreads, TcFwdShape<1>::SMEM, s>>>(p);
+  else if (NA == 2) k_tc_forward<2><<<grid, kTcThreads, TcFwdShape<2>::SMEM, s>>>(p);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t tc_launch_forward_reduce(const TcFwdParams& p, cudaStream_t s) {
+  k_tc_forward_reduce<<<dim3(p.sched.nb, kTcRows / 32), dim3(32, 32), 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_build_zs(const Geometry& g, const float* dz, float* zs, cudaStream_t s) {
+  const long long rows = (long long)g.T * kTcChunksPerTile * kTcChunk;
+  k_tc_build_zs<<<blocks_for(rows, 256), 256, 0, s>>>(g, dz, tc_na(g.D), zs);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_build_coeff(const Geometry& g, const float* coeff, const float2* anchors, float* czs, float2* rot,
+                           cudaStream_t s) {
+  const int nc64 = tc_spot_chunks(g.N);
+  k_tc_build_czs<<<blocks_for((long long)nc64 * kTcChunk, 256), 256, 0, s>>>(coeff, g.N, g.D, tc_na(g.D), nc64, czs);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long long nr = (long long)g.N * g.T;
+  k_tile_rotations<<<blocks_for(nr, 256), 256, 0, s>>>(coeff, anchors, g.N, g.D, g.T, rot);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_field_img(const Geometry& g, const float* amp_img, const float* phase, const float2* field,
+                         float4* fimg, cudaStream_t s) {
+  const long long px = (long long)g.T * kTilePix;
+  k_tc_field_img<<<blocks_for(px, 256), 256, 0, s>>>(g, amp_img, phase, field, reinterpret_cast<float*>(fimg));
+  return cudaGetLastError();
+}
+
+}  // namespace ash

@@ -1,9 +1,10 @@
 // Tensor-core (tcgen05) building blocks for the phase contraction.
 //
-// The phase matrix of a pixel block and a spot chunk, X[m][n] = dZ_m . C_n,
-// is a (128 x D) . (D x 16) product: it runs on the 5th-generation tensor
-// cores with the accumulator in tensor memory (TMEM), leaving the FP32 and
-// MUFU pipes to the sincos and the complex multiply-accumulate.
+// The phase matrix of 128 pixels and 64 spots (or 128 spots and 64 pixels),
+// X[m][n] = dZ_m . C_n, is a (128 x K) . (K x 64) product: it runs on the
+// 5th-generation tensor cores with the accumulator in tensor memory (TMEM),
+// leaving the FP32 and MUFU pipes to the sincos and the complex
+// multiply-accumulate.
 //
 // fp32 accuracy from tf32 operands (split-tf32): every operand v is split
 // into v_hi = tf32(v) and v_lo = tf32(v - v_hi); the product c.z is taken as
@@ -12,10 +13,10 @@
 // [z_hi | z_lo | z_hi], B row (spot) = [c_hi | c_hi | c_lo], padded with
 // zeros to KP = 32 (D <= 10) or 64 (D <= 21).
 //
-// Shared-memory operands use the K-major layout with the 128-byte swizzle:
-// a K-atom is 8 rows x 128 bytes (32 tf32), 16-byte chunk j of row r is
-// stored at chunk position j ^ (r & 7); atoms of consecutive rows are 1024 B
-// apart; a second K-atom (KP = 64) follows after all rows of the first.
+// Operands use the K-major layout with the 128-byte swizzle: rows of 128
+// bytes (32 tf32, one K-atom), 16-byte chunk j of row r stored at chunk
+// position j ^ (r & 7), 8-row groups 1024 B apart; a second K-atom (KP = 64)
+// follows after all rows of the first.
 #pragma once
 
 #include <stdint.h>
@@ -66,6 +67,29 @@ __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.a
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+// Make barrier initialisation visible to the async proxy (bulk copies, MMA commits).
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// One arrival on `bar` that also announces `bytes` of bulk-copy data to come.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// Global -> shared copy by the bulk-copy (TMA) engine; both addresses 16-byte
+// aligned, bytes a multiple of 16; completion is counted on `bar` in bytes.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ uint32_t atom_add_acq_rel_smem(uint32_t* a, uint32_t v) {
+  uint32_t old;
+  asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(smem_u32(a)), "r"(v) : "memory");
+  return old;
 }
 
 // Bounded wait for the phase with parity `parity` to complete. Returns false

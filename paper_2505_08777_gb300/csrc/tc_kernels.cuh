@@ -1,81 +1,144 @@
-// Tensor-core variants of the transforms (see tc_common.cuh for the
-// split-tf32 phase contraction and the shared-memory layout).
+// Tensor-core transforms (see tc_common.cuh for the split-tf32 phase
+// contraction and the operand layout, tc_launch.h for the parameter blocks).
 //
-// Pixel-stationary, like the FMA kernels: a CTA of 128 threads owns a
-// sub-tile of 128 x MB pixels of a 32x32 tile; thread t's pixels are
-// (column t % 32, rows t / 32 + 4 k) for k = h*MB .. h*MB + MB - 1, and pixel
-// block b (k = h*MB + b) is M-block b of the MMA: TMEM lane t holds thread
-// t's phases. Spots stream in chunks of 16 (the MMA's N): while the tensor
-// core computes chunk c + 1 into one TMEM buffer, the threads turn chunk c
-// into sin/cos and complex multiply-accumulates.
+// Both transforms contract 128 rows of one kind with 64 of the other per MMA
+// (M = 128, N = 64): the tensor core's cost per instruction is flat up to
+// N = 64, so wide chunks keep it far below the MUFU time.
+//
+//  * adjoint, pixel-stationary: A = the split basis rows of 128 pixels (a
+//    "group": rows 4h .. 4h + 3 of a 32x32 tile), B = 64 spots; thread t owns
+//    pixel t and accumulates g over all spots of its range;
+//  * forward, spot-stationary: A = 128 spots, B = 64 pixels (a "chunk": half
+//    a group); thread t owns spot t and accumulates E over its pixels, so no
+//    cross-thread reduction is needed.
+//
+// Operands are laid out in HBM exactly as the MMA reads them from shared
+// memory (pre-split, pre-swizzled), so one thread moves each chunk with the
+// bulk-copy engine (cp.async.bulk) into a ring of shared-memory slots
+// tracked by mbarriers. Two TMEM buffers of 64 fp32 columns alternate: each
+// warp copies a chunk's phases out of TMEM, arrives on a shared counter and
+// goes on to the sincos and the complex multiply-accumulate; the warp that
+// arrives last refills the rings and issues the MMA two chunks ahead into
+// the buffer just freed. No CTA-wide barrier is taken in the main loop. The
+// producer steps of consecutive chunks cannot overlap: the last arrival for
+// chunk c comes after every warp's arrival for c, and the warp that ran the
+// producer step of c - 1 arrives for c only after finishing it (its release
+// on the counter publishes the producer state to the next producer).
+//
+// Per-tile anchor phases: for a pixel m of tile tau,
+//   C_n . Z_m = 2 pi base(n, tau) + C_n . dZ_m,
+// with base reduced exactly in turns once per (spot, tile) (rot[tau][n] =
+// exp(+i 2 pi base)); the tensor core computes C_n . dZ_m only.
 #pragma once
 
+#include "common.cuh"
 #include "tc_common.cuh"
-#include "transform_kernels.cuh"
+#include "tc_launch.h"
 
 namespace ash {
 
-constexpr int kTcS = 16;                  // spots per MMA chunk
-constexpr int kTcThreads = 128;
-constexpr uint32_t kTcWaitPolls = 1u << 24;
-constexpr unsigned kErrTimeout = 2u;
+// Adjoint shared memory: 2 A slots (groups), 2 B slots (spot chunks), y' per
+// warp (four CTAs per SM for NA = 1).
+template <int NA>
+struct TcAdjShape {
+  static constexpr int NB = 2;
+  static constexpr uint32_t A_BYTES = NA * 16384, B_BYTES = NA * 8192;
+  static constexpr uint32_t Y_BYTES = 4 * 32 * 16;
+  static constexpr int NBARS = 4 + NB;
+  // [alignment slack][A x 2][B ring][y'][barriers][armed counts][counter][TMEM slot][producer state]
+  static constexpr size_t SMEM = 1024 + 2 * A_BYTES + NB * B_BYTES + Y_BYTES + NBARS * 12 + 8 + 16;
+};
 
-__host__ __device__ constexpr int tc_kp(int D) { return 3 * D <= 32 ? 32 : 64; }   // padded K
-__host__ __device__ constexpr int tc_mb(int D) { return tc_kp(D) == 32 ? 4 : 2; }  // M-blocks per CTA
-__host__ __device__ constexpr int tc_sub(int D) { return 8 / tc_mb(D); }           // sub-tiles per tile
+// Forward shared memory: 1 A slot (spot block), a ring of B slots (64 pixel
+// rows, read by the tensor core) and a ring of f slots (the 64 pixels'
+// nearfield, read by the threads). Each copy is issued several chunks
+// before its use, which keeps HBM latency hidden even where a chunk's
+// arithmetic is short (a partial last spot block).
+template <int NA>
+struct TcFwdShape {
+  static constexpr int NBB = NA == 1 ? 4 : 3, NF = 4;
+  static constexpr uint32_t A_BYTES = NA * 16384, B_BYTES = NA * 8192, F_BYTES = 512;
+  static constexpr int NBARS = 3 + NBB + NF;
+  // [alignment slack][A][B ring][f ring][barriers][armed counts][counter][TMEM slot][producer state]
+  static constexpr size_t SMEM = 1024 + A_BYTES + NBB * B_BYTES + NF * F_BYTES + NBARS * 12 + 8 + 32;
+};
 
-// Dynamic shared memory: [1 KB alignment slack][A][B x 2][Y x 3][2 mbarriers][tmem slot].
-// B (read only by the tensor core) is double-buffered: a thread stages chunk
-// c + 2 only after it has itself seen the MMA of chunk c complete. The y'
-// pairs are read by all threads and need three buffers: chunk c is read in
-// iteration c + 1 and its buffer is rewritten in iteration c + 3, after the
-// barrier of iteration c + 2.
-__host__ __device__ constexpr size_t tc_smem_bytes(int D) {
-  return 1024 + (size_t)tc_mb(D) * (tc_kp(D) / 32) * 16384 + 2 * (size_t)(tc_kp(D) / 32) * kTcS * 128 +
-         3 * (kTcS / 2) * 32 + 64;
+// --- operand images ---------------------------------------------------------
+
+// zs from the register-image basis dz: one thread per (chunk, row).
+static __global__ void k_tc_build_zs(const Geometry G, const float* __restrict__ dz, int NA, float* __restrict__ zs) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)G.T * kTcChunksPerTile * kTcChunk) return;
+  const long long qc = e / kTcChunk;
+  const int r = (int)(e % kTcChunk), D = G.D;
+  const TcPixel px = tc_pixel(G, qc, r);
+  const int tpx = px.img / G.P, k = px.img % G.P;
+  float* dst = zs + (size_t)qc * NA * 2048;
+  for (int a = 0; a < NA; ++a)
+    for (int kk = 0; kk < 32; ++kk) {
+      const int col = 32 * a + kk, seg = col / D, d = col % D;
+      float v = 0.0f;
+      if (seg < 3) {
+        const float z = dz[((size_t)tpx * D + d) * G.P + k];
+        const float hi = to_tf32(z);
+        v = seg == 1 ? to_tf32(z - hi) : hi;   // [hi | lo | hi]
+      }
+      dst[a * 2048 + swz128(r, kk)] = v;
+    }
 }
 
-struct TcFwdParams {
-  HoloView v;
-  Schedule sched;            // units: (sub-tile, spot)
-  const float* cz;           // [N][KP]
-  const float2* rot;         // [T][N] exp(+i 2 pi base(n, tile)); the forward applies the conjugate
-  const float* phase;        // user layout (kSrcPhase)
-  const float2* field;       // user layout (kSrcField)
-  int source;
-  float* partial;            // [T * SUB * 4][2N]: row (sub-tile, warp), each entry written once
-  unsigned* err;
-};
+// czs from the coefficients: one thread per (spot chunk, row); rows >= N are 0.
+static __global__ void k_tc_build_czs(const float* __restrict__ coeff, int N, int D, int NA, int nc64,
+                                      float* __restrict__ czs) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)nc64 * kTcChunk) return;
+  const int jc = (int)(e / kTcChunk), r = (int)(e % kTcChunk), n = jc * kTcChunk + r;
+  float* dst = czs + (size_t)jc * NA * 2048;
+  for (int a = 0; a < NA; ++a)
+    for (int kk = 0; kk < 32; ++kk) {
+      const int col = 32 * a + kk, seg = col / D, d = col % D;
+      float v = 0.0f;
+      if (seg < 3 && n < N) {
+        const float c = coeff[(size_t)n * D + d];
+        const float hi = to_tf32(c);
+        v = seg == 2 ? to_tf32(c - hi) : hi;   // [hi | hi | lo]
+      }
+      dst[a * 2048 + swz128(r, kk)] = v;
+    }
+}
 
-struct TcAdjParams {
-  HoloView v;
-  Schedule sched;            // units: (sub-tile, spot), W = T * tc_sub(D) * N
-  const float* cz;           // [N][KP] split coefficients [c_hi | c_hi | c_lo | 0]
-  const float2* rot;         // [T][N] exp(+i 2 pi base(n, tile))
-  const float2* y;           // [N]
-  AdjOut out;
-  float2* split;             // [G][2][kTilePix]
-  unsigned* err;
-};
-
-// cz[n][k] from C: split-tf32 coefficients in K order (one thread per entry).
-static __global__ void k_tc_split_coeff(const float* __restrict__ coeff, int N, int D, int KP, float* __restrict__ cz) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (long long)N * KP) return;
-  const int n = (int)(i / KP), k = (int)(i % KP);
-  float v = 0.0f;
-  if (k < 3 * D) {
-    const int seg = k / D, d = k % D;
-    const float c = coeff[(size_t)n * D + d];
-    const float hi = to_tf32(c);
-    v = (seg < 2) ? hi : to_tf32(c - hi);
+// Nearfield in tc layout from a phase (f = A exp(i phase)) or a complex
+// field, both in user layout; pixels outside the grid are 0.
+static __global__ void k_tc_field_img(const Geometry G, const float* __restrict__ amp_img,
+                                      const float* __restrict__ phase, const float2* __restrict__ field,
+                                      float* __restrict__ fimg) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)G.T * kTilePix) return;
+  const long long qc = e / kTcChunk;
+  const int r = (int)(e % kTcChunk);
+  const TcPixel px = tc_pixel(G, qc, r);
+  float fr = 0.0f, fi = 0.0f;
+  if (px.i < G.nx && px.j < G.ny) {
+    const size_t m = (size_t)px.j * G.nx + px.i;
+    if (phase) {
+      float s, c;
+      sincosf(phase[m], &s, &c);
+      const float a = amp_img[px.img];
+      fr = a * c;
+      fi = a * s;
+    } else {
+      const float2 f = field[m];
+      fr = f.x;
+      fi = f.y;
+    }
   }
-  cz[i] = v;
+  float* q = fimg + ((size_t)qc * 32 + (r >> 1)) * 4;
+  q[r & 1] = fr;
+  q[2 + (r & 1)] = fi;
 }
 
 // rot[tile][n] = exp(+i 2 pi base(n, tile)): the per-(spot, tile) phase of
-// the anchor pixel, reduced exactly in turns (set up once per coefficient
-// matrix; the forward uses its conjugate).
+// the anchor pixel, reduced exactly in turns.
 static __global__ void k_tile_rotations(const float* __restrict__ coeff, const float2* __restrict__ anchors, int N,
                                         int D, int T, float2* __restrict__ rot) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -91,444 +154,523 @@ static __global__ void k_tile_rotations(const float* __restrict__ coeff, const f
   rot[i] = cis_turns(base_turns<kMaxModes>(c, a));
 }
 
-template <int D>
-__global__ void __launch_bounds__(kTcThreads, 3) k_tc_adjoint(const TcAdjParams p) {
-  constexpr int KP = tc_kp(D), MB = tc_mb(D), NA = KP / 32, SUB = tc_sub(D), S = kTcS;
-  constexpr uint32_t NCOLS = 2 * MB * S;   // two TMEM buffers of MB x S fp32 columns
-  constexpr uint32_t IDESC = umma_idesc_tf32(128, S);
-  constexpr int BV = NA * S * 8 / kTcThreads;   // 16-byte pieces of a B chunk per thread
-  static_assert(BV * kTcThreads == NA * S * 8, "B chunk must split evenly over the CTA");
+// --- pieces shared by the two kernels ------------------------------------------
+
+// D[tmem] = A[128 rows] . B[64 rows]^T over KP = 32 NA, issued by one thread.
+template <int NA>
+__device__ __forceinline__ void tc_mma_chunk(uint32_t tmem_cols, const float* sA, const float* sB, uint64_t* done) {
+  constexpr uint32_t IDESC = umma_idesc_tf32(kTcRows, kTcChunk);
+#pragma unroll
+  for (int ks = 0; ks < 4 * NA; ++ks) {
+    const int atom = ks / 4, koff = (ks % 4) * 32;
+    const uint64_t ad = umma_desc(smem_u32(sA + atom * 4096) + koff);
+    const uint64_t bd = umma_desc(smem_u32(sB + atom * 2048) + koff);
+    umma_tf32(tmem_cols, ad, bd, IDESC, ks > 0 ? 1u : 0u);
+  }
+  umma_commit(done);
+}
+
+// Bulk copy of 128 operand rows (two consecutive 64-row chunk images) into
+// a [NA][128][32] slot.
+template <int NA>
+__device__ __forceinline__ void tc_copy_rows128(float* dst, const float* src, uint64_t* bar) {
+  if constexpr (NA == 1) {
+    bulk_g2s(dst, src, 16384, bar);
+  } else {
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+      bulk_g2s(dst + a * 4096, src + a * 2048, 8192, bar);
+      bulk_g2s(dst + a * 4096 + 2048, src + NA * 2048 + a * 2048, 8192, bar);
+    }
+  }
+}
+
+// 16-column groups [q_lo, q_hi) of this warp's 32 TMEM lanes, one wait.
+__device__ __forceinline__ void tc_load_cols(uint32_t taddr, int q_lo, int q_hi, uint32_t (&x)[4][16]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (q >= q_lo && q < q_hi) tmem_ld16_nowait(taddr + 16 * q, x[q]);
+  tmem_wait();
+}
+
+// Bounded wait for the last armed phase of each barrier, so that no copy or
+// MMA is still in flight when the CTA frees its memory (all of them have
+// completed already unless a wait timed out).
+__device__ __forceinline__ void tc_drain(uint64_t* bars, const uint32_t* armed, int nbars) {
+  for (int k = 0; k < nbars; ++k)
+    if (armed[k] > 0) mbar_wait(&bars[k], (armed[k] - 1) & 1u, kTcWaitPolls);
+}
+
+// Adjoint output of row r of chunk qc (in the pixel's user-layout slot and,
+// for kEpiFimg, in the tc-layout nearfield f = A exp(i arg g)).
+__device__ __forceinline__ void tc_adjoint_epilogue(const TcAdjParams& p, long long qc, int r, float gr, float gi) {
+  const Geometry& G = p.g;
+  const TcPixel px = tc_pixel(G, qc, r);
+  if (px.i >= G.nx || px.j >= G.ny) return;
+  const bool need_a = (p.out.epilogue & (kEpiGradPhase | kEpiFimg)) != 0;
+  const float a = need_a ? __ldg(p.amp_img + px.img) : 0.0f;
+  adjoint_epilogue(p.out, (size_t)px.j * G.nx + px.i, gr, gi, a);
+  if (p.out.epilogue & kEpiFimg) {
+    const float ph = (gr == 0.0f && gi == 0.0f) ? 0.0f : atan2f(gi, gr);
+    float s, c;
+    sincosf(ph, &s, &c);
+    float* q = reinterpret_cast<float*>(p.fimg + (size_t)qc * 32 + (r >> 1));
+    q[r & 1] = a * c;
+    q[2 + (r & 1)] = a * s;
+  }
+}
+
+// --- adjoint ------------------------------------------------------------------
+
+// g_m = sum_n y_n exp(+i C_n . Z_m) for the pixels of this CTA's (group,
+// spot chunk) range; groups whose spots are split between CTAs go through
+// `split` and k_tc_adjoint_fixup.
+//
+// Producer schedule (run by the warp that releases a chunk last): at the
+// release of chunk c, B of chunk c + NB goes into the slot MMA(c) has freed,
+// A of group s + 2 into the slot of group s once c is s's last chunk, and
+// the MMA of chunk c + 1 is issued into the other TMEM buffer; it completes
+// while the warps work through chunk c. (Two chunks of lookahead were
+// measured slower here: the deeper B ring it needs costs a CTA per SM.)
+template <int NA>
+__global__ void __launch_bounds__(kTcThreads, 4) k_tc_adjoint(const TcAdjParams p) {
+  using S = TcAdjShape<NA>;
+  constexpr int NB = S::NB, NBARS = S::NBARS;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  float* sA = reinterpret_cast<float*>(base);                        // [MB][NA][128 x 32]
-  float* sB = sA + MB * NA * 4096;                                   // [2][NA][S x 32]
-  float* sY = sB + 2 * NA * S * 32;                                  // [3][S/2][8]
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sY + 3 * (S / 2) * 8);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+  float* sA = reinterpret_cast<float*>(base);                      // [2][NA][128][32]
+  float* sB = sA + 2 * NA * 4096;                                  // [NB][NA][64][32]
+  float4* sY = reinterpret_cast<float4*>(sB + NB * NA * 2048);     // [4 warps][32 spot pairs]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sY + 4 * 32);       // full[2] | bfull[NB] | afull[2]
+  uint64_t* full = bars;
+  uint64_t* bfull = bars + 2;
+  uint64_t* afull = bars + 2 + NB;
+  uint32_t* armed = reinterpret_cast<uint32_t*>(bars + NBARS);     // phases armed per barrier
+  uint32_t* cnt = armed + NBARS;                                   // [2] arrivals per TMEM buffer
+  uint32_t* tslot = cnt + 2;
+  int* pst = reinterpret_cast<int*>(tslot + 1);                    // next MMA: chunk, group, spot chunk
 
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
-  if (w == 0) tmem_alloc(tslot, NCOLS);
+  const Geometry& G = p.g;
+  const int N = G.N;
+  const int nch = (N + kTcChunk - 1) / kTcChunk;
+  const long long u0 = p.sched.begin(blockIdx.x), u1 = p.sched.begin(blockIdx.x + 1);
+  const int nc = (int)(u1 - u0);
+  // chunk c of this range is spot chunk j of group s; (s, j) advance
+  // incrementally (no 64-bit division per chunk)
+  const int s0 = (int)(u0 / nch), j0 = (int)(u0 % nch);
+  const int s_last = nc > 0 ? (int)((u1 - 1) / nch) : s0;
+
+  if (w == 0) tmem_alloc(tslot, 2 * kTcChunk);
   if (t == 0) {
-    mbar_init(&mbar[0], 1);
-    mbar_init(&mbar[1], 1);
+    for (int k = 0; k < NBARS; ++k) {
+      mbar_init(&bars[k], 1);
+      armed[k] = 0;
+    }
+    cnt[0] = cnt[1] = 0;
+    fence_mbar_init();
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
   const uint32_t tlane = (uint32_t)(w * 32) << 16;
-  uint32_t parity = 0;
   bool ok = true;
 
-  const Geometry& G = p.v.g;
-  const int N = G.N;
-  const long long u0 = p.sched.begin(blockIdx.x), u1 = p.sched.begin(blockIdx.x + 1);
-  const int sf = (int)(u0 / N), sl = (int)((u1 - 1) / N);
-
-  // chunk staging in two halves: fetch() issues the global loads into
-  // registers, put() stores them (B rows to sB[buf], y' pairs to sY[ybuf])
-  float4 bv[BV];
-  float2 yv = make_float2(0.0f, 0.0f), rv = make_float2(0.0f, 0.0f);
-  auto fetch = [&](int tile, int n0, int se) {
-#pragma unroll
-    for (int q = 0; q < BV; ++q) {
-      const int e = t + q * kTcThreads;
-      const int atom = e / (S * 8), r = (e / 8) % S, j = e % 8;
-      const int n = n0 + r;
-      bv[q] = n < se ? __ldg(reinterpret_cast<const float4*>(p.cz + (size_t)n * KP + atom * 32 + 4 * j))
-                     : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    }
-    if (t < S) {
-      const int n = n0 + t;
-      yv = n < se ? __ldg(p.y + n) : make_float2(0.0f, 0.0f);
-      rv = n < se ? __ldg(p.rot + (size_t)tile * N + n) : make_float2(0.0f, 0.0f);
-    }
+  // --- producer steps (one thread at a time) ---
+  auto load_a = [&](int s) {
+    const int slot = (s - s0) & 1;
+    mbar_expect_tx(&afull[slot], S::A_BYTES);
+    ++armed[2 + NB + slot];
+    tc_copy_rows128<NA>(sA + slot * NA * 4096, p.zs + (size_t)(2 * s) * NA * 2048, &afull[slot]);
   };
-  auto put = [&](int buf, int ybuf) {
-#pragma unroll
-    for (int q = 0; q < BV; ++q) {
-      const int e = t + q * kTcThreads;
-      const int atom = e / (S * 8), r = (e / 8) % S, j = e % 8;
-      *reinterpret_cast<float4*>(sB + (buf * NA + atom) * (S * 32) + swz128(r, 4 * j)) = bv[q];
-    }
-    if (t < S) {
-      const float yr = yv.x * rv.x - yv.y * rv.y;
-      const float yi = yv.x * rv.y + yv.y * rv.x;
-      float* yq = sY + (ybuf * (S / 2) + (t >> 1)) * 8;
-      yq[(t & 1)] = yr;
-      yq[2 + (t & 1)] = yi;
-      yq[4 + (t & 1)] = -yi;
-      yq[6 + (t & 1)] = 0.0f;
-    }
-    fence_async_smem();
+  auto load_b = [&](int c, int j) {
+    const int slot = c % NB;
+    mbar_expect_tx(&bfull[slot], S::B_BYTES);
+    ++armed[2 + slot];
+    bulk_g2s(sB + slot * NA * 2048, p.czs + (size_t)j * NA * 2048, S::B_BYTES, &bfull[slot]);
   };
-
-  for (int st = sf; st <= sl; ++st) {
-    const int tile = st / SUB, h = st % SUB;
-    const int sb = (st == sf) ? (int)(u0 - (long long)st * N) : 0;
-    const int se = (st == sl) ? (int)(u1 - (long long)st * N) : N;
-    const int nch = (se - sb + S - 1) / S;
-
-    fetch(tile, sb, se);
-    // A: this thread's MB pixels as split-tf32 rows of the MB M-blocks
-    {
-      float z[D][MB];
-      const float* src = p.v.dz + ((size_t)tile * 128 + t) * D * 8 + h * MB;
-#pragma unroll
-      for (int d = 0; d < D; ++d) {
-        if constexpr (MB == 4) {
-          const float4 q = __ldg(reinterpret_cast<const float4*>(src + d * 8));
-          z[d][0] = q.x; z[d][1] = q.y; z[d][2] = q.z; z[d][3] = q.w;
-        } else {
-          const float2 q = __ldg(reinterpret_cast<const float2*>(src + d * 8));
-          z[d][0] = q.x; z[d][MB - 1] = q.y;
-        }
-      }
-#pragma unroll
-      for (int b = 0; b < MB; ++b) {
-        float row[KP];
-#pragma unroll
-        for (int d = 0; d < D; ++d) {
-          const float hi = to_tf32(z[d][b]);
-          row[d] = hi;
-          row[D + d] = to_tf32(z[d][b] - hi);
-          row[2 * D + d] = hi;
-        }
-#pragma unroll
-        for (int k = 3 * D; k < KP; ++k) row[k] = 0.0f;
-#pragma unroll
-        for (int j = 0; j < KP / 4; ++j) {
-          const int atom = (4 * j) / 32, kk = (4 * j) % 32;
-          *reinterpret_cast<float4*>(sA + (b * NA + atom) * 4096 + swz128(t, kk)) =
-              make_float4(row[4 * j], row[4 * j + 1], row[4 * j + 2], row[4 * j + 3]);
-        }
-      }
-    }
-    put(0, 0);
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-
-    float2 re2[MB], im2[MB];
-#pragma unroll
-    for (int b = 0; b < MB; ++b) re2[b] = im2[b] = make_float2(0.0f, 0.0f);
-
-    for (int c = 0; c <= nch; ++c) {
-      // B(c) and y'(c) are in shared memory (previous barrier): start MMA(c)
-      if (c < nch && t == 0) {
-        const int buf = c & 1;
-#pragma unroll
-        for (int b = 0; b < MB; ++b) {
-#pragma unroll
-          for (int ks = 0; ks < KP / 8; ++ks) {
-            const int atom = ks / 4, koff = (ks % 4) * 32;
-            const uint64_t ad = umma_desc(smem_u32(sA + (b * NA + atom) * 4096) + koff);
-            const uint64_t bd = umma_desc(smem_u32(sB + (buf * NA + atom) * (S * 32)) + koff);
-            umma_tf32(tmem + (uint32_t)(buf * MB * S + b * S), ad, bd, IDESC, ks > 0 ? 1u : 0u);
-          }
-        }
-        umma_commit(&mbar[buf]);
-      }
-      // loads for chunk c + 1 in flight while chunk c - 1 is consumed
-      if (c + 1 < nch) fetch(tile, sb + (c + 1) * S, se);
-      if (c >= 1) {
-        const int buf = (c - 1) & 1, ybuf = (c - 1) % 3;
-        ok = mbar_wait(&mbar[buf], (parity >> buf) & 1u, kTcWaitPolls) && ok;
-        parity ^= 1u << buf;
-        tc_fence_after();
-        float2 yr2[S / 2], yi2[S / 2], nyi2[S / 2];
-#pragma unroll
-        for (int q = 0; q < S / 2; ++q) {
-          const float4 a = *reinterpret_cast<const float4*>(sY + (ybuf * (S / 2) + q) * 8);
-          const float4 bq = *reinterpret_cast<const float4*>(sY + (ybuf * (S / 2) + q) * 8 + 4);
-          yr2[q] = make_float2(a.x, a.y);
-          yi2[q] = make_float2(a.z, a.w);
-          nyi2[q] = make_float2(bq.x, bq.y);
-        }
-        uint32_t xr[MB][16];
-#pragma unroll
-        for (int b = 0; b < MB; ++b) tmem_ld16_nowait(tmem + tlane + (uint32_t)(buf * MB * S + b * S), xr[b]);
-        tmem_wait();
-#pragma unroll
-        for (int b = 0; b < MB; ++b) {
-#pragma unroll
-          for (int q = 0; q < S / 2; ++q) {
-            float2 sn, cs;
-            sincos2(make_float2(__uint_as_float(xr[b][2 * q]), __uint_as_float(xr[b][2 * q + 1])), sn, cs);
-            re2[b] = fma2(yr2[q], cs, re2[b]);
-            re2[b] = fma2(nyi2[q], sn, re2[b]);
-            im2[b] = fma2(yi2[q], cs, im2[b]);
-            im2[b] = fma2(yr2[q], sn, im2[b]);
-          }
-        }
-      }
-      // chunk c + 1 into buffer (c + 1) & 1: its previous user, MMA(c - 1), is
-      // complete (this thread waited for it just above)
-      if (c + 1 < nch) put((c + 1) & 1, (c + 1) % 3);
-      tc_fence_before();
-      __syncthreads();
+  auto issue_upto = [&](int upto) -> bool {
+    bool r = true;
+    int k = pst[0], s = pst[1], j = pst[2];
+    for (; k <= upto && k < nc; ++k) {
+      const int ls = s - s0;
+      r = mbar_wait(&bfull[k % NB], (uint32_t)((k / NB) & 1), kTcWaitPolls) && r;
+      if (k == 0 || j == 0) r = mbar_wait(&afull[ls & 1], (uint32_t)((ls >> 1) & 1), kTcWaitPolls) && r;
       tc_fence_after();
+      ++armed[k & 1];
+      tc_mma_chunk<NA>(tmem + (uint32_t)((k & 1) * kTcChunk), sA + (ls & 1) * NA * 4096, sB + (k % NB) * NA * 2048,
+                       &full[k & 1]);
+      if (++j == nch) {
+        j = 0;
+        ++s;
+      }
     }
+    pst[0] = k;
+    pst[1] = s;
+    pst[2] = j;
+    return r;
+  };
 
-    // epilogue (whole spot range owned) or partial sums for the fix-up
-    const bool full = (sb == 0 && se == N);
-    const int tx = tile % G.tiles_x, ty = tile / G.tiles_x;
-    const int i = tx * kTileX + lane;
-    float2* slot = p.split + ((size_t)blockIdx.x * 2 + (st == sf ? 0 : 1)) * kTilePix;
+  int jb = j0;                       // spot chunk of chunk c + NB (the next B to load)
+  for (int k = 0; k < NB; ++k)
+    if (++jb == nch) jb = 0;
+  if (t == 0 && nc > 0) {
+    pst[0] = 0;
+    pst[1] = s0;
+    pst[2] = j0;
+    load_a(s0);
+    if (s0 + 1 <= s_last) load_a(s0 + 1);
+    for (int c = 0, j = j0; c < NB && c < nc; ++c, j = (j + 1 == nch ? 0 : j + 1)) load_b(c, j);
+    ok = issue_upto(0);
+  }
+
+  float4* yw = sY + w * 32;   // this warp's (yr, yr', yi, yi') of 32 spot pairs
+  float2 B1 = make_float2(0.0f, 0.0f), B2 = B1, B3 = B1, B4 = B1;
+  // y and exp(+i 2 pi base) of spots (n0 + 2 lane, n0 + 2 lane + 1) of
+  // chunk j of group s
+  auto fetch_y = [&](bool in, int s, int j, float4& yv, float4& rv) {
+    yv = rv = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (!in) return;
+    const int tile = s / kTcGroupsPerTile;
+    const int n = j * kTcChunk + 2 * lane;
+    if (n < N) {
+      const float2 a = __ldg(p.y + n), b = __ldg(p.rot + (size_t)tile * N + n);
+      yv.x = a.x; yv.y = a.y; rv.x = b.x; rv.y = b.y;
+    }
+    if (n + 1 < N) {
+      const float2 a = __ldg(p.y + n + 1), b = __ldg(p.rot + (size_t)tile * N + n + 1);
+      yv.z = a.x; yv.w = a.y; rv.z = b.x; rv.w = b.y;
+    }
+  };
+  float4 yv, rv;
+  fetch_y(nc > 0, s0, j0, yv, rv);
+
+  int s = s0, jch = j0;              // group and spot chunk of chunk c
+  for (int c = 0; c < nc; ++c) {
+    const bool last_of_group = jch + 1 == nch || c == nc - 1;
+    const int s_next = jch + 1 == nch ? s + 1 : s, j_next = jch + 1 == nch ? 0 : jch + 1;
+    const int valid = min(kTcChunk, N - jch * kTcChunk);
+    const int nq = (valid + 15) >> 4;
+    uint32_t x[4][16];
+    ok = ok && mbar_wait(&full[c & 1], (uint32_t)((c >> 1) & 1), kTcWaitPolls);
+    tc_fence_after();
+    tc_load_cols(tmem + tlane + (uint32_t)((c & 1) * kTcChunk), 0, nq, x);
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0 && (atom_add_acq_rel_smem(&cnt[c & 1], 1u) & 3u) == 3u) {
+      // every warp is done with TMEM buffer c & 1; MMA(c) has completed
+      tc_fence_after();
+      if (c + NB < nc) load_b(c + NB, jb);
+      if (last_of_group && s + 2 <= s_last) load_a(s + 2);   // every MMA of group s is complete
+      ok = issue_upto(c + 1) && ok;
+    }
+    __syncwarp();
+    if (++jb == nch) jb = 0;
+    // y' = y exp(+i 2 pi base) of this chunk into the warp's slot
+    yw[lane] = make_float4(yv.x * rv.x - yv.y * rv.y, yv.z * rv.z - yv.w * rv.w, yv.x * rv.y + yv.y * rv.x,
+                           yv.z * rv.w + yv.w * rv.z);
+    __syncwarp();
+    fetch_y(c + 1 < nc, s_next, j_next, yv, rv);
 #pragma unroll
-    for (int b = 0; b < MB; ++b) {
-      const float gr = re2[b].x + re2[b].y, gi = im2[b].x + im2[b].y;
-      if (full) {
-        const int k = h * MB + b;
-        const int j = ty * kTileY + w + 4 * k;
-        if (i < G.nx && j < G.ny) {
-          const float a = (p.out.epilogue & kEpiGradPhase) ? __ldg(p.v.amp_img + ((size_t)tile * 128 + t) * 8 + k) : 0.0f;
-          adjoint_epilogue(p.out, (size_t)j * G.nx + i, gr, gi, a);
+    for (int q = 0; q < 4; ++q) {
+      if (q < nq) {
+#pragma unroll
+        for (int pp = 0; pp < 8; ++pp) {
+          const float4 yq = yw[8 * q + pp];
+          const float2 yr = make_float2(yq.x, yq.y), yi = make_float2(yq.z, yq.w);
+          float2 sn, cs;
+          sincos2(make_float2(__uint_as_float(x[q][2 * pp]), __uint_as_float(x[q][2 * pp + 1])), sn, cs);
+          // y exp(+i x) = (yr cs - yi sn) + i (yi cs + yr sn)
+          B1 = fma2(yr, cs, B1);
+          B2 = fma2(yi, sn, B2);
+          B3 = fma2(yi, cs, B3);
+          B4 = fma2(yr, sn, B4);
         }
+      }
+    }
+    __syncwarp();   // the slot is rewritten for the next chunk
+    if (last_of_group) {
+      const float gr = (B1.x + B1.y) - (B2.x + B2.y), gi = (B3.x + B3.y) + (B4.x + B4.y);
+      B1 = B2 = B3 = B4 = make_float2(0.0f, 0.0f);
+      if ((long long)s * nch >= u0 && (long long)(s + 1) * nch <= u1) {
+        tc_adjoint_epilogue(p, 2LL * s + (t >> 6), t & 63, gr, gi);
       } else {
-        slot[b * kTcThreads + t] = make_float2(gr, gi);
+        p.split[((size_t)blockIdx.x * 2 + (s == s0 ? 0 : 1)) * kTcRows + t] = make_float2(gr, gi);
       }
     }
+    s = s_next;
+    jch = j_next;
   }
   tc_fence_before();
   __syncthreads();
-  if (w == 0) tmem_dealloc(tmem, NCOLS);
+  if (t == 0) tc_drain(bars, armed, NBARS);
+  __syncwarp();
+  if (w == 0) tmem_dealloc(tmem, 2 * kTcChunk);
   if (!ok && t == 0) atomicOr(p.err, kErrTimeout);
 }
 
-// Forward: partial[(sub-tile, warp)][2n..2n+1] = exp(-i 2 pi base(n, tile))
-// x sum over the warp's pixels of the sub-tile of f_m exp(-i dZ_m . C_n).
-template <int D>
-__global__ void __launch_bounds__(kTcThreads, 3) k_tc_forward(const TcFwdParams p) {
-  constexpr int KP = tc_kp(D), MB = tc_mb(D), NA = KP / 32, SUB = tc_sub(D), S = kTcS;
-  constexpr uint32_t NCOLS = 2 * MB * S;
-  constexpr uint32_t IDESC = umma_idesc_tf32(128, S);
-  constexpr int BV = NA * S * 8 / kTcThreads;
+// Groups whose spots were split between CTAs of k_tc_adjoint: the partial
+// sums in CTA order, then the epilogue. One CTA of 128 threads per split group.
+static __global__ void k_tc_adjoint_fixup(const TcAdjParams p) {
+  const int nch = (p.g.N + kTcChunk - 1) / kTcChunk;
+  const long long s = p.split_groups[blockIdx.x], ulo = s * nch, uhi = ulo + nch - 1;
+  const int t = threadIdx.x;
+  const int b_lo = p.sched.owner(ulo), b_hi = p.sched.owner(uhi);
+  float gr = 0.0f, gi = 0.0f;
+  for (int cb = b_lo; cb <= b_hi; ++cb) {
+    const long long beg = p.sched.begin(cb);
+    if (p.sched.begin(cb + 1) <= beg) continue;
+    const float2 v = p.split[((size_t)cb * 2 + (beg >= ulo ? 0 : 1)) * kTcRows + t];
+    gr += v.x;
+    gi += v.y;
+  }
+  tc_adjoint_epilogue(p, 2 * s + (t >> 6), t & 63, gr, gi);
+}
+
+// --- forward ------------------------------------------------------------------
+
+// E_n = sum_m f_m exp(-i C_n . Z_m) over this CTA's (spot block, pixel chunk)
+// range; blocks whose pixels are split between CTAs go through `part` and
+// k_tc_forward_reduce.
+//
+// Producer schedule (the warp releasing chunk c last): B of chunk c + NBB
+// into the slot MMA(c) has freed, f of chunk c + NF - 1 into the slot of
+// chunk c - 1 (every warp has finished reading it), and the MMAs up to chunk
+// c + 2. A spot block's first MMA waits until the previous block's last MMA
+// has completed, then its A is reloaded (once per block change).
+template <int NA>
+__global__ void __launch_bounds__(kTcThreads, 4) k_tc_forward(const TcFwdParams p) {
+  using S = TcFwdShape<NA>;
+  constexpr int NBB = S::NBB, NF = S::NF, NBARS = S::NBARS;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  float* sA = reinterpret_cast<float*>(base);
-  float* sB = sA + MB * NA * 4096;
-  float* sY = sB + 2 * NA * S * 32;                                  // unused by the forward
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sY + 3 * (S / 2) * 8);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+  float* sA = reinterpret_cast<float*>(base);                      // [NA][128][32]
+  float* sB = sA + NA * 4096;                                      // [NBB][NA][64][32]
+  float4* sF = reinterpret_cast<float4*>(sB + NBB * NA * 2048);    // [NF][32]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sF + NF * 32);      // full[2] | bfull[NBB] | ffull[NF] | afull
+  uint64_t* full = bars;
+  uint64_t* bfull = bars + 2;
+  uint64_t* ffull = bars + 2 + NBB;
+  uint64_t* afull = bars + 2 + NBB + NF;
+  uint32_t* armed = reinterpret_cast<uint32_t*>(bars + NBARS);
+  uint32_t* cnt = armed + NBARS;                                   // [2] arrivals per TMEM buffer
+  uint32_t* tslot = cnt + 2;
+  int* pst = reinterpret_cast<int*>(tslot + 1);   // next MMA: chunk, block, pixel chunk; block in A; A unchecked
 
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
-  if (w == 0) tmem_alloc(tslot, NCOLS);
+  const Geometry& G = p.g;
+  const int N = G.N;
+  const int nq = G.T * kTcChunksPerTile;
+  const long long u0 = p.sched.begin(blockIdx.x), u1 = p.sched.begin(blockIdx.x + 1);
+  const int nc = (int)(u1 - u0);
+  // chunk c of this range is pixel chunk q of spot block b; (b, q) advance
+  // incrementally
+  const int b0 = (int)(u0 / nq), q0 = (int)(u0 % nq);
+
+  if (w == 0) tmem_alloc(tslot, 2 * kTcChunk);
   if (t == 0) {
-    mbar_init(&mbar[0], 1);
-    mbar_init(&mbar[1], 1);
+    for (int k = 0; k < NBARS; ++k) {
+      mbar_init(&bars[k], 1);
+      armed[k] = 0;
+    }
+    cnt[0] = cnt[1] = 0;
+    fence_mbar_init();
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
   const uint32_t tlane = (uint32_t)(w * 32) << 16;
-  uint32_t parity = 0;
   bool ok = true;
 
-  const Geometry& G = p.v.g;
-  const int N = G.N;
-  const long long u0 = p.sched.begin(blockIdx.x), u1 = p.sched.begin(blockIdx.x + 1);
-  const int sf = (int)(u0 / N), sl = (int)((u1 - 1) / N);
-
-  float4 bv[BV];
-  float2 rot_next = make_float2(0.0f, 0.0f), rot_cur = make_float2(0.0f, 0.0f);
-  // loads of chunk (n0 .. n0 + S) issued one iteration ahead of their use:
-  // B rows (split coefficients) and this lane's spot rotation
-  auto fetch = [&](int tile, int n0, int se) {
-#pragma unroll
-    for (int q = 0; q < BV; ++q) {
-      const int e = t + q * kTcThreads;
-      const int atom = e / (S * 8), r = (e / 8) % S, j = e % 8;
-      const int n = n0 + r;
-      bv[q] = n < se ? __ldg(reinterpret_cast<const float4*>(p.cz + (size_t)n * KP + atom * 32 + 4 * j))
-                     : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    }
-    const int n = n0 + (lane >> 1);
-    rot_next = n < se ? __ldg(p.rot + (size_t)tile * N + n) : make_float2(1.0f, 0.0f);
+  // --- producer steps (one thread at a time) ---
+  auto load_a = [&](int b) {
+    mbar_expect_tx(afull, S::A_BYTES);
+    ++armed[NBARS - 1];
+    tc_copy_rows128<NA>(sA, p.czs + (size_t)(2 * b) * NA * 2048, afull);
   };
-  auto put = [&](int buf) {
-#pragma unroll
-    for (int q = 0; q < BV; ++q) {
-      const int e = t + q * kTcThreads;
-      const int atom = e / (S * 8), r = (e / 8) % S, j = e % 8;
-      *reinterpret_cast<float4*>(sB + (buf * NA + atom) * (S * 32) + swz128(r, 4 * j)) = bv[q];
-    }
-    fence_async_smem();
+  auto load_b = [&](int c, int q) {
+    const int slot = c % NBB;
+    mbar_expect_tx(&bfull[slot], S::B_BYTES);
+    ++armed[2 + slot];
+    bulk_g2s(sB + slot * NA * 2048, p.zs + (size_t)q * NA * 2048, S::B_BYTES, &bfull[slot]);
   };
-
-  for (int st = sf; st <= sl; ++st) {
-    const int tile = st / SUB, h = st % SUB;
-    const int sb = (st == sf) ? (int)(u0 - (long long)st * N) : 0;
-    const int se = (st == sl) ? (int)(u1 - (long long)st * N) : N;
-    const int nch = (se - sb + S - 1) / S;
-    const int tx = tile % G.tiles_x, ty = tile / G.tiles_x;
-    const int i = tx * kTileX + lane;
-
-    fetch(tile, sb, se);
-    // A rows and this thread's nearfield values (duplicated for packed FMAs)
-    float2 frr[MB], fii[MB], nfrr[MB];
-    {
-      float z[D][MB];
-      const float* src = p.v.dz + ((size_t)tile * 128 + t) * D * 8 + h * MB;
-#pragma unroll
-      for (int d = 0; d < D; ++d) {
-        if constexpr (MB == 4) {
-          const float4 q = __ldg(reinterpret_cast<const float4*>(src + d * 8));
-          z[d][0] = q.x; z[d][1] = q.y; z[d][2] = q.z; z[d][3] = q.w;
-        } else {
-          const float2 q = __ldg(reinterpret_cast<const float2*>(src + d * 8));
-          z[d][0] = q.x; z[d][MB - 1] = q.y;
-        }
+  auto load_f = [&](int c, int q) {
+    const int slot = c % NF;
+    mbar_expect_tx(&ffull[slot], S::F_BYTES);
+    ++armed[2 + NBB + slot];
+    bulk_g2s(sF + slot * 32, p.fimg + (size_t)q * 32, S::F_BYTES, &ffull[slot]);
+  };
+  auto next_q = [&](int q) { return q + 1 == nq ? 0 : q + 1; };
+  // MMAs of chunks pst[0] .. upto; `released`: the last chunk every warp has
+  // released (its MMA and all earlier ones are complete)
+  auto issue_upto = [&](int upto, int released) -> bool {
+    bool r = true;
+    int k = pst[0], b = pst[1], q = pst[2], ab = pst[3], fresh = pst[4];
+    for (; k <= upto && k < nc;) {
+      if (b != ab) {
+        if (k - 1 > released) break;   // an MMA with the old block may still be running
+        load_a(b);
+        ab = b;
+        fresh = 1;
       }
-#pragma unroll
-      for (int b = 0; b < MB; ++b) {
-        float row[KP];
-#pragma unroll
-        for (int d = 0; d < D; ++d) {
-          const float hi = to_tf32(z[d][b]);
-          row[d] = hi;
-          row[D + d] = to_tf32(z[d][b] - hi);
-          row[2 * D + d] = hi;
-        }
-#pragma unroll
-        for (int k = 3 * D; k < KP; ++k) row[k] = 0.0f;
-#pragma unroll
-        for (int j = 0; j < KP / 4; ++j) {
-          const int atom = (4 * j) / 32, kk = (4 * j) % 32;
-          *reinterpret_cast<float4*>(sA + (b * NA + atom) * 4096 + swz128(t, kk)) =
-              make_float4(row[4 * j], row[4 * j + 1], row[4 * j + 2], row[4 * j + 3]);
-        }
-        const int k = h * MB + b;
-        const int j = ty * kTileY + w + 4 * k;
-        const bool valid = (i < G.nx) && (j < G.ny);
-        const size_t m = (size_t)j * G.nx + i;
-        float fr = 0.0f, fi = 0.0f;
-        if (valid) {
-          if (p.source == kSrcPhase) {
-            const float a = __ldg(p.v.amp_img + ((size_t)tile * 128 + t) * 8 + k);
-            float sn, cs;
-            sincosf(__ldg(p.phase + m), &sn, &cs);
-            fr = a * cs;
-            fi = a * sn;
-          } else {
-            const float2 f = __ldg(p.field + m);
-            fr = f.x;
-            fi = f.y;
-          }
-        }
-        frr[b] = make_float2(fr, fr);
-        fii[b] = make_float2(fi, fi);
-        nfrr[b] = make_float2(-fr, -fr);
+      r = mbar_wait(&bfull[k % NBB], (uint32_t)((k / NBB) & 1), kTcWaitPolls) && r;
+      if (fresh) {
+        r = mbar_wait(afull, (uint32_t)((b - b0) & 1), kTcWaitPolls) && r;
+        fresh = 0;
       }
-    }
-    put(0);
-    rot_cur = rot_next;
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    float* prow = p.partial + ((size_t)st * 4 + w) * 2 * N;
-
-    for (int c = 0; c <= nch; ++c) {
-      if (c < nch && t == 0) {
-        const int buf = c & 1;
-#pragma unroll
-        for (int b = 0; b < MB; ++b) {
-#pragma unroll
-          for (int ks = 0; ks < KP / 8; ++ks) {
-            const int atom = ks / 4, koff = (ks % 4) * 32;
-            const uint64_t ad = umma_desc(smem_u32(sA + (b * NA + atom) * 4096) + koff);
-            const uint64_t bd = umma_desc(smem_u32(sB + (buf * NA + atom) * (S * 32)) + koff);
-            umma_tf32(tmem + (uint32_t)(buf * MB * S + b * S), ad, bd, IDESC, ks > 0 ? 1u : 0u);
-          }
-        }
-        umma_commit(&mbar[buf]);
-      }
-      // rot_cur belongs to chunk c - 1 (consumed below); chunk c's is in rot_next
-      const float2 rot_use = rot_cur;
-      rot_cur = rot_next;
-      if (c + 1 < nch) fetch(tile, sb + (c + 1) * S, se);
-      if (c >= 1) {
-        const int buf = (c - 1) & 1, n0 = sb + (c - 1) * S;
-        ok = mbar_wait(&mbar[buf], (parity >> buf) & 1u, kTcWaitPolls) && ok;
-        parity ^= 1u << buf;
-        tc_fence_after();
-        uint32_t xr[MB][16];
-#pragma unroll
-        for (int b = 0; b < MB; ++b) tmem_ld16_nowait(tmem + tlane + (uint32_t)(buf * MB * S + b * S), xr[b]);
-        tmem_wait();
-        float2 re2[S / 2], im2[S / 2];
-#pragma unroll
-        for (int q = 0; q < S / 2; ++q) {
-          re2[q] = im2[q] = make_float2(0.0f, 0.0f);
-#pragma unroll
-          for (int b = 0; b < MB; ++b) {
-            float2 sn, cs;
-            sincos2(make_float2(__uint_as_float(xr[b][2 * q]), __uint_as_float(xr[b][2 * q + 1])), sn, cs);
-            // f exp(-i x) = (fr cs + fi sn) + i (fi cs - fr sn)
-            re2[q] = fma2(frr[b], cs, re2[q]);
-            re2[q] = fma2(fii[b], sn, re2[q]);
-            im2[q] = fma2(fii[b], cs, im2[q]);
-            im2[q] = fma2(nfrr[b], sn, im2[q]);
-          }
-        }
-        float acc[32];
-#pragma unroll
-        for (int q = 0; q < S / 2; ++q) {
-          acc[4 * q] = re2[q].x;
-          acc[4 * q + 1] = im2[q].x;
-          acc[4 * q + 2] = re2[q].y;
-          acc[4 * q + 3] = im2[q].y;
-        }
-        const float v = warp_transpose_reduce32(acc, lane);
-        const float other = __shfl_xor_sync(kFull, v, 1);
-        const bool is_im = (lane & 1) != 0;
-        const int n = n0 + (lane >> 1);
-        if (n < se) {
-          const float re = is_im ? other : v;
-          const float im = is_im ? v : other;
-          // exp(+i 2 pi base) was loaded one iteration ago: multiply by its conjugate
-          prow[2 * n + (lane & 1)] = is_im ? fmaf(im, rot_use.x, -re * rot_use.y) : fmaf(re, rot_use.x, im * rot_use.y);
-        }
-      }
-      if (c + 1 < nch) put((c + 1) & 1);
-      tc_fence_before();
-      __syncthreads();
       tc_fence_after();
+      ++armed[k & 1];
+      tc_mma_chunk<NA>(tmem + (uint32_t)((k & 1) * kTcChunk), sA, sB + (k % NBB) * NA * 2048, &full[k & 1]);
+      ++k;
+      if (++q == nq) {
+        q = 0;
+        ++b;
+      }
+    }
+    pst[0] = k;
+    pst[1] = b;
+    pst[2] = q;
+    pst[3] = ab;
+    pst[4] = fresh;
+    return r;
+  };
+
+  int qb = q0, qf = q0;              // pixel chunks of chunks c + NBB and c + NF - 1 (the next to load)
+  for (int k = 0; k < NBB; ++k) qb = next_q(qb);
+  for (int k = 0; k < NF - 1; ++k) qf = next_q(qf);
+  if (t == 0 && nc > 0) {
+    pst[0] = 0;
+    pst[1] = b0;
+    pst[2] = q0;
+    pst[3] = b0;
+    pst[4] = 1;
+    load_a(b0);
+    for (int c = 0, q = q0; c < NBB && c < nc; ++c, q = next_q(q)) load_b(c, q);
+    for (int c = 0, q = q0; c < NF - 1 && c < nc; ++c, q = next_q(q)) load_f(c, q);
+    ok = issue_upto(1, -1);
+  }
+
+  float2 A1 = make_float2(0.0f, 0.0f), A2 = A1, A3 = A1, A4 = A1;
+  float er = 0.0f, ei = 0.0f;
+  int b = b0, q = q0;                // spot block and pixel chunk of chunk c
+  for (int c = 0; c < nc; ++c) {
+    const bool wrap = q + 1 == nq;
+    uint32_t x[4][16];
+    ok = ok && mbar_wait(&full[c & 1], (uint32_t)((c >> 1) & 1), kTcWaitPolls);
+    tc_fence_after();
+    tc_load_cols(tmem + tlane + (uint32_t)((c & 1) * kTcChunk), 0, 4, x);
+    tc_fence_before();
+    __syncwarp();
+    // a warp can be one chunk ahead of another (MMAs run two chunks ahead),
+    // so arrivals are counted per TMEM buffer
+    if (lane == 0 && (atom_add_acq_rel_smem(&cnt[c & 1], 1u) & 3u) == 3u) {
+      // every warp is done with TMEM buffer c & 1 and with the f slot of
+      // chunk c - 1; MMA(c) has completed
+      tc_fence_after();
+      if (c + NBB < nc) load_b(c + NBB, qb);
+      if (c + NF - 1 < nc) load_f(c + NF - 1, qf);
+      ok = issue_upto(c + 2, c) && ok;
+    }
+    __syncwarp();
+    qb = next_q(qb);
+    qf = next_q(qf);
+    const int n = b * kTcRows + t;
+    // warps whose 32 spots are all >= N have nothing to add
+    if (b * kTcRows + 32 * w < N) {
+      ok = ok && mbar_wait(&ffull[c % NF], (uint32_t)((c / NF) & 1), kTcWaitPolls);
+      const float4* f = sF + (c % NF) * 32;
+#pragma unroll
+      for (int qq = 0; qq < 4; ++qq) {
+#pragma unroll
+        for (int pp = 0; pp < 8; ++pp) {
+          const float4 fq = f[8 * qq + pp];
+          const float2 fr = make_float2(fq.x, fq.y), fi = make_float2(fq.z, fq.w);
+          float2 sn, cs;
+          sincos2(make_float2(__uint_as_float(x[qq][2 * pp]), __uint_as_float(x[qq][2 * pp + 1])), sn, cs);
+          // f exp(-i x) = (fr cs + fi sn) + i (fi cs - fr sn)
+          A1 = fma2(fr, cs, A1);
+          A2 = fma2(fi, sn, A2);
+          A3 = fma2(fi, cs, A3);
+          A4 = fma2(fr, sn, A4);
+        }
+      }
+      if (q % kTcChunksPerTile == kTcChunksPerTile - 1 || c == nc - 1) {
+        // end of a tile: rotate by exp(-i 2 pi base(n, tile))
+        const float re = (A1.x + A1.y) + (A2.x + A2.y), im = (A3.x + A3.y) - (A4.x + A4.y);
+        A1 = A2 = A3 = A4 = make_float2(0.0f, 0.0f);
+        if (n < N) {
+          const float2 rt = __ldg(p.rot + (size_t)(q / kTcChunksPerTile) * N + n);
+          er += re * rt.x + im * rt.y;
+          ei += im * rt.x - re * rt.y;
+        }
+      }
+    }
+    if (wrap || c == nc - 1) {
+      // end of spot block b in this range
+      if ((long long)b * nq >= u0 && (long long)(b + 1) * nq <= u1) {
+        if (n < N) p.E[n] = make_float2(er, ei);
+      } else {
+        p.part[((size_t)blockIdx.x * 2 + (b == b0 ? 0 : 1)) * kTcRows + t] = make_float2(er, ei);
+      }
+      er = ei = 0.0f;
+    }
+    if (wrap) {
+      q = 0;
+      ++b;
+    } else {
+      ++q;
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (w == 0) tmem_dealloc(tmem, NCOLS);
+  if (t == 0) tc_drain(bars, armed, NBARS);
+  __syncwarp();
+  if (w == 0) tmem_dealloc(tmem, 2 * kTcChunk);
   if (!ok && t == 0) atomicOr(p.err, kErrTimeout);
 }
 
-// Finishes sub-tiles split between CTAs of k_tc_adjoint (fixed CTA order).
-// One CTA of 128 threads per sub-tile; sub-tiles owned by one CTA return.
-static __global__ void k_tc_adjoint_fixup(const TcAdjParams p, int MB) {
-  const Geometry& G = p.v.g;
-  const int SUB = 8 / MB;
-  const int st = blockIdx.x, t = threadIdx.x;
-  const long long u_lo = (long long)st * G.N, u_hi = u_lo + G.N - 1;
-  const int b_lo = p.sched.owner(u_lo), b_hi = p.sched.owner(u_hi);
-  if (b_lo == b_hi) return;
-  const int tile = st / SUB, h = st % SUB;
-  const int tx = tile % G.tiles_x, ty = tile / G.tiles_x;
-  const int i = tx * kTileX + (t & 31);
-  for (int b = 0; b < MB; ++b) {
-    float gr = 0.0f, gi = 0.0f;
-    for (int cb = b_lo; cb <= b_hi; ++cb) {
-      const int slot = (p.sched.begin(cb) >= u_lo) ? 0 : 1;
-      const float2 v = p.split[((size_t)cb * 2 + slot) * kTilePix + b * kTcThreads + t];
-      gr += v.x;
-      gi += v.y;
+// Spot blocks whose pixels were split between CTAs of k_tc_forward: E_n is
+// the sum of the CTAs' partial sums. CTA (b, y) sums 32 spots of block b:
+// row-lane k of the 32 x 32 threads adds the partials of CTAs g_lo + k,
+// g_lo + k + 32, ..., then a fixed-shape tree combines the row-lanes.
+static __global__ void k_tc_forward_reduce(const TcFwdParams p) {
+  __shared__ float2 acc[32][33];
+  const int nq = p.g.T * kTcChunksPerTile;
+  const long long b = blockIdx.x, ulo = b * nq, uhi = ulo + nq - 1;
+  const int col = blockIdx.y * 32 + threadIdx.x, k = threadIdx.y;
+  // owners of the block's first and last units (binary search on the table)
+  auto owner = [&](long long u) {
+    int lo = 0, hi = p.sched.G - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (p.begin[mid] <= u) lo = mid;
+      else hi = mid - 1;
     }
-    const int k = h * MB + b;
-    const int j = ty * kTileY + (t >> 5) + 4 * k;
-    if (i >= G.nx || j >= G.ny) continue;
-    const float a = (p.out.epilogue & kEpiGradPhase) ? p.v.amp_img[((size_t)tile * 128 + t) * 8 + k] : 0.0f;
-    adjoint_epilogue(p.out, (size_t)j * G.nx + i, gr, gi, a);
+    return lo;
+  };
+  const int g_lo = owner(ulo), g_hi = owner(uhi);
+  if (g_lo == g_hi) return;   // one CTA owned the block and wrote E itself
+  float2 v = make_float2(0.0f, 0.0f);
+  for (int cb = g_lo + k; cb <= g_hi; cb += 32) {
+    const long long beg = p.begin[cb];
+    if (p.begin[cb + 1] <= beg) continue;
+    const float2 x = p.part[((size_t)cb * 2 + (beg >= ulo ? 0 : 1)) * kTcRows + col];
+    v.x += x.x;
+    v.y += x.y;
   }
+  acc[k][threadIdx.x] = v;
+  __syncthreads();
+  for (int h = 16; h > 0; h >>= 1) {
+    if (k < h) {
+      acc[k][threadIdx.x].x += acc[k + h][threadIdx.x].x;
+      acc[k][threadIdx.x].y += acc[k + h][threadIdx.x].y;
+    }
+    __syncthreads();
+  }
+  const int n = (int)(b * kTcRows) + col;
+  if (k == 0 && n < p.g.N) p.E[n] = acc[0][threadIdx.x];
 }
 
 }  // namespace ash

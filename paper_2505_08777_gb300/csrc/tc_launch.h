@@ -1,0 +1,117 @@
+// Tensor-core transform path: shapes, operand-image layouts, schedules,
+// parameter blocks and launchers (kernels in tc_kernels.cuh, tc.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace ash {
+
+constexpr int kTcThreads = 128;
+constexpr int kTcRows = 128;                           // M of one MMA
+constexpr int kTcChunk = 64;                           // N of one MMA
+constexpr int kTcChunksPerTile = kTilePix / kTcChunk;  // 16 chunks of 64 pixels
+constexpr int kTcGroupsPerTile = kTilePix / kTcRows;   // 8 groups of 128 pixels
+constexpr unsigned kTcWaitPolls = 1u << 24;
+constexpr unsigned kErrTimeout = 2u;
+constexpr int kTcMaxModes = 21;                        // 3 D <= 64
+
+// K-atoms of 32 tf32 per operand row: the row [hi | lo | hi] (pixels) or
+// [hi | hi | lo] (spots) of 3 D values, zero-padded.
+__host__ __device__ constexpr int tc_na(int D) { return 3 * D <= 32 ? 1 : 2; }
+
+// Operand images in HBM (floats), each [chunks][NA][64 rows][32] with the
+// 128-byte swizzle of tc_common.cuh:
+//  zs  : pixel rows, chunk qc = 16 tile + 2 h + half (see tc_pixel);
+//  czs : spot rows, chunk j = spots 64 j .. 64 j + 63 (an even number of
+//        chunks, rows >= N zero, so a 128-spot block is two chunks);
+//  fimg: the nearfield f_m of each pixel chunk as 32 float4 (fr, fr', fi, fi')
+//        of pixel pairs (2p, 2p + 1).
+inline size_t tc_zs_floats(const Geometry& g) { return (size_t)g.T * kTcChunksPerTile * tc_na(g.D) * 2048; }
+inline int tc_spot_chunks(int N) { return 2 * ((N + kTcRows - 1) / kTcRows); }
+inline size_t tc_czs_floats(int N, int D) { return (size_t)tc_spot_chunks(N) * tc_na(D) * 2048; }
+inline size_t tc_fimg_float4s(const Geometry& g) { return (size_t)g.T * kTilePix / 2; }
+
+// Pixel of row r of chunk qc (tile, group h, half): column r % 32, row
+// 4 h + 2 half + r / 32 of the tile; `img` is its index in the register-image
+// arrays of the FMA kernels (thread t, slot k, P pixels a thread).
+struct TcPixel {
+  int i, j, tile, img;
+};
+__host__ __device__ inline TcPixel tc_pixel(const Geometry& G, long long qc, int r) {
+  TcPixel px;
+  px.tile = (int)(qc / kTcChunksPerTile);
+  const int w = (int)(qc % kTcChunksPerTile);
+  const int h = w >> 1, half = w & 1;
+  const int col = r & 31, row = 4 * h + 2 * half + (r >> 5);
+  px.i = (px.tile % G.tiles_x) * kTileX + col;
+  px.j = (px.tile / G.tiles_x) * kTileY + row;
+  const int rows_per_k = G.NT / 32;
+  const int t = (row % rows_per_k) * 32 + col, k = row / rows_per_k;
+  px.img = (px.tile * G.NT + t) * G.P + k;
+  return px;
+}
+
+// Forward schedule: units (spot block b, pixel chunk q), u = b * nq + q, in
+// equal ranges per CTA. A chunk of a partial last block costs as much time
+// as a full one: its time is set by its busiest warp, and the warps share
+// their SM sub-partitions with the other resident CTAs.
+struct TcFwdSched {
+  int nb, nq, G;
+  __host__ __device__ long long units() const { return (long long)nb * nq; }
+  __host__ __device__ long long begin(int g) const { return (long long)g * units() / G; }
+  // the CTA whose (non-empty) range contains u
+  __host__ __device__ int owner(long long u) const {
+    int lo = 0, hi = G - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (begin(mid) <= u) lo = mid;
+      else hi = mid - 1;
+    }
+    return lo;
+  }
+};
+
+struct TcAdjParams {
+  Geometry g;
+  const float* zs;
+  const float* czs;
+  const float2* rot;      // [T][N] exp(+i 2 pi base(n, tile))
+  const float2* y;        // [N]
+  const float* amp_img;   // register-image amplitude
+  AdjOut out;
+  float4* fimg;           // written for kEpiFimg
+  Schedule sched;         // units (group, spot chunk of 64): W = T * 8 * ceil(N / 64)
+  float2* split;          // [G][2][128] partial sums of groups split between CTAs
+  const int* split_groups;   // the groups whose spots span two or more CTA ranges
+  unsigned* err;
+};
+
+struct TcFwdParams {
+  Geometry g;
+  const float* zs;
+  const float* czs;
+  const float2* rot;
+  const float4* fimg;
+  TcFwdSched sched;
+  const long long* begin; // [G + 1] sched.begin(g), tabulated on the host
+  float2* E;              // [N]
+  float2* part;           // [G][2][128] partial sums of spot blocks split between CTAs
+  unsigned* err;
+};
+
+// Kernel set-up for operand rows of NA K-atoms: shared-memory limits, and
+// resident CTAs per SM from registers, shared memory and TMEM columns.
+cudaError_t tc_prepare(int NA, int* adj_ctas_per_sm, int* fwd_ctas_per_sm);
+cudaError_t tc_launch_adjoint(int NA, const TcAdjParams& p, int grid, cudaStream_t s);
+cudaError_t tc_launch_adjoint_fixup(const TcAdjParams& p, int n_split_groups, cudaStream_t s);
+cudaError_t tc_launch_forward(int NA, const TcFwdParams& p, int grid, cudaStream_t s);
+cudaError_t tc_launch_forward_reduce(const TcFwdParams& p, cudaStream_t s);
+cudaError_t tc_build_zs(const Geometry& g, const float* dz, float* zs, cudaStream_t s);
+cudaError_t tc_build_coeff(const Geometry& g, const float* coeff, const float2* anchors, float* czs, float2* rot,
+                           cudaStream_t s);
+cudaError_t tc_field_img(const Geometry& g, const float* amp_img, const float* phase, const float2* field,
+                         float4* fimg, cudaStream_t s);
+
+}  // namespace ash

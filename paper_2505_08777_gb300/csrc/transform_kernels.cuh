@@ -119,13 +119,6 @@ __device__ __forceinline__ float2 local_phase(const float2 (&cc)[D], const float
   return x;
 }
 
-__device__ __forceinline__ void sincos2(float2 x, float2& s, float2& c) {
-  s.x = __sinf(x.x);
-  c.x = __cosf(x.x);
-  s.y = __sinf(x.y);
-  c.y = __cosf(x.y);
-}
-
 // ---------------------------------------------------------------------------
 // Nearfield pairs f = A exp(i phase) (or a caller field) of a thread's P pixels.
 template <int P>
