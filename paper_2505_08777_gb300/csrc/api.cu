@@ -168,6 +168,7 @@ TcFwdParams tc_fwd_params(const ash_hologram* h, float2* E) {
   p.rot = h->rot;
   p.fimg = h->fimg;
   p.sched = h->tfwd;
+  p.rep = tc_fwd_rep(h->g.N);
   p.begin = h->tfwd_begin;
   p.E = E;
   p.part = h->tc_part;

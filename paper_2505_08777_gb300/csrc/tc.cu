@@ -91,7 +91,8 @@ cudaError_t tc_build_zs(const Geometry& g, const float* dz, float* zs, cudaStrea
 cudaError_t tc_build_coeff(const Geometry& g, const float* coeff, const float2* anchors, float* czs, float2* rot,
                            cudaStream_t s) {
   const int nc64 = tc_spot_chunks(g.N);
-  k_tc_build_czs<<<blocks_for((long long)nc64 * kTcChunk, 256), 256, 0, s>>>(coeff, g.N, g.D, tc_na(g.D), nc64, czs);
+  k_tc_build_czs<<<blocks_for((long long)(nc64 + 2) * kTcChunk, 256), 256, 0, s>>>(coeff, g.N, g.D, tc_na(g.D), nc64,
+                                                                                 tc_fwd_rep(g.N), czs);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const long long nr = (long long)g.N * g.T;

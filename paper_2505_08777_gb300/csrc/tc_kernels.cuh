@@ -87,12 +87,16 @@ static __global__ void k_tc_build_zs(const Geometry G, const float* __restrict__
     }
 }
 
-// czs from the coefficients: one thread per (spot chunk, row); rows >= N are 0.
-static __global__ void k_tc_build_czs(const float* __restrict__ coeff, int N, int D, int NA, int nc64,
+// czs from the coefficients: one thread per (spot chunk, row); rows >= N are
+// 0. The two chunks after the nc64 main ones hold the last 128-spot block
+// with its first 128 / rep spots repeated rep times.
+static __global__ void k_tc_build_czs(const float* __restrict__ coeff, int N, int D, int NA, int nc64, int rep,
                                       float* __restrict__ czs) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (long long)nc64 * kTcChunk) return;
-  const int jc = (int)(e / kTcChunk), r = (int)(e % kTcChunk), n = jc * kTcChunk + r;
+  if (e >= (long long)(nc64 + 2) * kTcChunk) return;
+  const int jc = (int)(e / kTcChunk), r = (int)(e % kTcChunk);
+  int n = jc * kTcChunk + r;
+  if (jc >= nc64) n = (nc64 - 2) * kTcChunk + ((jc - nc64) * kTcChunk + r) % (kTcRows / rep);
   float* dst = czs + (size_t)jc * NA * 2048;
   for (int a = 0; a < NA; ++a)
     for (int kk = 0; kk < 32; ++kk) {
@@ -155,6 +159,11 @@ static __global__ void k_tile_rotations(const float* __restrict__ coeff, const f
 }
 
 // --- pieces shared by the two kernels ------------------------------------------
+
+template <bool V>
+struct BoolTag {
+  static constexpr bool value = V;
+};
 
 // D[tmem] = A[128 rows] . B[64 rows]^T over KP = 32 NA, issued by one thread.
 template <int NA>
@@ -485,10 +494,13 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_tc_forward(const TcFwdParams 
   bool ok = true;
 
   // --- producer steps (one thread at a time) ---
+  const int nb = p.sched.nb;
+  // the last block uses its replicated image (chunks 2 nb, 2 nb + 1)
   auto load_a = [&](int b) {
     mbar_expect_tx(afull, S::A_BYTES);
     ++armed[NBARS - 1];
-    tc_copy_rows128<NA>(sA, p.czs + (size_t)(2 * b) * NA * 2048, afull);
+    const int chunk = (b == nb - 1 && p.rep > 1) ? 2 * nb : 2 * b;
+    tc_copy_rows128<NA>(sA, p.czs + (size_t)chunk * NA * 2048, afull);
   };
   auto load_b = [&](int c, int q) {
     const int slot = c % NBB;
@@ -555,79 +567,117 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_tc_forward(const TcFwdParams 
   float2 A1 = make_float2(0.0f, 0.0f), A2 = A1, A3 = A1, A4 = A1;
   float er = 0.0f, ei = 0.0f;
   int b = b0, q = q0;                // spot block and pixel chunk of chunk c
-  for (int c = 0; c < nc; ++c) {
-    const bool wrap = q + 1 == nq;
-    uint32_t x[4][16];
-    ok = ok && mbar_wait(&full[c & 1], (uint32_t)((c >> 1) & 1), kTcWaitPolls);
-    tc_fence_after();
-    tc_load_cols(tmem + tlane + (uint32_t)((c & 1) * kTcChunk), 0, 4, x);
-    tc_fence_before();
-    __syncwarp();
-    // a warp can be one chunk ahead of another (MMAs run two chunks ahead),
-    // so arrivals are counted per TMEM buffer
-    if (lane == 0 && (atom_add_acq_rel_smem(&cnt[c & 1], 1u) & 3u) == 3u) {
-      // every warp is done with TMEM buffer c & 1 and with the f slot of
-      // chunk c - 1; MMA(c) has completed
+  // chunks [0, c_rep) belong to full blocks, [c_rep, nc) to the replicated
+  // last block; the two passes are compiled separately
+  const int c_rep = p.rep > 1 ? (int)min((long long)nc, max(0LL, (long long)(nb - 1) * nq - u0)) : nc;
+  const bool had_rep = c_rep < nc;
+  auto chunks = [&](auto tag, int c_beg, int c_end) {
+    constexpr bool REPL = decltype(tag)::value;
+    // replicated block: warp w takes columns [ri width, (ri + 1) width) for
+    // the spots of rows t % spb
+    const int spb = REPL ? kTcRows / p.rep : kTcRows;
+    const int ri = REPL ? w / (4 / p.rep) : 0;
+    const int width = REPL ? kTcChunk / p.rep : kTcChunk;
+    const int g_lo = ri * width / 16, g_hi = g_lo + width / 16;
+    for (int c = c_beg; c < c_end; ++c) {
+      const bool wrap = q + 1 == nq;
+      uint32_t x[4][16];
+      ok = ok && mbar_wait(&full[c & 1], (uint32_t)((c >> 1) & 1), kTcWaitPolls);
       tc_fence_after();
-      if (c + NBB < nc) load_b(c + NBB, qb);
-      if (c + NF - 1 < nc) load_f(c + NF - 1, qf);
-      ok = issue_upto(c + 2, c) && ok;
-    }
-    __syncwarp();
-    qb = next_q(qb);
-    qf = next_q(qf);
-    const int n = b * kTcRows + t;
-    // warps whose 32 spots are all >= N have nothing to add
-    if (b * kTcRows + 32 * w < N) {
-      ok = ok && mbar_wait(&ffull[c % NF], (uint32_t)((c / NF) & 1), kTcWaitPolls);
-      const float4* f = sF + (c % NF) * 32;
+      tc_load_cols(tmem + tlane + (uint32_t)((c & 1) * kTcChunk), REPL ? g_lo : 0, REPL ? g_hi : 4, x);
+      tc_fence_before();
+      __syncwarp();
+      // a warp can be one chunk ahead of another (MMAs run two chunks
+      // ahead), so arrivals are counted per TMEM buffer
+      if (lane == 0 && (atom_add_acq_rel_smem(&cnt[c & 1], 1u) & 3u) == 3u) {
+        // every warp is done with TMEM buffer c & 1 and with the f slot of
+        // chunk c - 1; MMA(c) has completed
+        tc_fence_after();
+        if (c + NBB < nc) load_b(c + NBB, qb);
+        if (c + NF - 1 < nc) load_f(c + NF - 1, qf);
+        ok = issue_upto(c + 2, c) && ok;
+      }
+      __syncwarp();
+      qb = next_q(qb);
+      qf = next_q(qf);
+      const int n = b * kTcRows + t % spb;
+      // warps whose 32 spots are all >= N have nothing to add
+      if (REPL || b * kTcRows + 32 * w < N) {
+        ok = ok && mbar_wait(&ffull[c % NF], (uint32_t)((c / NF) & 1), kTcWaitPolls);
+        const float4* f = sF + (c % NF) * 32;
 #pragma unroll
-      for (int qq = 0; qq < 4; ++qq) {
+        for (int qq = 0; qq < 4; ++qq) {
+          if (REPL && (qq < g_lo || qq >= g_hi)) continue;
 #pragma unroll
-        for (int pp = 0; pp < 8; ++pp) {
-          const float4 fq = f[8 * qq + pp];
-          const float2 fr = make_float2(fq.x, fq.y), fi = make_float2(fq.z, fq.w);
-          float2 sn, cs;
-          sincos2(make_float2(__uint_as_float(x[qq][2 * pp]), __uint_as_float(x[qq][2 * pp + 1])), sn, cs);
-          // f exp(-i x) = (fr cs + fi sn) + i (fi cs - fr sn)
-          A1 = fma2(fr, cs, A1);
-          A2 = fma2(fi, sn, A2);
-          A3 = fma2(fi, cs, A3);
-          A4 = fma2(fr, sn, A4);
+          for (int pp = 0; pp < 8; ++pp) {
+            const float4 fq = f[8 * qq + pp];
+            const float2 fr = make_float2(fq.x, fq.y), fi = make_float2(fq.z, fq.w);
+            float2 sn, cs;
+            sincos2(make_float2(__uint_as_float(x[qq][2 * pp]), __uint_as_float(x[qq][2 * pp + 1])), sn, cs);
+            // f exp(-i x) = (fr cs + fi sn) + i (fi cs - fr sn)
+            A1 = fma2(fr, cs, A1);
+            A2 = fma2(fi, sn, A2);
+            A3 = fma2(fi, cs, A3);
+            A4 = fma2(fr, sn, A4);
+          }
+        }
+        if (q % kTcChunksPerTile == kTcChunksPerTile - 1 || c == nc - 1) {
+          // end of a tile: rotate by exp(-i 2 pi base(n, tile))
+          const float re = (A1.x + A1.y) + (A2.x + A2.y), im = (A3.x + A3.y) - (A4.x + A4.y);
+          A1 = A2 = A3 = A4 = make_float2(0.0f, 0.0f);
+          if (n < N) {
+            const float2 rt = __ldg(p.rot + (size_t)(q / kTcChunksPerTile) * N + n);
+            er += re * rt.x + im * rt.y;
+            ei += im * rt.x - re * rt.y;
+          }
         }
       }
-      if (q % kTcChunksPerTile == kTcChunksPerTile - 1 || c == nc - 1) {
-        // end of a tile: rotate by exp(-i 2 pi base(n, tile))
-        const float re = (A1.x + A1.y) + (A2.x + A2.y), im = (A3.x + A3.y) - (A4.x + A4.y);
-        A1 = A2 = A3 = A4 = make_float2(0.0f, 0.0f);
-        if (n < N) {
-          const float2 rt = __ldg(p.rot + (size_t)(q / kTcChunksPerTile) * N + n);
-          er += re * rt.x + im * rt.y;
-          ei += im * rt.x - re * rt.y;
+      if (!REPL && (wrap || c == nc - 1)) {
+        // end of spot block b in this range
+        if ((long long)b * nq >= u0 && (long long)(b + 1) * nq <= u1) {
+          if (n < N) p.E[n] = make_float2(er, ei);
+        } else {
+          p.part[((size_t)blockIdx.x * 2 + (b == b0 ? 0 : 1)) * kTcRows + t] = make_float2(er, ei);
         }
+        er = ei = 0.0f;
       }
-    }
-    if (wrap || c == nc - 1) {
-      // end of spot block b in this range
-      if ((long long)b * nq >= u0 && (long long)(b + 1) * nq <= u1) {
-        if (n < N) p.E[n] = make_float2(er, ei);
+      if (wrap) {
+        q = 0;
+        ++b;
       } else {
-        p.part[((size_t)blockIdx.x * 2 + (b == b0 ? 0 : 1)) * kTcRows + t] = make_float2(er, ei);
+        ++q;
       }
-      er = ei = 0.0f;
     }
-    if (wrap) {
-      q = 0;
-      ++b;
-    } else {
-      ++q;
-    }
-  }
+  };
+  chunks(BoolTag<false>{}, 0, c_rep);
+  if (had_rep) chunks(BoolTag<true>{}, c_rep, nc);
   tc_fence_before();
   __syncthreads();
   if (t == 0) tc_drain(bars, armed, NBARS);
   __syncwarp();
   if (w == 0) tmem_dealloc(tmem, 2 * kTcChunk);
+  if (had_rep) {
+    // the replicated last block ends this range: sum the replicas in a fixed
+    // order (every MMA has completed, so A's slot is free)
+    __syncthreads();
+    float2* red = reinterpret_cast<float2*>(sA);
+    red[t] = make_float2(er, ei);
+    __syncthreads();
+    const int spb = kTcRows / p.rep;
+    if (t < spb) {
+      float sr = 0.0f, si = 0.0f;
+      for (int k = 0; k < p.rep; ++k) {
+        sr += red[t + k * spb].x;
+        si += red[t + k * spb].y;
+      }
+      const int bl = nb - 1, n = bl * kTcRows + t;
+      if ((long long)bl * nq >= u0 && (long long)(bl + 1) * nq <= u1) {
+        if (n < N) p.E[n] = make_float2(sr, si);
+      } else {
+        p.part[((size_t)blockIdx.x * 2 + (bl == b0 ? 0 : 1)) * kTcRows + t] = make_float2(sr, si);
+      }
+    }
+  }
   if (!ok && t == 0) atomicOr(p.err, kErrTimeout);
 }
 

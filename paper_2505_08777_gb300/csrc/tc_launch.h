@@ -25,12 +25,21 @@ __host__ __device__ constexpr int tc_na(int D) { return 3 * D <= 32 ? 1 : 2; }
 // 128-byte swizzle of tc_common.cuh:
 //  zs  : pixel rows, chunk qc = 16 tile + 2 h + half (see tc_pixel);
 //  czs : spot rows, chunk j = spots 64 j .. 64 j + 63 (an even number of
-//        chunks, rows >= N zero, so a 128-spot block is two chunks);
+//        chunks, rows >= N zero, so a 128-spot block is two chunks), then
+//        two chunks holding the last block's spots replicated (tc_fwd_rep);
 //  fimg: the nearfield f_m of each pixel chunk as 32 float4 (fr, fr', fi, fi')
 //        of pixel pairs (2p, 2p + 1).
 inline size_t tc_zs_floats(const Geometry& g) { return (size_t)g.T * kTcChunksPerTile * tc_na(g.D) * 2048; }
 inline int tc_spot_chunks(int N) { return 2 * ((N + kTcRows - 1) / kTcRows); }
-inline size_t tc_czs_floats(int N, int D) { return (size_t)tc_spot_chunks(N) * tc_na(D) * 2048; }
+inline size_t tc_czs_floats(int N, int D) { return (size_t)(tc_spot_chunks(N) + 2) * tc_na(D) * 2048; }
+// The forward's last spot block holds v = N - 128 (nb - 1) spots. With
+// v <= 32 (64) its rows are replicated 4 (2) times and each replica's warps
+// take a quarter (half) of every pixel chunk, so that the block's work is
+// spread over all four warps (and SM sub-partitions) instead of one.
+inline int tc_fwd_rep(int N) {
+  const int v = N - kTcRows * ((N + kTcRows - 1) / kTcRows - 1);
+  return v <= 32 ? 4 : v <= 64 ? 2 : 1;
+}
 inline size_t tc_fimg_float4s(const Geometry& g) { return (size_t)g.T * kTilePix / 2; }
 
 // Pixel of row r of chunk qc (tile, group h, half): column r % 32, row
@@ -95,6 +104,7 @@ struct TcFwdParams {
   const float2* rot;
   const float4* fimg;
   TcFwdSched sched;
+  int rep;                // tc_fwd_rep(N)
   const long long* begin; // [G + 1] sched.begin(g), tabulated on the host
   float2* E;              // [N]
   float2* part;           // [G][2][128] partial sums of spot blocks split between CTAs
