@@ -157,7 +157,7 @@ constexpr int kSrcImg = 2;
 
 cudaError_t enqueue_tc_coeff(ash_hologram* h, cudaStream_t s) {
   if (!h->tc_ok) return cudaSuccess;
-  return tc_build_coeff(h->g, h->coeff, h->anchors, h->czs, h->rot, s);
+  return tc_build_coeff(h->g, h->tc_layout, h->coeff, h->anchors, h->czs, h->rot, s);
 }
 
 TcFwdParams tc_fwd_params(const ash_hologram* h, float2* E) {
@@ -407,7 +407,8 @@ ash_status ash_hologram_create(ash_hologram** out, int nx, int ny, const float* 
   if (D <= kTcMaxModes) {
     // tensor-core path: one range of units per resident CTA, at least two
     // MMA chunks per CTA
-    h->tc_na = tc_na(D);
+    h->tc_layout = tc_layout(D, noll, nx, ny);
+    h->tc_na = h->tc_layout.NA;
     ce = tc_prepare(h->tc_na, &h->li.tc_adj_ctas_per_sm, &h->li.tc_fwd_ctas_per_sm);
     if (ce != cudaSuccess) return fail(cuda_fail(ce, "tensor-core kernel preparation"));
     h->tc_ok = true;
@@ -455,8 +456,8 @@ ash_status ash_hologram_create(ash_hologram** out, int nx, int ny, const float* 
   if ((st = ws(h, &h->partial, (size_t)h->fwd_rows * 2 * N)) != ASH_OK) return fail(st);
   if ((st = ws(h, &h->split, (size_t)h->sched.G * 2 * kTilePix)) != ASH_OK) return fail(st);
   if (h->tc_ok) {
-    if ((st = ws(h, &h->zs, tc_zs_floats(g))) != ASH_OK) return fail(st);
-    if ((st = ws(h, &h->czs, tc_czs_floats(N, D))) != ASH_OK) return fail(st);
+    if ((st = ws(h, &h->zs, tc_zs_floats(g, h->tc_na))) != ASH_OK) return fail(st);
+    if ((st = ws(h, &h->czs, tc_czs_floats(N, h->tc_na))) != ASH_OK) return fail(st);
     if ((st = ws(h, &h->fimg, tc_fimg_float4s(g))) != ASH_OK) return fail(st);
     if ((st = ws(h, &h->rot, (size_t)N * g.T)) != ASH_OK) return fail(st);
     if ((st = ws(h, &h->tc_split, (size_t)h->tadj.G * 2 * kTcRows)) != ASH_OK) return fail(st);
@@ -508,7 +509,7 @@ ash_status ash_hologram_create(ash_hologram** out, int nx, int ny, const float* 
     if (!tadj_groups.empty())
       CREATE_CUDA(cudaMemcpyAsync(h->tadj_groups, tadj_groups.data(), tadj_groups.size() * sizeof(int),
                                   cudaMemcpyHostToDevice, s));
-    CREATE_CUDA(tc_build_zs(g, h->dz, h->zs, s));
+    CREATE_CUDA(tc_build_zs(g, h->tc_layout, h->dz, h->zs, s));
     // pixels outside the grid stay 0 in every nearfield image
     CREATE_CUDA(cudaMemsetAsync(h->fimg, 0, tc_fimg_float4s(g) * sizeof(float4), s));
   }

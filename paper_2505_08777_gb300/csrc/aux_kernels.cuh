@@ -20,15 +20,6 @@ struct BasisParams {
   float2* anchors;         // [T][D]
 };
 
-// Anchor pixel of a tile: centre of its in-grid part.
-__host__ __device__ inline void tile_anchor(const Geometry& g, int tile, int& ia, int& ja) {
-  const int tx = tile % g.tiles_x, ty = tile / g.tiles_x;
-  const int x0 = tx * kTileX, y0 = ty * kTileY;
-  const int x1 = min(x0 + kTileX, g.nx), y1 = min(y0 + kTileY, g.ny);
-  ia = (x0 + x1 - 1) / 2;
-  ja = (y0 + y1 - 1) / 2;
-}
-
 __device__ inline double eval_mono(const MonoTerm* __restrict__ terms, int b, int e, const double* xp,
                                    const double* yp) {
   double z = 0.0;

@@ -123,6 +123,15 @@ enum FwdSource : int { kSrcPhase = 0, kSrcField = 1 };
 // forward's tc layout, so the next WGS forward needs no sincos of its own.
 enum AdjEpilogue : int { kEpiField = 1, kEpiPhase = 2, kEpiGradPhase = 4, kEpiFimg = 8 };
 
+// Anchor pixel of a tile: centre of its in-grid part.
+__host__ __device__ inline void tile_anchor(const Geometry& g, int tile, int& ia, int& ja) {
+  const int tx = tile % g.tiles_x, ty = tile / g.tiles_x;
+  const int x0 = tx * kTileX, y0 = ty * kTileY;
+  const int x1 = min(x0 + kTileX, g.nx), y1 = min(y0 + kTileY, g.ny);
+  ia = (x0 + x1 - 1) / 2;
+  ja = (y0 + y1 - 1) / 2;
+}
+
 // sin and cos of two local phases on the MUFU pipe (the phases are kept
 // small by the tile anchoring, where sin.approx / cos.approx are accurate).
 __device__ __forceinline__ void sincos2(float2 x, float2& s, float2& c) {

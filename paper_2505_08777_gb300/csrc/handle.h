@@ -32,6 +32,7 @@ struct ash_hologram {
   int variant = 0;              // 0 auto, 1 FMA-pipe kernels, 2 tensor-core kernels
   bool tc_ok = false;
   int tc_na = 0;                // K-atoms per operand row
+  ash::TcLayout tc_layout{};
   ash::Schedule tadj{};         // adjoint units (group, spot chunk)
   bool tadj_split = false;      // some group's spots span two CTA ranges
   ash::TcFwdSched tfwd{};       // forward units (spot block, pixel chunk)

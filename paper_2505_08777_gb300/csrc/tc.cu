@@ -82,16 +82,16 @@ cudaError_t tc_launch_forward_reduce(const TcFwdParams& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t tc_build_zs(const Geometry& g, const float* dz, float* zs, cudaStream_t s) {
+cudaError_t tc_build_zs(const Geometry& g, const TcLayout& L, const float* dz, float* zs, cudaStream_t s) {
   const long long rows = (long long)g.T * kTcChunksPerTile * kTcChunk;
-  k_tc_build_zs<<<blocks_for(rows, 256), 256, 0, s>>>(g, dz, tc_na(g.D), zs);
+  k_tc_build_zs<<<blocks_for(rows, 256), 256, 0, s>>>(g, L, dz, zs);
   return cudaGetLastError();
 }
 
-cudaError_t tc_build_coeff(const Geometry& g, const float* coeff, const float2* anchors, float* czs, float2* rot,
-                           cudaStream_t s) {
+cudaError_t tc_build_coeff(const Geometry& g, const TcLayout& L, const float* coeff, const float2* anchors, float* czs,
+                           float2* rot, cudaStream_t s) {
   const int nc64 = tc_spot_chunks(g.N);
-  k_tc_build_czs<<<blocks_for((long long)(nc64 + 2) * kTcChunk, 256), 256, 0, s>>>(coeff, g.N, g.D, tc_na(g.D), nc64,
+  k_tc_build_czs<<<blocks_for((long long)(nc64 + 2) * kTcChunk, 256), 256, 0, s>>>(coeff, g.N, L, nc64,
                                                                                  tc_fwd_rep(g.N), czs);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

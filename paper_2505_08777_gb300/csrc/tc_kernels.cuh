@@ -66,22 +66,31 @@ struct TcFwdShape {
 // --- operand images ---------------------------------------------------------
 
 // zs from the register-image basis dz: one thread per (chunk, row).
-static __global__ void k_tc_build_zs(const Geometry G, const float* __restrict__ dz, int NA, float* __restrict__ zs) {
+static __global__ void k_tc_build_zs(const Geometry G, const TcLayout L, const float* __restrict__ dz,
+                                     float* __restrict__ zs) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)G.T * kTcChunksPerTile * kTcChunk) return;
   const long long qc = e / kTcChunk;
   const int r = (int)(e % kTcChunk), D = G.D;
   const TcPixel px = tc_pixel(G, qc, r);
+  const bool in = px.i < G.nx && px.j < G.ny;
+  int ia, ja;
+  tile_anchor(G, px.tile, ia, ja);
   const int tpx = px.img / G.P, k = px.img % G.P;
-  float* dst = zs + (size_t)qc * NA * 2048;
-  for (int a = 0; a < NA; ++a)
+  float* dst = zs + (size_t)qc * L.NA * 2048;
+  for (int a = 0; a < L.NA; ++a)
     for (int kk = 0; kk < 32; ++kk) {
-      const int col = 32 * a + kk, seg = col / D, d = col % D;
+      int kind, mode;
+      tc_slot(L, 32 * a + kk, kind, mode);
       float v = 0.0f;
-      if (seg < 3) {
-        const float z = dz[((size_t)tpx * D + d) * G.P + k];
+      if (kind >= 0 && kind < 3) {
+        const float z = dz[((size_t)tpx * D + mode) * G.P + k];
         const float hi = to_tf32(z);
-        v = seg == 1 ? to_tf32(z - hi) : hi;   // [hi | lo | hi]
+        v = kind == 1 ? to_tf32(z - hi) : hi;   // [hi | lo | hi]
+      } else if (kind == 3 && in) {
+        v = (float)(px.i - ia);                 // exact integer offsets
+      } else if (kind == 4 && in) {
+        v = (float)(px.j - ja);
       }
       dst[a * 2048 + swz128(r, kk)] = v;
     }
@@ -90,22 +99,29 @@ static __global__ void k_tc_build_zs(const Geometry G, const float* __restrict__
 // czs from the coefficients: one thread per (spot chunk, row); rows >= N are
 // 0. The two chunks after the nc64 main ones hold the last 128-spot block
 // with its first 128 / rep spots repeated rep times.
-static __global__ void k_tc_build_czs(const float* __restrict__ coeff, int N, int D, int NA, int nc64, int rep,
+static __global__ void k_tc_build_czs(const float* __restrict__ coeff, int N, const TcLayout L, int nc64, int rep,
                                       float* __restrict__ czs) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)(nc64 + 2) * kTcChunk) return;
-  const int jc = (int)(e / kTcChunk), r = (int)(e % kTcChunk);
+  const int jc = (int)(e / kTcChunk), r = (int)(e % kTcChunk), D = L.D;
   int n = jc * kTcChunk + r;
   if (jc >= nc64) n = (nc64 - 2) * kTcChunk + ((jc - nc64) * kTcChunk + r) % (kTcRows / rep);
-  float* dst = czs + (size_t)jc * NA * 2048;
-  for (int a = 0; a < NA; ++a)
+  float* dst = czs + (size_t)jc * L.NA * 2048;
+  for (int a = 0; a < L.NA; ++a)
     for (int kk = 0; kk < 32; ++kk) {
-      const int col = 32 * a + kk, seg = col / D, d = col % D;
+      int kind, mode;
+      tc_slot(L, 32 * a + kk, kind, mode);
       float v = 0.0f;
-      if (seg < 3 && n < N) {
-        const float c = coeff[(size_t)n * D + d];
-        const float hi = to_tf32(c);
-        v = seg == 2 ? to_tf32(c - hi) : hi;   // [hi | hi | lo]
+      if (kind >= 0 && n < N) {
+        if (kind < 3) {
+          const float c = coeff[(size_t)n * D + mode];
+          const float hi = to_tf32(c);
+          v = kind == 2 ? to_tf32(c - hi) : hi;   // [hi | hi | lo]
+        } else {
+          const float cr = coeff[(size_t)n * D + (kind == 3 ? L.tx : L.ty)] / L.R;   // rad per pixel
+          const float hi = to_tf32(cr);
+          v = mode == 0 ? hi : to_tf32(cr - hi);
+        }
       }
       dst[a * 2048 + swz128(r, kk)] = v;
     }

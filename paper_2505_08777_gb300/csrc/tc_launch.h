@@ -17,9 +17,63 @@ constexpr unsigned kTcWaitPolls = 1u << 24;
 constexpr unsigned kErrTimeout = 2u;
 constexpr int kTcMaxModes = 21;                        // 3 D <= 64
 
-// K-atoms of 32 tf32 per operand row: the row [hi | lo | hi] (pixels) or
-// [hi | hi | lo] (spots) of 3 D values, zero-padded.
+// K layout of the operand rows. Regular: the pixel row [hi | lo | hi] and the
+// spot row [hi | hi | lo] of the D basis values / coefficients (3 D slots).
+// Tilt-exact (when the basis holds the x and y tilts, Noll 2 and 3, and the
+// regular layout would need a second K-atom): across a tile the tilts change
+// by exactly (i - i_anchor) / R and (j - j_anchor) / R, so the pixel row
+// carries the integer offsets di, dj (exact in tf32) and the spot row the
+// split c_x / R and c_y / R, two slots per tilt:
+//   pixel [hi | lo | hi (other D - 2 modes) | di  di  dj  dj ]
+//   spot  [hi | hi | lo (other D - 2 modes) | xh  xl  yh  yl ]
+// which fits D = 11 into one K-atom of 32.
+struct TcLayout {
+  int D;
+  int NA;        // K-atoms of 32 tf32 per row
+  int tx, ty;    // positions of the x / y tilt among the D modes (tilt-exact), else -1
+  float R;       // min(nx, ny) / 2
+};
 __host__ __device__ constexpr int tc_na(int D) { return 3 * D <= 32 ? 1 : 2; }
+inline TcLayout tc_layout(int D, const int* noll, int nx, int ny) {
+  TcLayout L{D, tc_na(D), -1, -1, 0.5f * (float)(nx < ny ? nx : ny)};
+  if (noll && L.NA > 1 && 3 * (D - 2) + 4 <= 32) {
+    for (int d = 0; d < D; ++d) {
+      if (noll[d] == 2) L.tx = d;
+      if (noll[d] == 3) L.ty = d;
+    }
+    if (L.tx >= 0 && L.ty >= 0) L.NA = 1;
+    else L.tx = L.ty = -1;
+  }
+  return L;
+}
+// Slot `col` of a row: kind 0..2 = segment of mode `mode`, 3 = x tilt
+// (part `mode` = 0 hi / 1 lo), 4 = y tilt, -1 = padding.
+__host__ __device__ inline void tc_slot(const TcLayout& L, int col, int& kind, int& mode) {
+  kind = -1;
+  mode = 0;
+  if (L.tx < 0) {
+    if (col < 3 * L.D) {
+      kind = col / L.D;
+      mode = col % L.D;
+    }
+    return;
+  }
+  const int Dp = L.D - 2;
+  if (col < 3 * Dp) {
+    kind = col / Dp;
+    int k = col % Dp;   // k-th mode that is not a tilt
+    for (int d = 0; d < L.D; ++d) {
+      if (d == L.tx || d == L.ty) continue;
+      if (k-- == 0) {
+        mode = d;
+        break;
+      }
+    }
+  } else if (col < 3 * Dp + 4) {
+    kind = col < 3 * Dp + 2 ? 3 : 4;
+    mode = (col - 3 * Dp) & 1;
+  }
+}
 
 // Operand images in HBM (floats), each [chunks][NA][64 rows][32] with the
 // 128-byte swizzle of tc_common.cuh:
@@ -29,9 +83,9 @@ __host__ __device__ constexpr int tc_na(int D) { return 3 * D <= 32 ? 1 : 2; }
 //        two chunks holding the last block's spots replicated (tc_fwd_rep);
 //  fimg: the nearfield f_m of each pixel chunk as 32 float4 (fr, fr', fi, fi')
 //        of pixel pairs (2p, 2p + 1).
-inline size_t tc_zs_floats(const Geometry& g) { return (size_t)g.T * kTcChunksPerTile * tc_na(g.D) * 2048; }
+inline size_t tc_zs_floats(const Geometry& g, int NA) { return (size_t)g.T * kTcChunksPerTile * NA * 2048; }
 inline int tc_spot_chunks(int N) { return 2 * ((N + kTcRows - 1) / kTcRows); }
-inline size_t tc_czs_floats(int N, int D) { return (size_t)(tc_spot_chunks(N) + 2) * tc_na(D) * 2048; }
+inline size_t tc_czs_floats(int N, int NA) { return (size_t)(tc_spot_chunks(N) + 2) * NA * 2048; }
 // The forward's last spot block holds v = N - 128 (nb - 1) spots. With
 // v <= 32 (64) its rows are replicated 4 (2) times and each replica's warps
 // take a quarter (half) of every pixel chunk, so that the block's work is
@@ -118,9 +172,9 @@ cudaError_t tc_launch_adjoint(int NA, const TcAdjParams& p, int grid, cudaStream
 cudaError_t tc_launch_adjoint_fixup(const TcAdjParams& p, int n_split_groups, cudaStream_t s);
 cudaError_t tc_launch_forward(int NA, const TcFwdParams& p, int grid, cudaStream_t s);
 cudaError_t tc_launch_forward_reduce(const TcFwdParams& p, cudaStream_t s);
-cudaError_t tc_build_zs(const Geometry& g, const float* dz, float* zs, cudaStream_t s);
-cudaError_t tc_build_coeff(const Geometry& g, const float* coeff, const float2* anchors, float* czs, float2* rot,
-                           cudaStream_t s);
+cudaError_t tc_build_zs(const Geometry& g, const TcLayout& L, const float* dz, float* zs, cudaStream_t s);
+cudaError_t tc_build_coeff(const Geometry& g, const TcLayout& L, const float* coeff, const float2* anchors, float* czs,
+                           float2* rot, cudaStream_t s);
 cudaError_t tc_field_img(const Geometry& g, const float* amp_img, const float* phase, const float2* field,
                          float4* fimg, cudaStream_t s);
 

@@ -171,6 +171,8 @@ def test_full_size_sampled(make):
 
 
 @pytest.mark.parametrize("nx,ny,N,noll,dmax", [(97, 61, 37, list(range(2, 12)), 5.0), (160, 128, 300, list(range(2, 13)), 20.0),
+                                                (128, 96, 150, [4, 5, 2, 6, 7, 3, 8, 9, 10, 11, 12], 10.0),
+                                                (96, 96, 70, list(range(4, 15)), 6.0),
                                                 (64, 40, 17, [2, 3, 4, 5, 6], 10.0), (33, 70, 5, [4], 20.0),
                                                 (256, 256, 400, list(range(2, 12)), 8.0)])
 def test_adjoint_kernel_variants_agree_with_oracle(nx, ny, N, noll, dmax):
@@ -191,6 +193,8 @@ def test_adjoint_kernel_variants_agree_with_oracle(nx, ny, N, noll, dmax):
 
 
 @pytest.mark.parametrize("nx,ny,N,noll,dmax", [(97, 61, 37, list(range(2, 12)), 5.0), (160, 128, 300, list(range(2, 13)), 20.0),
+                                                (128, 96, 150, [4, 5, 2, 6, 7, 3, 8, 9, 10, 11, 12], 10.0),
+                                                (96, 96, 70, list(range(4, 15)), 6.0),
                                                 (64, 40, 17, [2, 3, 4, 5, 6], 10.0), (33, 70, 5, [4], 20.0),
                                                 (256, 256, 400, list(range(2, 12)), 8.0)])
 def test_forward_kernel_variants_agree_with_oracle(nx, ny, N, noll, dmax):
