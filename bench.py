@@ -37,7 +37,7 @@ MAX_SM_MHZ = 2070.0
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
 # ncu capture of the named kernel on this workload; see profiles/. Reported as
 # roofline.traffic only for the kernel build these counters were taken on.
-NCU_TRAFFIC_BYTES = {}
+NCU_TRAFFIC_BYTES = {"k_tc_forward<1>": 146.449408e6 + 3.635200e6, "k_tc_adjoint<1>": 151.372544e6 + 7.582208e6}
 
 
 WORKLOAD_TEXT = {
@@ -285,7 +285,8 @@ def main():
     e2e_value = world * terms_per_step * args.steps / (float(t.item()) * 1e-3) / 1e9
 
     # ---- per-kernel timing: ash_profile records CUDA events around each kernel
-    # on this stream; L2 is flushed between repetitions
+    # on this stream, back to back as in the WGS loop (no L2 flush between the
+    # kernels: a WGS step does none either)
     import ctypes
 
     from paper_2505_08777_gb300 import _lib
@@ -297,7 +298,6 @@ def main():
     reps = 20
     ms = (ctypes.c_float * 6)()
     for r in range(reps + 1):
-        flush.zero_()
         _lib.check(L.ash_profile(h.handle, ctypes.c_void_p(phase0.data_ptr()), ctypes.c_void_p(y.data_ptr()), ms,
                                  ctypes.c_void_p(stream.cuda_stream)), "ash_profile")
         if r > 0:
