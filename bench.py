@@ -314,7 +314,9 @@ def main():
     linfo = h.launch_info()
     fwd_tc = bool(linfo["adjoint_variant"] & 4)
     adj_tc = bool(linfo["adjoint_variant"] & 2)
-    NA = 1 if 3 * p.D <= 32 else 2
+    # K-atoms per tensor-core operand row: one for D <= 10, and for D = 11
+    # when the basis holds both tilts (their two-slot exact form)
+    NA = 1 if 3 * p.D <= 32 or (3 * (p.D - 2) + 4 <= 32 and 2 in p.noll and 3 in p.noll) else 2
     kernel_names = {"forward": (f"k_tc_forward<{NA}> (spot-stationary: tcgen05 split-tf32 MMA of 128 spots x 64 "
                                 f"pixels into TMEM, sincos + packed complex MAC)") if fwd_tc else
                                f"k_forward<D={p.D},P={P}> (pixel-stationary forward, warp transpose reduction)",
