@@ -130,6 +130,47 @@ ash_status ash_hologram_create(ash_hologram **out, int nx, int ny, const float *
                                const int *noll, const float *basis, int N, const float *coeff,
                                void *stream);
 
+/*
+ * Create a hologram whose D modes are fixed combinations of Zernike modes
+ * (paper Sec. III and Methods "Anisoplanatic Singular Value Decomposition":
+ * principal isoplanatic modes are a rotation of the Zernike basis; Methods
+ * "Computational Scaling": other bases can be used to reduce D).
+ *   noll    host int[D_in] Noll indices of the input Zernike modes, 1 <= D_in <= 64.
+ *   mix     host double[D*D_in], row-major: output mode k = sum_d mix[k][d] Z_{noll[d]}
+ *           (e.g. the `mix` of ash_principal_modes).
+ *   D       number of output modes, 1 <= D <= ASH_MAX_MODES.
+ *   coeff   device float[N*D], coefficients of the output modes.
+ * Other arguments as ash_hologram_create. The combined polynomials are
+ * formed and evaluated in FP64, so the basis carries no extra rounding; an
+ * output row that is a single input mode with weight 1 counts as that
+ * Zernike (a pair of exact tilts keeps the one-K-atom tensor-core layout).
+ */
+ash_status ash_hologram_create_mixed(ash_hologram **out, int nx, int ny, const float *amp, int D_in,
+                                     const int *noll, int D, const double *mix, int N,
+                                     const float *coeff, void *stream);
+
+/*
+ * Principal isoplanatic modes (paper, Methods "Anisoplanatic Singular Value
+ * Decomposition"; Sec. III "principal isoplanatic modes"): the SVD
+ * W = U Sigma V^T of the N x ncols block W of the coefficient matrix formed
+ * by the modes `cols`, truncated to the K largest singular values. Host
+ * memory only, FP64, no GPU work.
+ *   coeff      host float[N*D], C row-major.
+ *   cols       host int[ncols], distinct mode positions in [0, D) to rotate
+ *              (e.g. all but the tilts, which define the spot positions).
+ *   K          principal modes kept, 0 <= K <= ncols.
+ *   mix        host double[(D - ncols + K) * D] out: rows = output modes; first the
+ *              modes not in `cols` (unit rows, original order), then the K
+ *              principal modes (rows of V^T, by decreasing singular value; sign
+ *              chosen so that each row's largest-magnitude entry is positive).
+ *   coeff_out  host float[N * (D - ncols + K)] out: C of the output modes,
+ *              untouched columns then (U Sigma)_k.
+ *   sigma      host double[ncols] out (may be NULL): all singular values, decreasing.
+ * With K = ncols, coeff_out . (mix . Z) equals C . Z up to rounding.
+ */
+ash_status ash_principal_modes(int N, int D, const float *coeff, int ncols, const int *cols, int K,
+                               double *mix, float *coeff_out, double *sigma);
+
 /* Destroy a handle (NULL is ignored). Synchronises the device (work on any
  * stream may still use the workspace), then frees the workspace. */
 void ash_hologram_destroy(ash_hologram *h);

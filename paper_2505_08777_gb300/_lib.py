@@ -27,6 +27,11 @@ SIGNATURES = {
     "ash_debug_fail_after": (c_int, [c_int]),
     "ash_hologram_create": (c_int, [ctypes.POINTER(c_void_p), c_int, c_int, c_void_p, c_int, c_int_p, c_void_p,
                                     c_int, c_void_p, c_void_p]),
+    "ash_hologram_create_mixed": (c_int, [ctypes.POINTER(c_void_p), c_int, c_int, c_void_p, c_int, c_int_p, c_int,
+                                          ctypes.POINTER(ctypes.c_double), c_int, c_void_p, c_void_p]),
+    "ash_principal_modes": (c_int, [c_int, c_int, ctypes.POINTER(ctypes.c_float), c_int, c_int_p, c_int,
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float),
+                                    ctypes.POINTER(ctypes.c_double)]),
     "ash_hologram_destroy": (None, [c_void_p]),
     "ash_hologram_info": (c_int, [c_void_p, c_int_p, c_int_p, c_int_p, c_int_p, ctypes.POINTER(c_size_t)]),
     "ash_set_coefficients": (c_int, [c_void_p, c_void_p, c_void_p]),

@@ -62,6 +62,7 @@ cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 namespace ash {
 // Lets other translation units report through ash_last_error().
 void record_error(const char* msg) { g_last_error = msg; }
+ash_status status_invalid(const char* msg) { return set_error(ASH_ERR_INVALID_ARG, "%s", msg); }
 ash_status status_cuda(cudaError_t e, const char* where) { return cuda_fail(e, where); }
 bool consume_injected_failure() { return injected_failure(); }
 }  // namespace ash
@@ -336,30 +337,56 @@ ash_status ash_debug_fail_after(int n_calls) {
   return ASH_OK;
 }
 
-ash_status ash_hologram_create(ash_hologram** out, int nx, int ny, const float* amp, int D, const int* noll,
-                               const float* basis, int N, const float* coeff, void* stream) {
-  if (!out) return set_error(ASH_ERR_INVALID_ARG, "out is NULL");
-  *out = nullptr;
-  if (nx < 1 || ny < 1 || nx > 16384 || ny > 16384)
-    return set_error(ASH_ERR_INVALID_ARG, "grid %dx%d outside [1, 16384]", nx, ny);
-  if (D < 1 || D > ASH_MAX_MODES) return set_error(ASH_ERR_INVALID_ARG, "D=%d outside [1, %d]", D, ASH_MAX_MODES);
-  if (N < 1 || N > (1 << 20)) return set_error(ASH_ERR_INVALID_ARG, "N=%d outside [1, 2^20]", N);
-  if (bad_ptr(amp) || bad_ptr(coeff)) return set_error(ASH_ERR_INVALID_ARG, "amp and coeff must be device pointers");
-  if ((noll == nullptr) == (basis == nullptr))
-    return set_error(ASH_ERR_INVALID_ARG, "exactly one of noll / basis must be given");
+}  // extern "C"
+
+namespace {
+
+// The basis of a hologram built from Zernike modes: monomial tables of the
+// D output modes (each a fixed combination of Noll-indexed Zernikes), and
+// the Noll index of every output mode that is a single Zernike (0 otherwise).
+struct BasisSpec {
   std::vector<MonoTerm> terms;
-  std::vector<int> off(1, 0);
+  std::vector<int> off{0};
+  std::vector<int> noll_eff;
   int max_order = 0;
-  if (noll) {
-    for (int d = 0; d < D; ++d) {
-      int n, m;
-      if (noll[d] < 1 || noll[d] > 231 || !noll_to_nm(noll[d], &n, &m))
-        return set_error(ASH_ERR_INVALID_ARG, "Noll index %d outside [1, 231]", noll[d]);
-      if (!zernike_monomials(n, m, &terms)) return set_error(ASH_ERR_INVALID_ARG, "bad Zernike (%d, %d)", n, m);
-      off.push_back((int)terms.size());
-      max_order = n > max_order ? n : max_order;
-    }
+};
+
+// Output mode k = sum_d mix[k][d] Z_{noll[d]} (mix = NULL: the identity);
+// equal monomials are merged in fp64.
+ash_status build_spec(int D_in, const int* noll, int D, const double* mix, BasisSpec* sp) {
+  std::vector<std::vector<MonoTerm>> in(D_in);
+  std::vector<int> order(D_in);
+  for (int d = 0; d < D_in; ++d) {
+    int n, m;
+    if (noll[d] < 1 || noll[d] > 231 || !noll_to_nm(noll[d], &n, &m))
+      return set_error(ASH_ERR_INVALID_ARG, "Noll index %d outside [1, 231]", noll[d]);
+    if (!zernike_monomials(n, m, &in[d])) return set_error(ASH_ERR_INVALID_ARG, "bad Zernike (%d, %d)", n, m);
+    order[d] = n;
   }
+  sp->noll_eff.assign(D, 0);
+  for (int k = 0; k < D; ++k) {
+    std::map<std::pair<int, int>, double> acc;
+    int nz = 0, last = -1;
+    for (int d = 0; d < D_in; ++d) {
+      const double wgt = mix ? mix[(size_t)k * D_in + d] : (d == k ? 1.0 : 0.0);
+      if (wgt == 0.0) continue;
+      ++nz;
+      last = d;
+      sp->max_order = order[d] > sp->max_order ? order[d] : sp->max_order;
+      for (const MonoTerm& t : in[d]) acc[{t.px, t.py}] += wgt * t.coef;
+    }
+    if (nz == 1 && (mix ? mix[(size_t)k * D_in + last] : 1.0) == 1.0) sp->noll_eff[k] = noll[last];
+    for (const auto& kv : acc)
+      if (kv.second != 0.0) sp->terms.push_back(MonoTerm{kv.second, kv.first.first, kv.first.second});
+    sp->off.push_back((int)sp->terms.size());
+  }
+  return ASH_OK;
+}
+
+ash_status create_impl(ash_hologram** out, int nx, int ny, const float* amp, int D, const BasisSpec* spec,
+                       const float* basis, int N, const float* coeff, void* stream) {
+  const int* noll = spec ? spec->noll_eff.data() : nullptr;
+  const int max_order = spec ? spec->max_order : 0;
   if (injected_failure()) return set_error(ASH_ERR_INJECTED, "injected failure (ash_debug_fail_after)");
 
   ash_hologram* h = new ash_hologram();
@@ -475,9 +502,9 @@ ash_status ash_hologram_create(ash_hologram** out, int nx, int ny, const float* 
   if ((st = ws(h, &h->wgs_metrics, 4)) != ASH_OK) return fail(st);
   if ((st = ws(h, &h->sum_a2, 1)) != ASH_OK) return fail(st);
   if ((st = ws(h, &h->err_word, 1)) != ASH_OK) return fail(st);
-  if (noll) {
-    if ((st = ws(h, &h->terms, terms.size())) != ASH_OK) return fail(st);
-    if ((st = ws(h, &h->term_off, off.size())) != ASH_OK) return fail(st);
+  if (spec) {
+    if ((st = ws(h, &h->terms, spec->terms.size() + 1)) != ASH_OK) return fail(st);
+    if ((st = ws(h, &h->term_off, spec->off.size())) != ASH_OK) return fail(st);
   }
   ce = cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking);
   if (ce != cudaSuccess) return fail(cuda_fail(ce, "capture stream"));
@@ -487,9 +514,12 @@ ash_status ash_hologram_create(ash_hologram** out, int nx, int ny, const float* 
     cudaError_t e_ = (call);                                  \
     if (e_ != cudaSuccess) return fail(cuda_fail(e_, #call)); \
   } while (0)
-  if (noll) {
-    CREATE_CUDA(cudaMemcpyAsync(h->terms, terms.data(), terms.size() * sizeof(MonoTerm), cudaMemcpyHostToDevice, s));
-    CREATE_CUDA(cudaMemcpyAsync(h->term_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  if (spec) {
+    if (!spec->terms.empty())
+      CREATE_CUDA(cudaMemcpyAsync(h->terms, spec->terms.data(), spec->terms.size() * sizeof(MonoTerm),
+                                  cudaMemcpyHostToDevice, s));
+    CREATE_CUDA(cudaMemcpyAsync(h->term_off, spec->off.data(), spec->off.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                s));
   }
   CREATE_CUDA(cudaMemsetAsync(h->err_word, 0, sizeof(unsigned), s));
   CREATE_CUDA(cudaMemcpyAsync(h->coeff, coeff, (size_t)N * D * sizeof(float), cudaMemcpyDeviceToDevice, s));
@@ -524,6 +554,45 @@ ash_status ash_hologram_create(ash_hologram** out, int nx, int ny, const float* 
 #undef CREATE_CUDA
   *out = h;
   return ASH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ash_status ash_hologram_create(ash_hologram** out, int nx, int ny, const float* amp, int D, const int* noll,
+                               const float* basis, int N, const float* coeff, void* stream) {
+  if (!out) return set_error(ASH_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (nx < 1 || ny < 1 || nx > 16384 || ny > 16384)
+    return set_error(ASH_ERR_INVALID_ARG, "grid %dx%d outside [1, 16384]", nx, ny);
+  if (D < 1 || D > ASH_MAX_MODES) return set_error(ASH_ERR_INVALID_ARG, "D=%d outside [1, %d]", D, ASH_MAX_MODES);
+  if (N < 1 || N > (1 << 20)) return set_error(ASH_ERR_INVALID_ARG, "N=%d outside [1, 2^20]", N);
+  if (bad_ptr(amp) || bad_ptr(coeff)) return set_error(ASH_ERR_INVALID_ARG, "amp and coeff must be device pointers");
+  if ((noll == nullptr) == (basis == nullptr))
+    return set_error(ASH_ERR_INVALID_ARG, "exactly one of noll / basis must be given");
+  if (!noll) return create_impl(out, nx, ny, amp, D, nullptr, basis, N, coeff, stream);
+  BasisSpec spec;
+  ash_status st = build_spec(D, noll, D, nullptr, &spec);
+  if (st != ASH_OK) return st;
+  return create_impl(out, nx, ny, amp, D, &spec, nullptr, N, coeff, stream);
+}
+
+ash_status ash_hologram_create_mixed(ash_hologram** out, int nx, int ny, const float* amp, int D_in, const int* noll,
+                                     int D, const double* mix, int N, const float* coeff, void* stream) {
+  if (!out) return set_error(ASH_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (nx < 1 || ny < 1 || nx > 16384 || ny > 16384)
+    return set_error(ASH_ERR_INVALID_ARG, "grid %dx%d outside [1, 16384]", nx, ny);
+  if (D_in < 1 || D_in > 64) return set_error(ASH_ERR_INVALID_ARG, "D_in=%d outside [1, 64]", D_in);
+  if (D < 1 || D > ASH_MAX_MODES) return set_error(ASH_ERR_INVALID_ARG, "D=%d outside [1, %d]", D, ASH_MAX_MODES);
+  if (N < 1 || N > (1 << 20)) return set_error(ASH_ERR_INVALID_ARG, "N=%d outside [1, 2^20]", N);
+  if (bad_ptr(amp) || bad_ptr(coeff) || !noll || !mix)
+    return set_error(ASH_ERR_INVALID_ARG, "amp, coeff (device), noll and mix (host) must be given");
+  BasisSpec spec;
+  ash_status st = build_spec(D_in, noll, D, mix, &spec);
+  if (st != ASH_OK) return st;
+  return create_impl(out, nx, ny, amp, D, &spec, nullptr, N, coeff, stream);
 }
 
 void ash_hologram_destroy(ash_hologram* h) {

@@ -9,6 +9,8 @@ from __future__ import annotations
 
 import ctypes
 
+import numpy as np
+
 import torch
 
 from . import _lib
@@ -44,7 +46,11 @@ class Hologram:
     N x D coefficient matrix (paper Sec. II / Methods). Owns a libash handle."""
 
     def __init__(self, amp: torch.Tensor, coeff: torch.Tensor, noll=None, basis: torch.Tensor | None = None,
-                 stream=None):
+                 mix=None, stream=None):
+        """`noll`: Noll indices of the modes (one per column of coeff), or of
+        the input Zernikes when `mix` is given; `mix` (D x len(noll), float64):
+        output mode k = sum_d mix[k, d] Z_noll[d] (e.g. from principal_modes);
+        `basis`: a caller basis (D, ny, nx) instead of Noll modes."""
         self._lib = _lib.load()
         self._h = ctypes.c_void_p(0)
         if amp.dim() != 2:
@@ -58,13 +64,25 @@ class Hologram:
         noll_arr = None
         if noll is not None:
             noll = [int(v) for v in noll]
-            if len(noll) != self.D:
+            if mix is None and len(noll) != self.D:
                 raise ValueError("noll must list one index per column of coeff")
-            noll_arr = (ctypes.c_int * self.D)(*noll)
+            noll_arr = (ctypes.c_int * len(noll))(*noll)
         if basis is not None:
             _need(basis, torch.float32, (self.D, self.ny, self.nx), "basis")
         self.noll = noll
         self._coeff = coeff.detach().clone()
+        if mix is not None:
+            if noll is None or basis is not None:
+                raise ValueError("mix needs noll (and no basis)")
+            mix = np.ascontiguousarray(np.asarray(mix, dtype=np.float64))
+            if mix.shape != (self.D, len(noll)):
+                raise ValueError("mix must be (D, len(noll))")
+            self.mix = mix
+            st = self._lib.ash_hologram_create_mixed(
+                ctypes.byref(self._h), self.nx, self.ny, _ptr(amp), len(noll), noll_arr, self.D,
+                mix.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self.N, _ptr(coeff), _stream_ptr(stream))
+            _lib.check(st, "ash_hologram_create_mixed")
+            return
         st = self._lib.ash_hologram_create(ctypes.byref(self._h), self.nx, self.ny, _ptr(amp), self.D,
                                            noll_arr, _ptr(basis), self.N, _ptr(coeff), _stream_ptr(stream))
         _lib.check(st, "ash_hologram_create")
@@ -253,3 +271,30 @@ class Batch:
         path = cache_path.encode() if cache_path else None
         _lib.check(self._lib.ash_batch_tune(self._b, ph, path, ctypes.byref(g), _stream_ptr(stream)), "ash_batch_tune")
         return g.value
+
+
+def principal_modes(coeff, cols, K: int):
+    """Principal isoplanatic modes (paper, Methods "Anisoplanatic Singular
+    Value Decomposition"): rotate the modes at positions `cols` of the N x D
+    coefficient matrix to their K leading principal modes (host FP64 SVD in
+    the library). Returns (mix, coeff_out, sigma): mix (D', D) float64 for
+    Hologram(..., noll=noll, mix=mix), coeff_out (N, D') float32 with
+    D' = D - len(cols) + K, and all len(cols) singular values."""
+    c = np.ascontiguousarray(np.asarray(coeff.detach().cpu() if isinstance(coeff, torch.Tensor) else coeff,
+                                        dtype=np.float32))
+    if c.ndim != 2:
+        raise ValueError("coeff must be (N, D)")
+    N, D = c.shape
+    cols = [int(v) for v in cols]
+    Dout = D - len(cols) + int(K)
+    mix = np.zeros((max(Dout, 0), D), np.float64)
+    out = np.zeros((N, max(Dout, 0)), np.float32)
+    sigma = np.zeros(len(cols), np.float64)
+    lib = _lib.load()
+    cols_arr = (ctypes.c_int * max(len(cols), 1))(*cols)
+    st = lib.ash_principal_modes(N, D, c.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), len(cols), cols_arr, int(K),
+                                 mix.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                 out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                 sigma.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    _lib.check(st, "ash_principal_modes")
+    return mix, out, sigma
