@@ -273,6 +273,19 @@ ash_status ash_hologram_launch_info(const ash_hologram *h, int *out);
 ash_status ash_set_kernel_variant(ash_hologram *h, int variant);
 
 /*
+ * WGS variants (the paper uses weighted GS after Kim et al., Sec. II "...with
+ * the weighted Gerchberg-Saxton algorithm"): for the following
+ * ash_wgs_iterate calls on this handle,
+ *   feedback   exponent p of the weight update w <- w (T^/E^)^p, 0 <= p <= 16
+ *              (1: the plain rule; 0: plain GS with the target amplitudes);
+ *   fix_phase  1: hold every spot's phase psi_n at its value from the last
+ *              update made with fix_phase = 0 (phase fixing), 0: psi_n = arg E_n.
+ * The held phases live in the handle (they start at 0) and are the third part
+ * of the WGS state besides (phase, w). Cached loop graphs are discarded.
+ */
+ash_status ash_wgs_set_options(ash_hologram *h, float feedback, int fix_phase);
+
+/*
  * Number of kernel launches one ash_wgs_iterate call with `iters` iterations
  * enqueues (transform kernels, reductions, fix-ups, spot updates, metrics);
  * -1 on a NULL handle.

@@ -18,6 +18,11 @@ weighted GS, scale-invariant form, feedback exponent 1, no phase fixing):
      phi = arg g   (0 where g == 0 exactly)
   finally E = K (A exp(i phi)) is the reported field.
 
+Variants (SURVEY's next step on WGS; Kim et al. is only cited): the weight
+update with a feedback exponent p, w = w * (T^ / max(E^, 1e-30))^p (p = 1
+above; p = 0 keeps w = T^, plain GS), and phase fixing, where psi is held
+at given values instead of arg E.
+
 Metrics (the paper reports camera Strehl instead; these are the readings):
   uniformity U = 1 - (max I^ - min I^)/(max I^ + min I^), I^_n = |E_n|^2 / T_n^2
   efficiency eta = sum_n |E_n|^2 / (M sum_m A_m^2)
@@ -39,6 +44,7 @@ class WGSResult:
     uniformity: float
     efficiency: float
     history: list         # per-iteration uniformity of the forward inside the loop
+    psi: np.ndarray = None  # (N,) spot phases used by the last update
 
 
 def uniformity(E: np.ndarray, target: np.ndarray) -> float:
@@ -52,29 +58,41 @@ def efficiency(E: np.ndarray, amp: np.ndarray) -> float:
     return float(np.sum(np.abs(E) ** 2) / (a.size * np.sum(a * a)))
 
 
-def weight_update(E: np.ndarray, w: np.ndarray, target: np.ndarray):
-    """One spot-side update: returns (new w, y = w exp(i arg E))."""
+def weight_update(E: np.ndarray, w: np.ndarray, target: np.ndarray, feedback: float = 1.0, psi=None):
+    """One spot-side update: returns (new w, y = w exp(i psi)).
+
+    w <- w (T^/E^)^feedback, renormalised (feedback 1 is the plain weighted
+    GS rule, 0 plain GS with the target amplitudes); psi = arg E unless a
+    held phase `psi` is given (phase fixing, after Kim et al.)."""
     t = np.asarray(target, np.float64)
     t_hat = t / np.linalg.norm(t)
     a = np.abs(E)
     nrm = np.linalg.norm(a)
     e_hat = a / nrm if nrm > 0 else a
-    w = w * t_hat / np.maximum(e_hat, 1e-30)
+    w = w * (t_hat / np.maximum(e_hat, 1e-30)) ** feedback
     w = w / np.linalg.norm(w)
-    psi = transform.phase_of(E)
+    if psi is None:
+        psi = transform.phase_of(E)
     return w, w * np.exp(1j * psi)
 
 
-def run(amp, phase0, C, Z, target, iters: int, weights0=None, workers: int = 1) -> WGSResult:
+def run(amp, phase0, C, Z, target, iters: int, weights0=None, workers: int = 1, feedback: float = 1.0,
+        fixed_psi=None) -> WGSResult:
+    """`iters` WGS iterations and a final forward. `fixed_psi`: hold the spot
+    phases at these values (phase fixing); otherwise psi = arg E each time.
+    The result's `psi` is the spot phase of the last update."""
     amp = np.asarray(amp, np.float64).ravel()
     phase = np.asarray(phase0, np.float64).ravel().copy()
     w = np.asarray(target if weights0 is None else weights0, np.float64).copy()
     hist = []
+    psi = None if fixed_psi is None else np.asarray(fixed_psi, np.float64)
     for _ in range(iters):
         E = transform.forward(transform.field(amp, phase), C, Z, workers=workers)
         hist.append(uniformity(E, target))
-        w, y = weight_update(E, w, target)
+        if fixed_psi is None:
+            psi = transform.phase_of(E)
+        w, y = weight_update(E, w, target, feedback, psi)
         g = transform.adjoint(y, C, Z, workers=workers)
         phase = transform.phase_of(g)
     E = transform.forward(transform.field(amp, phase), C, Z, workers=workers)
-    return WGSResult(phase, w, E, uniformity(E, target), efficiency(E, amp), hist)
+    return WGSResult(phase, w, E, uniformity(E, target), efficiency(E, amp), hist, psi)

@@ -282,7 +282,8 @@ ash_status enqueue_wgs_body(ash_hologram* h, int iters, cudaStream_t s) {
   ash_status st = enqueue_forward(h, kSrcPhase, h->wgs_phase, nullptr, h->wgs_E, s);
   if (st != ASH_OK) return st;
   for (int it = 0; it < iters; ++it) {
-    k_wgs_update<<<1, 1024, 0, s>>>(h->wgs_E, h->wgs_w, h->wgs_T, h->y, h->g.N);
+    k_wgs_update<<<1, 1024, 0, s>>>(h->wgs_E, h->wgs_w, h->wgs_T, h->y, h->g.N, h->wgs_feedback,
+                                    h->wgs_fix ? h->wgs_u : nullptr, h->wgs_fix ? nullptr : h->wgs_u);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "wgs update launch");
     st = enqueue_adjoint(h, h->y, nullptr, h->wgs_phase, nullptr, nullptr, adj_epi, s);
@@ -499,6 +500,7 @@ ash_status create_impl(ash_hologram** out, int nx, int ny, const float* amp, int
   if ((st = ws(h, &h->wgs_w, (size_t)N)) != ASH_OK) return fail(st);
   if ((st = ws(h, &h->wgs_T, (size_t)N)) != ASH_OK) return fail(st);
   if ((st = ws(h, &h->wgs_E, (size_t)N)) != ASH_OK) return fail(st);
+  if ((st = ws(h, &h->wgs_u, (size_t)N)) != ASH_OK) return fail(st);
   if ((st = ws(h, &h->wgs_metrics, 4)) != ASH_OK) return fail(st);
   if ((st = ws(h, &h->sum_a2, 1)) != ASH_OK) return fail(st);
   if ((st = ws(h, &h->err_word, 1)) != ASH_OK) return fail(st);
@@ -522,6 +524,9 @@ ash_status create_impl(ash_hologram** out, int nx, int ny, const float* amp, int
                                 s));
   }
   CREATE_CUDA(cudaMemsetAsync(h->err_word, 0, sizeof(unsigned), s));
+  // stored spot phases of the phase-fixing variant start at 0
+  k_fill_c<<<(N + 255) / 256, 256, 0, s>>>(h->wgs_u, N, make_float2(1.0f, 0.0f));
+  CREATE_CUDA(cudaGetLastError());
   CREATE_CUDA(cudaMemcpyAsync(h->coeff, coeff, (size_t)N * D * sizeof(float), cudaMemcpyDeviceToDevice, s));
   BasisParams bp{};
   bp.g = g;
@@ -752,6 +757,17 @@ ash_status ash_set_kernel_variant(ash_hologram* h, int variant) {
   return ASH_OK;
 }
 
+ash_status ash_wgs_set_options(ash_hologram* h, float feedback, int fix_phase) {
+  if (!h) return set_error(ASH_ERR_INVALID_ARG, "handle is NULL");
+  if (!(feedback >= 0.0f && feedback <= 16.0f)) return set_error(ASH_ERR_INVALID_ARG, "feedback outside [0, 16]");
+  if (fix_phase != 0 && fix_phase != 1) return set_error(ASH_ERR_INVALID_ARG, "fix_phase must be 0 or 1");
+  h->wgs_feedback = feedback;
+  h->wgs_fix = fix_phase != 0;
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);   // the graphs hold the old options
+  h->graphs.clear();
+  return ASH_OK;
+}
+
 int ash_wgs_launches(const ash_hologram* h, int iters) {
   if (!h || iters < 0) return -1;
   // forward: tensor-core (nearfield image unless fused, kernel, reduce if
@@ -823,7 +839,8 @@ ash_status ash_profile(ash_hologram* h, const float* phase, const float* y, floa
   }
   if (e == cudaSuccess) {
     cudaEventRecord(ev[8], s);
-    k_wgs_update<<<1, 1024, 0, s>>>(h->E, h->wgs_w, reinterpret_cast<const float*>(h->wgs_T), h->y, h->g.N);
+    k_wgs_update<<<1, 1024, 0, s>>>(h->E, h->wgs_w, reinterpret_cast<const float*>(h->wgs_T), h->y, h->g.N, 1.0f,
+                                    nullptr, nullptr);
     e = cudaGetLastError();
     cudaEventRecord(ev[9], s);
   }

@@ -167,8 +167,14 @@ __device__ __forceinline__ float block_sum_f(float v, float* red) {
 //   y = w exp(i arg E) (arg 0 -> 0).
 // The norms only fix a global scale of w (removed by the renormalisation,
 // and arg g is invariant to it), so fp32 sums are sufficient.
+// Weighted GS spot update. Variants (feedback exponent p, phase fixing; p = 1
+// and no fixing is the plain rule): w <- w (T^/E^)^p, renormalised; the spot
+// phase is arg E, stored as a unit phasor in u_store when given, or, when
+// u_fixed is given, the stored phasor instead of arg E.
 __device__ __forceinline__ void wgs_update_body(const float2* __restrict__ E, float* __restrict__ w,
-                                                const float* __restrict__ T, float2* __restrict__ y, int N) {
+                                                const float* __restrict__ T, float2* __restrict__ y, int N,
+                                                float feedback = 1.0f, const float2* __restrict__ u_fixed = nullptr,
+                                                float2* __restrict__ u_store = nullptr) {
   __shared__ float red[32];
   float se = 0.0f, st = 0.0f;
   for (int n = threadIdx.x; n < N; n += 1024) {
@@ -184,7 +190,7 @@ __device__ __forceinline__ void wgs_update_body(const float2* __restrict__ E, fl
     const float2 e = E[n];
     const float ea = sqrtf(e.x * e.x + e.y * e.y);
     const float eh = fmaxf(ea / ne, 1e-30f);
-    const float wn = w[n] * (T[n] / nt) / eh;
+    const float wn = feedback == 1.0f ? w[n] * (T[n] / nt) / eh : w[n] * powf((T[n] / nt) / eh, feedback);
     w[n] = wn;
     sw = fmaf(wn, wn, sw);
   }
@@ -193,9 +199,16 @@ __device__ __forceinline__ void wgs_update_body(const float2* __restrict__ E, fl
   for (int n = threadIdx.x; n < N; n += 1024) {
     const float wn = w[n] / nw;
     w[n] = wn;
-    const float2 e = E[n];
-    const float ea = sqrtf(e.x * e.x + e.y * e.y);
-    y[n] = ea > 0.0f ? make_float2(wn * (e.x / ea), wn * (e.y / ea)) : make_float2(wn, 0.0f);
+    float2 u;
+    if (u_fixed) {
+      u = u_fixed[n];
+    } else {
+      const float2 e = E[n];
+      const float ea = sqrtf(e.x * e.x + e.y * e.y);
+      u = ea > 0.0f ? make_float2(e.x / ea, e.y / ea) : make_float2(1.0f, 0.0f);
+      if (u_store) u_store[n] = u;
+    }
+    y[n] = make_float2(wn * u.x, wn * u.y);
   }
 }
 
@@ -272,10 +285,16 @@ static __global__ void k_col_reduce(const float* __restrict__ in, int rows, int 
   col_reduce_body(in, rows, cols, out, blockIdx.x);
 }
 
+static __global__ void k_fill_c(float2* __restrict__ x, int n, float2 v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = v;
+}
+
 static __global__ void __launch_bounds__(1024) k_wgs_update(const float2* __restrict__ E, float* __restrict__ w,
                                                             const float* __restrict__ T, float2* __restrict__ y,
-                                                            int N) {
-  wgs_update_body(E, w, T, y, N);
+                                                            int N, float feedback, const float2* __restrict__ u_fixed,
+                                                            float2* __restrict__ u_store) {
+  wgs_update_body(E, w, T, y, N, feedback, u_fixed, u_store);
 }
 
 static __global__ void __launch_bounds__(1024) k_metrics(const float2* __restrict__ E, const float* __restrict__ T,

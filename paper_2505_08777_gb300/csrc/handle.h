@@ -54,6 +54,9 @@ struct ash_hologram {
   float* wgs_w = nullptr;
   float* wgs_T = nullptr;
   float2* wgs_E = nullptr;
+  float2* wgs_u = nullptr;      // spot phases (unit phasors) of the last unfixed update
+  float wgs_feedback = 1.0f;    // feedback exponent p of the weight update
+  bool wgs_fix = false;         // phase fixing: hold the spot phases at wgs_u
   float* wgs_metrics = nullptr;
   double* sum_a2 = nullptr;
   ash::MonoTerm* terms = nullptr;

@@ -178,6 +178,12 @@ class Hologram:
                    "ash_grad")
         return dph, dC
 
+    def set_wgs_options(self, feedback: float = 1.0, fix_phase: bool = False):
+        """WGS variants for later wgs() calls: weight-update exponent p
+        (w <- w (T^/E^)^p) and phase fixing (hold each spot's phase at its value
+        from the last update made without fixing)."""
+        _lib.check(self._lib.ash_wgs_set_options(self._h, float(feedback), int(bool(fix_phase))), "ash_wgs_set_options")
+
     def launch_info(self) -> dict:
         out = (ctypes.c_int * 8)()
         _lib.check(self._lib.ash_hologram_launch_info(self._h, out), "ash_hologram_launch_info")

@@ -62,6 +62,25 @@ def test_wgs_random_uniformity(N, noll, flat):
     assert abs(float(met[0].item()) - res.uniformity) <= UNIF_TOL, (met[0].item(), res.uniformity)
 
 
+@pytest.mark.parametrize("feedback", [0.0, 0.7, 2.0])
+def test_wgs_variants_match_oracle(feedback):
+    """Feedback exponent p, then phase fixing: 6 plain iterations store the
+    spot phases, 6 fixed ones hold them; final uniformity vs the oracle."""
+    p = random_problem(41, 96, 80, 37, list(range(2, 12)), defocus_max=6.0, target_range=(0.5, 1.0))
+    h = _holo(p)
+    Z, C, A = oracle_inputs(p)
+    h.set_wgs_options(feedback=feedback)
+    ph, ww, _, met = _run_wgs(h, p, 6)
+    res = wgs.run(A, p.phase0, C, Z, p.target, 6, workers=4, feedback=feedback)
+    assert abs(float(met[0].item()) - res.uniformity) <= UNIF_TOL, (met[0].item(), res.uniformity)
+    h.set_wgs_options(feedback=feedback, fix_phase=True)
+    _, _, _, met2 = _run_wgs(h, p, 6, phase=ph.cpu().numpy(), w=ww.cpu().numpy())
+    res2 = wgs.run(A, ph.cpu().numpy().astype(np.float64), C, Z, p.target, 6, weights0=ww.cpu().numpy(), workers=4,
+                   feedback=feedback, fixed_psi=res.psi)
+    assert abs(float(met2[0].item()) - res2.uniformity) <= UNIF_TOL, (met2[0].item(), res2.uniformity)
+    h.set_wgs_options()   # back to the plain rule
+
+
 def test_wgs_resume_is_bitwise():
     p = random_problem(3, 128, 128, 64, list(range(2, 12)))
     h = _holo(p)

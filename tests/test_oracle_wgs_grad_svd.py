@@ -25,8 +25,9 @@ def _bin_problem(nx, ny, bins):
     return C, zernike.basis(nx, ny, [2, 3])
 
 
-def _fft_wgs(amp, phase0, bins, nx, ny, target, iters):
-    """Same update rule, with the transform done by numpy FFTs (DFT special case)."""
+def _fft_wgs(amp, phase0, bins, nx, ny, target, iters, feedback=1.0, fixed=None):
+    """Same update rule, with the transform done by numpy FFTs (DFT special
+    case); `feedback` is the weight exponent, `fixed` held spot phases."""
     A = amp.reshape(ny, nx)
     phase = phase0.reshape(ny, nx).copy()
     t = np.asarray(target, np.float64)
@@ -37,9 +38,9 @@ def _fft_wgs(amp, phase0, bins, nx, ny, target, iters):
         F = np.fft.fft2(A * np.exp(1j * phase))
         E = np.array([F[ky % ny, kx % nx] for kx, ky in bins]) * cen
         e_hat = np.abs(E) / np.linalg.norm(np.abs(E))
-        w = w * t_hat / np.maximum(e_hat, 1e-30)
+        w = w * np.power(t_hat / np.maximum(e_hat, 1e-30), feedback)
         w = w / np.linalg.norm(w)
-        y = w * np.exp(1j * np.angle(E))
+        y = w * np.exp(1j * (np.angle(E) if fixed is None else fixed))
         spec = np.zeros((ny, nx), np.complex128)
         for (kx, ky), v, c in zip(bins, y, cen):
             spec[ky % ny, kx % nx] += v * np.conj(c)
@@ -60,6 +61,31 @@ def test_wgs_matches_fft_implementation_on_integer_bins():
     ph_fft, w_fft = _fft_wgs(amp, phase0, bins, nx, ny, target, 6)
     np.testing.assert_allclose(np.exp(1j * res.phase), np.exp(1j * ph_fft), atol=1e-9)
     np.testing.assert_allclose(res.weights, w_fft, rtol=1e-9)
+
+
+@pytest.mark.parametrize("feedback", [0.0, 0.5, 2.0])
+def test_wgs_variants_match_fft_implementation(feedback):
+    """Feedback exponent and phase fixing against the FFT implementation; p = 0
+    keeps the weights at the normalised targets (plain GS)."""
+    nx, ny = 24, 20
+    bins = [(-5, -4), (-5, 3), (4, -4), (4, 3), (0, 6), (-2, 0), (7, -1)]
+    C, Z = _bin_problem(nx, ny, bins)
+    rng = np.random.default_rng(4)
+    amp = flat_amplitude(nx, ny).astype(np.float64).ravel()
+    phase0 = rng.uniform(0, 2 * math.pi, nx * ny)
+    target = rng.uniform(0.5, 1.0, len(bins))
+    res = wgs.run(amp, phase0, C, Z, target, 5, feedback=feedback)
+    ph_fft, w_fft = _fft_wgs(amp, phase0, bins, nx, ny, target, 5, feedback=feedback)
+    np.testing.assert_allclose(np.exp(1j * res.phase), np.exp(1j * ph_fft), atol=1e-9)
+    np.testing.assert_allclose(res.weights, w_fft, rtol=1e-9)
+    if feedback == 0.0:
+        np.testing.assert_allclose(res.weights, target / np.linalg.norm(target), rtol=1e-12)
+    psi = rng.uniform(-math.pi, math.pi, len(bins))
+    fixed = wgs.run(amp, phase0, C, Z, target, 4, feedback=feedback, fixed_psi=psi)
+    ph_fix, w_fix = _fft_wgs(amp, phase0, bins, nx, ny, target, 4, feedback=feedback, fixed=psi)
+    np.testing.assert_allclose(np.exp(1j * fixed.phase), np.exp(1j * ph_fix), atol=1e-9)
+    np.testing.assert_allclose(fixed.weights, w_fix, rtol=1e-9)
+    np.testing.assert_array_equal(fixed.psi, psi)
 
 
 def test_wgs_reaches_uniformity_on_integer_bins():
