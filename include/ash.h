@@ -350,6 +350,13 @@ ash_status ash_batch_info(const ash_batch *b, int *count, int *grid, int *reside
  * [1, 4 x resident CTAs]); invalidates captured graphs. */
 ash_status ash_batch_set_grid(ash_batch *b, int grid);
 
+/* Kernel family of the batch: 0 automatic (the tensor-core transforms when
+ * every hologram has tensor-core operand images with the same K-atom count,
+ * else the FMA-pipe kernels), 1 FMA-pipe kernels, 2 tensor-core kernels
+ * (ASH_ERR_UNSUPPORTED if not every hologram qualifies). Resets the grid to
+ * the family's resident CTAs and invalidates captured graphs. */
+ash_status ash_batch_set_variant(ash_batch *b, int variant);
+
 /* Kernel launches one ash_batch_wgs call enqueues for `iters`; -1 if NULL. */
 int ash_batch_wgs_launches(const ash_batch *b, int iters);
 

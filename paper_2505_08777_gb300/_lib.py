@@ -33,6 +33,7 @@ SIGNATURES = {
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float),
                                     ctypes.POINTER(ctypes.c_double)]),
     "ash_wgs_set_options": (c_int, [c_void_p, ctypes.c_float, c_int]),
+    "ash_batch_set_variant": (c_int, [c_void_p, c_int]),
     "ash_hologram_destroy": (None, [c_void_p]),
     "ash_hologram_info": (c_int, [c_void_p, c_int_p, c_int_p, c_int_p, c_int_p, ctypes.POINTER(c_size_t)]),
     "ash_set_coefficients": (c_int, [c_void_p, c_void_p, c_void_p]),

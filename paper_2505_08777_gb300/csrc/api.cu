@@ -187,7 +187,8 @@ TcAdjParams tc_adj_params(const ash_hologram* h, const float2* y, const AdjOut& 
   p.amp_img = h->amp_img;
   p.out = out;
   p.fimg = h->fimg;
-  p.sched = h->tadj;
+  p.begin = h->tadj_begin;
+  p.G = h->tadj.G;
   p.split = h->tc_split;
   p.split_groups = h->tadj_groups;
   p.err = h->err_word;
@@ -431,7 +432,7 @@ ash_status create_impl(ash_hologram** out, int nx, int ny, const float* amp, int
   }
   h->fwd_rows = g.T * (g.NT / 32);
   std::vector<int> tadj_groups;
-  std::vector<long long> tfwd_begin;
+  std::vector<long long> tfwd_begin, tadj_begin;
   if (D <= kTcMaxModes) {
     // tensor-core path: one range of units per resident CTA, at least two
     // MMA chunks per CTA
@@ -447,6 +448,7 @@ ash_status create_impl(ash_hologram** out, int nx, int ny, const float* amp, int
     if (Ga < 1) Ga = 1;
     h->tadj.W = Wa;
     h->tadj.G = (int)Ga;
+    for (int b = 0; b <= h->tadj.G; ++b) tadj_begin.push_back(h->tadj.begin(b));
     for (int b = 1; b < h->tadj.G; ++b) {
       const long long u = h->tadj.begin(b);
       if (u % nch == 0) continue;
@@ -491,6 +493,7 @@ ash_status create_impl(ash_hologram** out, int nx, int ny, const float* amp, int
     if ((st = ws(h, &h->tc_split, (size_t)h->tadj.G * 2 * kTcRows)) != ASH_OK) return fail(st);
     if ((st = ws(h, &h->tc_part, (size_t)h->tfwd.G * 2 * kTcRows)) != ASH_OK) return fail(st);
     if ((st = ws(h, &h->tfwd_begin, tfwd_begin.size())) != ASH_OK) return fail(st);
+    if ((st = ws(h, &h->tadj_begin, tadj_begin.size())) != ASH_OK) return fail(st);
     if ((st = ws(h, &h->tadj_groups, tadj_groups.size() + 1)) != ASH_OK) return fail(st);
   }
   if ((st = ws(h, &h->gradc_partial, (size_t)h->gradc_gx * N * D)) != ASH_OK) return fail(st);
@@ -540,6 +543,8 @@ ash_status create_impl(ash_hologram** out, int nx, int ny, const float* amp, int
   CREATE_CUDA(cudaGetLastError());
   if (h->tc_ok) {
     CREATE_CUDA(cudaMemcpyAsync(h->tfwd_begin, tfwd_begin.data(), tfwd_begin.size() * sizeof(long long),
+                                cudaMemcpyHostToDevice, s));
+    CREATE_CUDA(cudaMemcpyAsync(h->tadj_begin, tadj_begin.data(), tadj_begin.size() * sizeof(long long),
                                 cudaMemcpyHostToDevice, s));
     if (!tadj_groups.empty())
       CREATE_CUDA(cudaMemcpyAsync(h->tadj_groups, tadj_groups.data(), tadj_groups.size() * sizeof(int),

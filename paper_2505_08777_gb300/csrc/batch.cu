@@ -8,6 +8,14 @@
 // tail effects. Each tile is dispatched on its hologram's D to the same
 // specialised tile code the single-hologram kernels use. Tiles split between
 // CTAs are finished by a fix-up pass in a fixed CTA order (deterministic).
+//
+// When every hologram has the tensor-core operand images (same K-atom count),
+// the batch runs the tensor-core transforms instead: persistent CTAs walk
+// their equal slice of the concatenated (hologram, group, spot chunk) /
+// (hologram, spot block, pixel chunk) units hologram by hologram, with the
+// same per-range code as the single-hologram kernels; each hologram sees the
+// CTAs that meet it as its own local CTAs, with its own boundary table,
+// split slots and fix-up / reduction work.
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -16,6 +24,7 @@
 
 #include "aux_kernels.cuh"
 #include "handle.h"
+#include "tc_launch.h"
 #include "transform_kernels.cuh"
 
 namespace {
@@ -240,14 +249,156 @@ struct ash_batch {
   cudaStream_t capture = nullptr;
   std::map<int, cudaGraphExec_t> graphs;
   std::string key;         // autotuner cache key
+  // tensor-core path
+  int variant = 0;         // 0 auto, 1 FMA-pipe kernels, 2 tensor-core kernels
+  bool tc_ok = false;      // every hologram has tensor-core images with the same K-atom count
+  int tc_na = 0;
+  int tc_slots = 0;        // resident CTAs of the tensor-core adjoint
+  int tc_fwd_per_sm = 0, tc_adj_per_sm = 0;
+  TcAdjParams* d_adj = nullptr;
+  TcFwdParams* d_fwd = nullptr;
+  long long* d_hu0 = nullptr;      // [2][count + 1] unit offsets: adjoint, forward
+  int* d_g0 = nullptr;             // [2][count] first CTA meeting each hologram
+  long long* d_begin = nullptr;    // per-hologram CTA boundary tables
+  float2* d_tsplit = nullptr;      // per-hologram split slots
+  int2* d_lists = nullptr;         // adjoint fix-up list, then forward reduction list
+  TcFieldDesc* d_field = nullptr;
+  int* d_tiles0 = nullptr;
+  TcBatchSched bs_adj{}, bs_fwd{};
+  int n_fix = 0, n_red = 0;
+  size_t cap_begin = 0, cap_split = 0, cap_fix = 0;
+  bool use_tc() const { return tc_ok && variant != 1; }
 };
 
 namespace {
 
-void set_grid(ash_batch* b, int G) {
+// CTA boundary tables, split slots and work lists of the tensor-core
+// launches for the current grid (adjoint grid G, forward grid scaled by the
+// two kernels' resident CTAs per SM).
+ash_status build_tc(ash_batch* b) {
+  const int count = b->count;
+  std::vector<long long> hu0(2 * (count + 1)), begins;
+  std::vector<int> g0(2 * count);
+  std::vector<int2> fix, red;
+  std::vector<TcAdjParams> adj(count);
+  std::vector<TcFwdParams> fwd(count);
+  size_t split_off = 0;
+  for (int x = 0; x < 2; ++x) {   // 0 adjoint, 1 forward
+    long long* off = &hu0[(size_t)x * (count + 1)];
+    off[0] = 0;
+    for (int h = 0; h < count; ++h) {
+      const Geometry& g = b->holos[h]->g;
+      const long long W = x == 0 ? (long long)g.T * kTcGroupsPerTile * ((g.N + kTcChunk - 1) / kTcChunk)
+                                 : (long long)((g.N + kTcRows - 1) / kTcRows) * g.T * kTcChunksPerTile;
+      off[h + 1] = off[h] + W;
+    }
+    const long long U = off[count];
+    long long Gl = x == 0 ? b->G : ((long long)b->G * b->tc_fwd_per_sm) / (b->tc_adj_per_sm > 0 ? b->tc_adj_per_sm : 1);
+    if (Gl < 1) Gl = 1;
+    if (Gl > U) Gl = U;
+    const int G = (int)Gl;
+    TcBatchSched& bs = x == 0 ? b->bs_adj : b->bs_fwd;
+    bs.count = count;
+    bs.U = U;
+    bs.G = G;
+    auto owner = [&](long long u) {
+      int lo = 0, hi = G - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (bs.begin(mid) <= u) lo = mid;
+        else hi = mid - 1;
+      }
+      return lo;
+    };
+    for (int h = 0; h < count; ++h) {
+      const ash_hologram* H = b->holos[h];
+      const Geometry& g = H->g;
+      const long long Uh = off[h], Wh = off[h + 1] - off[h];
+      const int ga = owner(Uh), gb = owner(Uh + Wh - 1), Gh = gb - ga + 1;
+      g0[(size_t)x * count + h] = ga;
+      const size_t tab = begins.size();
+      for (int k = 0; k <= Gh; ++k) {
+        const long long v = bs.begin(ga + k) - Uh;
+        begins.push_back(v < 0 ? 0 : (v > Wh ? Wh : v));
+      }
+      const size_t so = split_off;
+      split_off += (size_t)Gh * 2 * kTcRows;
+      if (x == 0) {
+        const int nch = (g.N + kTcChunk - 1) / kTcChunk;
+        for (int k = 1; k < Gh; ++k) {
+          const long long u = begins[tab + k];
+          if (u % nch == 0) continue;
+          const int grp = (int)(u / nch);
+          if (fix.empty() || fix.back().x != h || fix.back().y != grp) fix.push_back(make_int2(h, grp));
+        }
+        TcAdjParams& p = adj[h];
+        p.g = g;
+        p.zs = H->zs;
+        p.czs = H->czs;
+        p.rot = H->rot;
+        p.y = H->y;
+        p.amp_img = H->amp_img;
+        p.out.phase_out = H->wgs_phase;
+        p.out.epilogue = kEpiPhase | kEpiFimg;
+        p.fimg = H->fimg;
+        p.begin = reinterpret_cast<const long long*>(tab);    // offsets, rebased below
+        p.G = Gh;
+        p.split = reinterpret_cast<float2*>(so);
+        p.err = H->err_word;
+      } else {
+        TcFwdParams& p = fwd[h];
+        p.g = g;
+        p.zs = H->zs;
+        p.czs = H->czs;
+        p.rot = H->rot;
+        p.fimg = H->fimg;
+        p.sched.nb = (g.N + kTcRows - 1) / kTcRows;
+        p.sched.nq = g.T * kTcChunksPerTile;
+        p.sched.G = Gh;
+        p.rep = tc_fwd_rep(g.N);
+        p.begin = reinterpret_cast<const long long*>(tab);
+        p.E = H->wgs_E;
+        p.part = reinterpret_cast<float2*>(so);
+        p.err = H->err_word;
+        for (int blk = 0; blk < p.sched.nb; ++blk) red.push_back(make_int2(h, blk));
+      }
+    }
+  }
+  if (begins.size() > b->cap_begin || split_off > b->cap_split || fix.size() + red.size() > b->cap_fix)
+    return fail(ASH_ERR_INVALID_ARG, "batch tensor-core tables exceed their capacity");
+  for (auto& p : adj) {
+    p.begin = b->d_begin + reinterpret_cast<size_t>(p.begin);
+    p.split = b->d_tsplit + reinterpret_cast<size_t>(p.split);
+  }
+  for (auto& p : fwd) {
+    p.begin = b->d_begin + reinterpret_cast<size_t>(p.begin);
+    p.part = b->d_tsplit + reinterpret_cast<size_t>(p.part);
+  }
+  b->n_fix = (int)fix.size();
+  b->n_red = (int)red.size();
+  std::vector<int2> lists(fix);
+  lists.insert(lists.end(), red.begin(), red.end());
+  b->bs_adj.hu0 = b->d_hu0;
+  b->bs_adj.g0 = b->d_g0;
+  b->bs_fwd.hu0 = b->d_hu0 + (count + 1);
+  b->bs_fwd.g0 = b->d_g0 + count;
+  cudaError_t e;
+  if ((e = cudaMemcpy(b->d_hu0, hu0.data(), hu0.size() * sizeof(long long), cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(b->d_g0, g0.data(), g0.size() * sizeof(int), cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(b->d_begin, begins.data(), begins.size() * sizeof(long long), cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(b->d_adj, adj.data(), adj.size() * sizeof(TcAdjParams), cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(b->d_fwd, fwd.data(), fwd.size() * sizeof(TcFwdParams), cudaMemcpyHostToDevice)) ||
+      (!lists.empty() &&
+       (e = cudaMemcpy(b->d_lists, lists.data(), lists.size() * sizeof(int2), cudaMemcpyHostToDevice))))
+    return status_cuda(e, "batch tensor-core tables");
+  return ASH_OK;
+}
+
+ash_status set_grid(ash_batch* b, int G) {
+  const int slots = b->use_tc() ? b->tc_slots : b->slots;
   if (G < 1) G = 1;
-  if (G > kGridFactorMax * b->slots) G = kGridFactorMax * b->slots;
-  if ((long long)G > b->U) G = (int)b->U;
+  if (G > kGridFactorMax * slots) G = kGridFactorMax * slots;
+  if (!b->use_tc() && (long long)G > b->U) G = (int)b->U;
   if (G != b->G) {
     for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
     b->graphs.clear();
@@ -266,6 +417,8 @@ void set_grid(ash_batch* b, int G) {
       }
     }
   }
+  if (b->use_tc()) return build_tc(b);
+  return ASH_OK;
 }
 
 BatchParams params_of(const ash_batch* b) {
@@ -297,7 +450,38 @@ ash_status enqueue_batch_adjoint(ash_batch* b, cudaStream_t s) {
   return ASH_OK;
 }
 
+ash_status enqueue_tc_forward(ash_batch* b, cudaStream_t s) {
+  BCUDA(tc_launch_forward_batch(b->tc_na, b->d_fwd, b->bs_fwd, s));
+  BCUDA(tc_launch_forward_reduce_batch(b->d_fwd, b->d_lists + b->n_fix, b->n_red, s));
+  return ASH_OK;
+}
+
+ash_status enqueue_tc_adjoint(ash_batch* b, cudaStream_t s) {
+  BCUDA(tc_launch_adjoint_batch(b->tc_na, b->d_adj, b->bs_adj, s));
+  BCUDA(tc_launch_adjoint_fixup_batch(b->d_adj, b->d_lists, b->n_fix, s));
+  return ASH_OK;
+}
+
+// Tensor-core loop: the first forward converts the phases; every adjoint
+// also writes the next forward's nearfield images.
+ash_status enqueue_tc_body(ash_batch* b, int iters, cudaStream_t s) {
+  const BatchParams p = params_of(b);
+  ash_status st;
+  BCUDA(tc_field_img_batch(b->d_field, b->d_tiles0, b->count, b->total_tiles, s));
+  if ((st = enqueue_tc_forward(b, s)) != ASH_OK) return st;
+  for (int it = 0; it < iters; ++it) {
+    k_batch_update<<<b->count, 1024, 0, s>>>(p);
+    BCUDA(cudaGetLastError());
+    if ((st = enqueue_tc_adjoint(b, s)) != ASH_OK) return st;
+    if ((st = enqueue_tc_forward(b, s)) != ASH_OK) return st;
+  }
+  k_batch_metrics<<<b->count, 1024, 0, s>>>(p);
+  BCUDA(cudaGetLastError());
+  return ASH_OK;
+}
+
 ash_status enqueue_batch_body(ash_batch* b, int iters, cudaStream_t s) {
+  if (b->use_tc()) return enqueue_tc_body(b, iters, s);
   const BatchParams p = params_of(b);
   ash_status st;
   for (int it = 0; it < iters; ++it) {
@@ -318,6 +502,9 @@ void destroy_batch(ash_batch* b) {
   b->graphs.clear();
   if (b->dev) cudaFree(b->dev);
   if (b->split_buf) cudaFree(b->split_buf);
+  for (void* q : {(void*)b->d_adj, (void*)b->d_fwd, (void*)b->d_hu0, (void*)b->d_g0, (void*)b->d_begin,
+                  (void*)b->d_tsplit, (void*)b->d_lists, (void*)b->d_field, (void*)b->d_tiles0})
+    if (q) cudaFree(q);
   if (b->capture) cudaStreamDestroy(b->capture);
   for (ash_hologram* h : b->holos) ash_hologram_destroy(h);
   delete b;
@@ -432,8 +619,45 @@ ash_status ash_batch_create(ash_batch** out, int count, const ash_hologram_desc*
     return bail(status_cuda(e, "batch descriptor upload"));
   if ((e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking)) != cudaSuccess)
     return bail(status_cuda(e, "batch capture stream"));
-  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return bail(status_cuda(e, "batch set-up"));
-  set_grid(b, b->slots);
+  // tensor-core path: every hologram has the operand images, one K-atom count
+  b->tc_ok = true;
+  for (const ash_hologram* h : b->holos)
+    if (!h->tc_ok || h->tc_na != b->holos[0]->tc_na) b->tc_ok = false;
+  if (b->tc_ok) {
+    b->tc_na = b->holos[0]->tc_na;
+    // the batch kernels' smem limits are set with the single-hologram kernels' (tc_prepare)
+    if ((e = tc_batch_ctas_per_sm(b->tc_na, &b->tc_adj_per_sm, &b->tc_fwd_per_sm)) != cudaSuccess)
+      return bail(status_cuda(e, "batch tensor-core occupancy"));
+    b->tc_slots = sms * b->tc_adj_per_sm;
+    const size_t gmax = (size_t)kGridFactorMax * b->tc_slots;
+    size_t blocks = 0;
+    std::vector<TcFieldDesc> fd(count);
+    std::vector<int> tiles0(count);
+    int t0 = 0;
+    for (int i = 0; i < count; ++i) {
+      const ash_hologram* h = b->holos[i];
+      blocks += (h->g.N + kTcRows - 1) / kTcRows;
+      fd[i] = TcFieldDesc{h->g, h->amp_img, h->wgs_phase, h->fimg};
+      tiles0[i] = t0;
+      t0 += h->g.T;
+    }
+    b->cap_begin = 2 * gmax + 4 * (size_t)count + 4;
+    b->cap_split = (2 * gmax + 2 * (size_t)count) * 2 * kTcRows;
+    b->cap_fix = gmax + blocks + (size_t)count;
+    if (cudaMalloc(&b->d_adj, sizeof(TcAdjParams) * count) || cudaMalloc(&b->d_fwd, sizeof(TcFwdParams) * count) ||
+        cudaMalloc(&b->d_hu0, sizeof(long long) * 2 * (count + 1)) || cudaMalloc(&b->d_g0, sizeof(int) * 2 * count) ||
+        cudaMalloc(&b->d_begin, sizeof(long long) * b->cap_begin) ||
+        cudaMalloc(&b->d_tsplit, sizeof(float2) * b->cap_split) || cudaMalloc(&b->d_lists, sizeof(int2) * b->cap_fix) ||
+        cudaMalloc(&b->d_field, sizeof(TcFieldDesc) * count) || cudaMalloc(&b->d_tiles0, sizeof(int) * count)) {
+      cudaGetLastError();
+      return bail(fail(ASH_ERR_OOM, "batch tensor-core table allocation"));
+    }
+    if ((e = cudaMemcpy(b->d_field, fd.data(), sizeof(TcFieldDesc) * count, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(b->d_tiles0, tiles0.data(), sizeof(int) * count, cudaMemcpyHostToDevice)))
+      return bail(status_cuda(e, "batch tensor-core descriptors"));
+  }
+  ash_status gst = set_grid(b, b->use_tc() ? b->tc_slots : b->slots);
+  if (gst != ASH_OK) return bail(gst);
   *out = b;
   return ASH_OK;
 }
@@ -446,19 +670,33 @@ ash_status ash_batch_info(const ash_batch* b, int* count, int* grid, int* reside
   if (!b) return fail(ASH_ERR_INVALID_ARG, "batch is NULL");
   if (count) *count = b->count;
   if (grid) *grid = b->G;
-  if (resident_ctas) *resident_ctas = b->slots;
+  if (resident_ctas) *resident_ctas = b->use_tc() ? b->tc_slots : b->slots;
   if (units) *units = b->U;
   return ASH_OK;
 }
 
 ash_status ash_batch_set_grid(ash_batch* b, int grid) {
   if (!b || grid < 1) return fail(ASH_ERR_INVALID_ARG, "NULL batch or grid < 1");
-  set_grid(b, grid);
-  return ASH_OK;
+  return set_grid(b, grid);
+}
+
+ash_status ash_batch_set_variant(ash_batch* b, int variant) {
+  if (!b || variant < 0 || variant > 2) return fail(ASH_ERR_INVALID_ARG, "variant must be 0, 1 or 2");
+  if (variant == 2 && !b->tc_ok)
+    return fail(ASH_ERR_UNSUPPORTED, "tensor-core batch needs every hologram with the same K-atom count (D <= 21)");
+  b->variant = variant;
+  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  b->graphs.clear();
+  b->G = 0;
+  return set_grid(b, b->use_tc() ? b->tc_slots : b->slots);
 }
 
 int ash_batch_wgs_launches(const ash_batch* b, int iters) {
   if (!b || iters < 0) return -1;
+  if (b->use_tc()) {
+    const int fwd = 1 + (b->n_red > 0 ? 1 : 0), adj = 1 + (b->n_fix > 0 ? 1 : 0);
+    return 1 + fwd + iters * (1 + adj + fwd) + 1;   // nearfield images, forward, iterations, metrics
+  }
   const int fwd = 2, adj = b->split ? 2 : 1;
   return iters * (fwd + 1 + adj) + fwd + 1;
 }
@@ -512,9 +750,11 @@ ash_status ash_batch_wgs(ash_batch* b, float* const* phases, float* const* weigh
 ash_status ash_batch_tune(ash_batch* b, const float* const* phases, const char* cache_path, int* grid_out,
                           void* stream) {
   if (!b || !phases) return fail(ASH_ERR_INVALID_ARG, "NULL argument");
-  const std::string hit = cache_lookup(cache_path, b->key);
+  const std::string key = b->key + (b->use_tc() ? "_tc" : "");
+  const std::string hit = cache_lookup(cache_path, key);
   if (!hit.empty()) {
-    set_grid(b, std::stoi(hit));
+    ash_status gst = set_grid(b, std::stoi(hit));
+    if (gst != ASH_OK) return gst;
     if (grid_out) *grid_out = b->G;
     return ASH_OK;
   }
@@ -525,8 +765,18 @@ ash_status ash_batch_tune(ash_batch* b, const float* const* phases, const char* 
     BCUDA(cudaMemcpyAsync(h->wgs_phase, phases[i], (size_t)h->g.nx * h->g.ny * 4, cudaMemcpyDeviceToDevice, s));
     BCUDA(cudaMemsetAsync(h->y, 0, (size_t)h->g.N * sizeof(float2), s));
   }
+  if (b->use_tc()) BCUDA(tc_field_img_batch(b->d_field, b->d_tiles0, b->count, b->total_tiles, s));
+  auto fwd_adj = [&]() -> ash_status {
+    if (b->use_tc()) {
+      ash_status st = enqueue_tc_forward(b, s);
+      return st == ASH_OK ? enqueue_tc_adjoint(b, s) : st;
+    }
+    ash_status st = enqueue_batch_forward(b, s);
+    return st == ASH_OK ? enqueue_batch_adjoint(b, s) : st;
+  };
   // candidate launch shapes: fractions and multiples of the resident CTAs
-  const int cands[] = {b->slots / 2, b->slots, (3 * b->slots) / 2, 2 * b->slots, 3 * b->slots, 4 * b->slots};
+  const int sl = b->use_tc() ? b->tc_slots : b->slots;
+  const int cands[] = {sl / 2, sl, (3 * sl) / 2, 2 * sl, 3 * sl, 4 * sl};
   cudaEvent_t e0, e1;
   BCUDA(cudaEventCreate(&e0));
   BCUDA(cudaEventCreate(&e1));
@@ -534,15 +784,11 @@ ash_status ash_batch_tune(ash_batch* b, const float* const* phases, const char* 
   int best_g = b->slots;
   for (int c : cands) {
     if (c < 1) continue;
-    set_grid(b, c);
-    ash_status st = enqueue_batch_forward(b, s);   // warm-up
-    if (st == ASH_OK) st = enqueue_batch_adjoint(b, s);
+    ash_status st = set_grid(b, c);
+    if (st == ASH_OK) st = fwd_adj();   // warm-up
     if (st != ASH_OK) return st;
     BCUDA(cudaEventRecord(e0, s));
-    for (int r = 0; r < 2 && st == ASH_OK; ++r) {
-      st = enqueue_batch_forward(b, s);
-      if (st == ASH_OK) st = enqueue_batch_adjoint(b, s);
-    }
+    for (int r = 0; r < 2 && st == ASH_OK; ++r) st = fwd_adj();
     if (st != ASH_OK) return st;
     BCUDA(cudaEventRecord(e1, s));
     BCUDA(cudaEventSynchronize(e1));
@@ -555,8 +801,9 @@ ash_status ash_batch_tune(ash_batch* b, const float* const* phases, const char* 
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  set_grid(b, best_g);
-  cache_store(cache_path, b->key, b->G);
+  ash_status gst = set_grid(b, best_g);
+  if (gst != ASH_OK) return gst;
+  cache_store(cache_path, key, b->G);
   if (grid_out) *grid_out = b->G;
   return ASH_OK;
 }

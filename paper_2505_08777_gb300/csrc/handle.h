@@ -44,6 +44,7 @@ struct ash_hologram {
   float2* tc_split = nullptr;   // [tadj.G][2][128]
   float2* tc_part = nullptr;    // [tfwd.G][2][128]
   long long* tfwd_begin = nullptr;   // [tfwd.G + 1] CTA range starts of the forward
+  long long* tadj_begin = nullptr;   // [tadj.G + 1] CTA range starts of the adjoint
   int* tadj_groups = nullptr;   // groups split between adjoint CTA ranges
   int tadj_nsplit = 0;
   float2* split = nullptr;

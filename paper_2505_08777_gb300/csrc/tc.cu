@@ -33,6 +33,14 @@ cudaError_t prepare_na(int* adj, int* fwd) {
   const void* ka = (const void*)k_tc_adjoint<NA>;
   const void* kf = (const void*)k_tc_forward<NA>;
   cudaError_t e;
+  // the batched kernels share the single-hologram kernels' shapes
+  for (const void* k : {(const void*)k_tc_adjoint_batch<NA>, (const void*)k_tc_forward_batch<NA>}) {
+    const int smem = k == (const void*)k_tc_adjoint_batch<NA> ? (int)TcAdjShape<NA>::SMEM : (int)TcFwdShape<NA>::SMEM;
+    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
+    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  (int)cudaSharedmemCarveoutMaxShared)))
+      return e;
+  }
   if ((e = cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcAdjShape<NA>::SMEM)))
     return e;
   if ((e = cudaFuncSetAttribute(ka, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -57,10 +65,55 @@ cudaError_t tc_prepare(int NA, int* adj_ctas_per_sm, int* fwd_ctas_per_sm) {
   return cudaErrorInvalidValue;
 }
 
+cudaError_t tc_batch_ctas_per_sm(int NA, int* adj, int* fwd) {
+  cudaError_t e;
+  if (NA == 1) {
+    if ((e = ctas_per_sm((const void*)k_tc_adjoint_batch<1>, TcAdjShape<1>::SMEM, 2 * kTcChunk, adj))) return e;
+    return ctas_per_sm((const void*)k_tc_forward_batch<1>, TcFwdShape<1>::SMEM, 2 * kTcChunk, fwd);
+  }
+  if (NA == 2) {
+    if ((e = ctas_per_sm((const void*)k_tc_adjoint_batch<2>, TcAdjShape<2>::SMEM, 2 * kTcChunk, adj))) return e;
+    return ctas_per_sm((const void*)k_tc_forward_batch<2>, TcFwdShape<2>::SMEM, 2 * kTcChunk, fwd);
+  }
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t tc_launch_adjoint(int NA, const TcAdjParams& p, int grid, cudaStream_t s) {
   if (NA == 1) k_tc_adjoint<1><<<grid, kTcThreads, TcAdjShape<1>::SMEM, s>>>(p);
   else if (NA == 2) k_tc_adjoint<2><<<grid, kTcThreads, TcAdjShape<2>::SMEM, s>>>(p);
   else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t tc_launch_adjoint_batch(int NA, const TcAdjParams* ps, const TcBatchSched& bs, cudaStream_t s) {
+  if (NA == 1) k_tc_adjoint_batch<1><<<bs.G, kTcThreads, TcAdjShape<1>::SMEM, s>>>(ps, bs);
+  else if (NA == 2) k_tc_adjoint_batch<2><<<bs.G, kTcThreads, TcAdjShape<2>::SMEM, s>>>(ps, bs);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t tc_launch_adjoint_fixup_batch(const TcAdjParams* ps, const int2* list, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_tc_adjoint_fixup_batch<<<n, kTcThreads, 0, s>>>(ps, list);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_launch_forward_batch(int NA, const TcFwdParams* ps, const TcBatchSched& bs, cudaStream_t s) {
+  if (NA == 1) k_tc_forward_batch<1><<<bs.G, kTcThreads, TcFwdShape<1>::SMEM, s>>>(ps, bs);
+  else if (NA == 2) k_tc_forward_batch<2><<<bs.G, kTcThreads, TcFwdShape<2>::SMEM, s>>>(ps, bs);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t tc_launch_forward_reduce_batch(const TcFwdParams* ps, const int2* list, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_tc_forward_reduce_batch<<<dim3(n, kTcRows / 32), dim3(32, 32), 0, s>>>(ps, list);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_field_img_batch(const TcFieldDesc* ds, const int* tiles0, int count, int total_tiles, cudaStream_t s) {
+  const long long px = (long long)total_tiles * kTilePix;
+  k_tc_field_img_batch<<<blocks_for(px, 256), 256, 0, s>>>(ds, tiles0, count, total_tiles);
   return cudaGetLastError();
 }
 

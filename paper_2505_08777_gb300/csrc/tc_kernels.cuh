@@ -47,6 +47,7 @@ struct TcAdjShape {
   static constexpr int NBARS = 4 + NB;
   // [alignment slack][A x 2][B ring][y'][barriers][armed counts][counter][TMEM slot][producer state]
   static constexpr size_t SMEM = 1024 + 2 * A_BYTES + NB * B_BYTES + Y_BYTES + NBARS * 12 + 8 + 16;
+  static constexpr size_t TSLOT = 2 * A_BYTES + NB * B_BYTES + Y_BYTES + NBARS * 12 + 8;   // from the aligned base
 };
 
 // Forward shared memory: 1 A slot (spot block), a ring of B slots (64 pixel
@@ -61,6 +62,7 @@ struct TcFwdShape {
   static constexpr int NBARS = 3 + NBB + NF;
   // [alignment slack][A][B ring][f ring][barriers][armed counts][counter][TMEM slot][producer state]
   static constexpr size_t SMEM = 1024 + A_BYTES + NBB * B_BYTES + NF * F_BYTES + NBARS * 12 + 8 + 32;
+  static constexpr size_t TSLOT = A_BYTES + NBB * B_BYTES + NF * F_BYTES + NBARS * 12 + 8;
 };
 
 // --- operand images ---------------------------------------------------------
@@ -226,6 +228,52 @@ __device__ __forceinline__ void tc_drain(uint64_t* bars, const uint32_t* armed, 
     if (armed[k] > 0) mbar_wait(&bars[k], (armed[k] - 1) & 1u, kTcWaitPolls);
 }
 
+__device__ __forceinline__ uint8_t* tc_smem_base(uint8_t* raw) {
+  return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~(uintptr_t)1023);
+}
+
+// Two TMEM buffers of 64 fp32 columns for the CTA's lifetime (warp 0).
+__device__ __forceinline__ uint32_t tc_tmem_alloc(uint32_t* slot) {
+  if ((threadIdx.x >> 5) == 0) tmem_alloc(slot, 2 * kTcChunk);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  return *slot;
+}
+
+__device__ __forceinline__ void tc_tmem_free(uint32_t tmem) {
+  tc_fence_before();
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0) tmem_dealloc(tmem, 2 * kTcChunk);
+}
+
+// Start of one unit range: fresh barriers (the previous range's, if any, are
+// invalidated first), counters at zero, then a CTA barrier.
+__device__ __forceinline__ void tc_range_begin(uint64_t* bars, uint32_t* armed, uint32_t* cnt, int nbars, bool first) {
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < nbars; ++k) {
+      if (!first) mbar_inval(&bars[k]);
+      mbar_init(&bars[k], 1);
+      armed[k] = 0;
+    }
+    cnt[0] = cnt[1] = 0;
+    fence_mbar_init();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+}
+
+// End of a range: every thread is done, every copy and MMA has landed.
+__device__ __forceinline__ void tc_range_end(uint64_t* bars, const uint32_t* armed, int nbars, bool drained = false) {
+  if (!drained) {
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0) tc_drain(bars, armed, nbars);
+  }
+  __syncthreads();
+}
+
 // Adjoint output of row r of chunk qc (in the pixel's user-layout slot and,
 // for kEpiFimg, in the tc-layout nearfield f = A exp(i arg g)).
 __device__ __forceinline__ void tc_adjoint_epilogue(const TcAdjParams& p, long long qc, int r, float gr, float gi) {
@@ -258,11 +306,10 @@ __device__ __forceinline__ void tc_adjoint_epilogue(const TcAdjParams& p, long l
 // while the warps work through chunk c. (Two chunks of lookahead were
 // measured slower here: the deeper B ring it needs costs a CTA per SM.)
 template <int NA>
-__global__ void __launch_bounds__(kTcThreads, 4) k_tc_adjoint(const TcAdjParams p) {
+__device__ __forceinline__ void tc_adjoint_range(const TcAdjParams& p, long long u0, long long u1, int cta,
+                                                 uint8_t* base, uint32_t tmem, bool first_range) {
   using S = TcAdjShape<NA>;
   constexpr int NB = S::NB, NBARS = S::NBARS;
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   float* sA = reinterpret_cast<float*>(base);                      // [2][NA][128][32]
   float* sB = sA + 2 * NA * 4096;                                  // [NB][NA][64][32]
   float4* sY = reinterpret_cast<float4*>(sB + NB * NA * 2048);     // [4 warps][32 spot pairs]
@@ -275,30 +322,18 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_tc_adjoint(const TcAdjParams 
   uint32_t* tslot = cnt + 2;
   int* pst = reinterpret_cast<int*>(tslot + 1);                    // next MMA: chunk, group, spot chunk
 
+  (void)tslot;
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
   const Geometry& G = p.g;
   const int N = G.N;
   const int nch = (N + kTcChunk - 1) / kTcChunk;
-  const long long u0 = p.sched.begin(blockIdx.x), u1 = p.sched.begin(blockIdx.x + 1);
   const int nc = (int)(u1 - u0);
   // chunk c of this range is spot chunk j of group s; (s, j) advance
   // incrementally (no 64-bit division per chunk)
   const int s0 = (int)(u0 / nch), j0 = (int)(u0 % nch);
   const int s_last = nc > 0 ? (int)((u1 - 1) / nch) : s0;
 
-  if (w == 0) tmem_alloc(tslot, 2 * kTcChunk);
-  if (t == 0) {
-    for (int k = 0; k < NBARS; ++k) {
-      mbar_init(&bars[k], 1);
-      armed[k] = 0;
-    }
-    cnt[0] = cnt[1] = 0;
-    fence_mbar_init();
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *tslot;
+  tc_range_begin(bars, armed, cnt, NBARS, first_range);
   const uint32_t tlane = (uint32_t)(w * 32) << 16;
   bool ok = true;
 
@@ -421,36 +456,76 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_tc_adjoint(const TcAdjParams 
       if ((long long)s * nch >= u0 && (long long)(s + 1) * nch <= u1) {
         tc_adjoint_epilogue(p, 2LL * s + (t >> 6), t & 63, gr, gi);
       } else {
-        p.split[((size_t)blockIdx.x * 2 + (s == s0 ? 0 : 1)) * kTcRows + t] = make_float2(gr, gi);
+        p.split[((size_t)cta * 2 + (s == s0 ? 0 : 1)) * kTcRows + t] = make_float2(gr, gi);
       }
     }
     s = s_next;
     jch = j_next;
   }
-  tc_fence_before();
-  __syncthreads();
-  if (t == 0) tc_drain(bars, armed, NBARS);
-  __syncwarp();
-  if (w == 0) tmem_dealloc(tmem, 2 * kTcChunk);
+  tc_range_end(bars, armed, NBARS);
   if (!ok && t == 0) atomicOr(p.err, kErrTimeout);
+}
+
+template <int NA>
+__global__ void __launch_bounds__(kTcThreads, 4) k_tc_adjoint(const TcAdjParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = tc_smem_base(smem_raw);
+  const uint32_t tmem = tc_tmem_alloc(reinterpret_cast<uint32_t*>(base + TcAdjShape<NA>::TSLOT));
+  const int g = blockIdx.x;
+  tc_adjoint_range<NA>(p, p.begin[g], p.begin[g + 1], g, base, tmem, true);
+  tc_tmem_free(tmem);
+}
+
+// Batched form: CTA g of a launch over the concatenated units of many
+// holograms (hologram h owns units [hu0[h], hu0[h + 1])) runs its slice of
+// each hologram it meets, in order, as that hologram's local CTA g - g0[h].
+template <int NA>
+__global__ void __launch_bounds__(kTcThreads, 4) k_tc_adjoint_batch(const TcAdjParams* __restrict__ ps,
+                                                                     const TcBatchSched bs) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = tc_smem_base(smem_raw);
+  const uint32_t tmem = tc_tmem_alloc(reinterpret_cast<uint32_t*>(base + TcAdjShape<NA>::TSLOT));
+  const int g = blockIdx.x;
+  const long long B0 = bs.begin(g), B1 = bs.begin(g + 1);
+  bool first = true;
+  for (int h = bs.holo_of(B0); h < bs.count && bs.hu0[h] < B1; ++h) {
+    const long long lu0 = max(B0, bs.hu0[h]) - bs.hu0[h], lu1 = min(B1, bs.hu0[h + 1]) - bs.hu0[h];
+    if (lu1 <= lu0) continue;
+    // this hologram's parameter block, staged in shared memory
+    __shared__ TcAdjParams sp;
+    __syncthreads();
+    if (threadIdx.x == 0) sp = ps[h];
+    __syncthreads();
+    tc_adjoint_range<NA>(sp, lu0, lu1, g - bs.g0[h], base, tmem, first);
+    first = false;
+  }
+  tc_tmem_free(tmem);
 }
 
 // Groups whose spots were split between CTAs of k_tc_adjoint: the partial
 // sums in CTA order, then the epilogue. One CTA of 128 threads per split group.
-static __global__ void k_tc_adjoint_fixup(const TcAdjParams p) {
+__device__ __forceinline__ void tc_adjoint_fixup_group(const TcAdjParams& p, long long s) {
   const int nch = (p.g.N + kTcChunk - 1) / kTcChunk;
-  const long long s = p.split_groups[blockIdx.x], ulo = s * nch, uhi = ulo + nch - 1;
+  const long long ulo = s * nch, uhi = ulo + nch - 1;
   const int t = threadIdx.x;
-  const int b_lo = p.sched.owner(ulo), b_hi = p.sched.owner(uhi);
+  const int b_lo = tc_owner(p.begin, p.G, ulo), b_hi = tc_owner(p.begin, p.G, uhi);
   float gr = 0.0f, gi = 0.0f;
   for (int cb = b_lo; cb <= b_hi; ++cb) {
-    const long long beg = p.sched.begin(cb);
-    if (p.sched.begin(cb + 1) <= beg) continue;
+    const long long beg = p.begin[cb];
+    if (p.begin[cb + 1] <= beg) continue;
     const float2 v = p.split[((size_t)cb * 2 + (beg >= ulo ? 0 : 1)) * kTcRows + t];
     gr += v.x;
     gi += v.y;
   }
   tc_adjoint_epilogue(p, 2 * s + (t >> 6), t & 63, gr, gi);
+}
+
+static __global__ void k_tc_adjoint_fixup(const TcAdjParams p) { tc_adjoint_fixup_group(p, p.split_groups[blockIdx.x]); }
+
+// Batched fix-up: entry i of `list` is (hologram, split group).
+static __global__ void k_tc_adjoint_fixup_batch(const TcAdjParams* __restrict__ ps, const int2* __restrict__ list) {
+  const int2 e = list[blockIdx.x];
+  tc_adjoint_fixup_group(ps[e.x], e.y);
 }
 
 // --- forward ------------------------------------------------------------------
@@ -465,11 +540,10 @@ static __global__ void k_tc_adjoint_fixup(const TcAdjParams p) {
 // c + 2. A spot block's first MMA waits until the previous block's last MMA
 // has completed, then its A is reloaded (once per block change).
 template <int NA>
-__global__ void __launch_bounds__(kTcThreads, 4) k_tc_forward(const TcFwdParams p) {
+__device__ __forceinline__ void tc_forward_range(const TcFwdParams& p, long long u0, long long u1, int cta,
+                                                 uint8_t* base, uint32_t tmem, bool first_range) {
   using S = TcFwdShape<NA>;
   constexpr int NBB = S::NBB, NF = S::NF, NBARS = S::NBARS;
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   float* sA = reinterpret_cast<float*>(base);                      // [NA][128][32]
   float* sB = sA + NA * 4096;                                      // [NBB][NA][64][32]
   float4* sF = reinterpret_cast<float4*>(sB + NBB * NA * 2048);    // [NF][32]
@@ -483,29 +557,17 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_tc_forward(const TcFwdParams 
   uint32_t* tslot = cnt + 2;
   int* pst = reinterpret_cast<int*>(tslot + 1);   // next MMA: chunk, block, pixel chunk; block in A; A unchecked
 
+  (void)tslot;
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
   const Geometry& G = p.g;
   const int N = G.N;
   const int nq = G.T * kTcChunksPerTile;
-  const long long u0 = p.sched.begin(blockIdx.x), u1 = p.sched.begin(blockIdx.x + 1);
   const int nc = (int)(u1 - u0);
   // chunk c of this range is pixel chunk q of spot block b; (b, q) advance
   // incrementally
   const int b0 = (int)(u0 / nq), q0 = (int)(u0 % nq);
 
-  if (w == 0) tmem_alloc(tslot, 2 * kTcChunk);
-  if (t == 0) {
-    for (int k = 0; k < NBARS; ++k) {
-      mbar_init(&bars[k], 1);
-      armed[k] = 0;
-    }
-    cnt[0] = cnt[1] = 0;
-    fence_mbar_init();
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *tslot;
+  tc_range_begin(bars, armed, cnt, NBARS, first_range);
   const uint32_t tlane = (uint32_t)(w * 32) << 16;
   bool ok = true;
 
@@ -653,7 +715,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_tc_forward(const TcFwdParams 
         if ((long long)b * nq >= u0 && (long long)(b + 1) * nq <= u1) {
           if (n < N) p.E[n] = make_float2(er, ei);
         } else {
-          p.part[((size_t)blockIdx.x * 2 + (b == b0 ? 0 : 1)) * kTcRows + t] = make_float2(er, ei);
+          p.part[((size_t)cta * 2 + (b == b0 ? 0 : 1)) * kTcRows + t] = make_float2(er, ei);
         }
         er = ei = 0.0f;
       }
@@ -671,7 +733,6 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_tc_forward(const TcFwdParams 
   __syncthreads();
   if (t == 0) tc_drain(bars, armed, NBARS);
   __syncwarp();
-  if (w == 0) tmem_dealloc(tmem, 2 * kTcChunk);
   if (had_rep) {
     // the replicated last block ends this range: sum the replicas in a fixed
     // order (every MMA has completed, so A's slot is free)
@@ -690,33 +751,59 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_tc_forward(const TcFwdParams 
       if ((long long)bl * nq >= u0 && (long long)(bl + 1) * nq <= u1) {
         if (n < N) p.E[n] = make_float2(sr, si);
       } else {
-        p.part[((size_t)blockIdx.x * 2 + (bl == b0 ? 0 : 1)) * kTcRows + t] = make_float2(sr, si);
+        p.part[((size_t)cta * 2 + (bl == b0 ? 0 : 1)) * kTcRows + t] = make_float2(sr, si);
       }
     }
   }
+  tc_range_end(bars, armed, NBARS, /*drained=*/true);
   if (!ok && t == 0) atomicOr(p.err, kErrTimeout);
+}
+
+template <int NA>
+__global__ void __launch_bounds__(kTcThreads, 4) k_tc_forward(const TcFwdParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = tc_smem_base(smem_raw);
+  const uint32_t tmem = tc_tmem_alloc(reinterpret_cast<uint32_t*>(base + TcFwdShape<NA>::TSLOT));
+  const int g = blockIdx.x;
+  tc_forward_range<NA>(p, p.begin[g], p.begin[g + 1], g, base, tmem, true);
+  tc_tmem_free(tmem);
+}
+
+// Batched form (see k_tc_adjoint_batch). Its parameter block comes from
+// memory rather than the constant bank, which costs registers: three CTAs
+// per SM instead of four.
+template <int NA>
+__global__ void __launch_bounds__(kTcThreads, 3) k_tc_forward_batch(const TcFwdParams* __restrict__ ps,
+                                                                     const TcBatchSched bs) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = tc_smem_base(smem_raw);
+  const uint32_t tmem = tc_tmem_alloc(reinterpret_cast<uint32_t*>(base + TcFwdShape<NA>::TSLOT));
+  const int g = blockIdx.x;
+  const long long B0 = bs.begin(g), B1 = bs.begin(g + 1);
+  bool first = true;
+  for (int h = bs.holo_of(B0); h < bs.count && bs.hu0[h] < B1; ++h) {
+    const long long lu0 = max(B0, bs.hu0[h]) - bs.hu0[h], lu1 = min(B1, bs.hu0[h + 1]) - bs.hu0[h];
+    if (lu1 <= lu0) continue;
+    __shared__ TcFwdParams sp;
+    __syncthreads();
+    if (threadIdx.x == 0) sp = ps[h];
+    __syncthreads();
+    tc_forward_range<NA>(sp, lu0, lu1, g - bs.g0[h], base, tmem, first);
+    first = false;
+  }
+  tc_tmem_free(tmem);
 }
 
 // Spot blocks whose pixels were split between CTAs of k_tc_forward: E_n is
 // the sum of the CTAs' partial sums. CTA (b, y) sums 32 spots of block b:
 // row-lane k of the 32 x 32 threads adds the partials of CTAs g_lo + k,
 // g_lo + k + 32, ..., then a fixed-shape tree combines the row-lanes.
-static __global__ void k_tc_forward_reduce(const TcFwdParams p) {
+__device__ __forceinline__ void tc_forward_reduce_block(const TcFwdParams& p, long long b, int col) {
   __shared__ float2 acc[32][33];
   const int nq = p.g.T * kTcChunksPerTile;
-  const long long b = blockIdx.x, ulo = b * nq, uhi = ulo + nq - 1;
-  const int col = blockIdx.y * 32 + threadIdx.x, k = threadIdx.y;
-  // owners of the block's first and last units (binary search on the table)
-  auto owner = [&](long long u) {
-    int lo = 0, hi = p.sched.G - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) / 2;
-      if (p.begin[mid] <= u) lo = mid;
-      else hi = mid - 1;
-    }
-    return lo;
-  };
-  const int g_lo = owner(ulo), g_hi = owner(uhi);
+  const long long ulo = b * nq, uhi = ulo + nq - 1;
+  const int k = threadIdx.y;
+  const int g_lo = tc_owner(p.begin, p.sched.G, ulo), g_hi = tc_owner(p.begin, p.sched.G, uhi);
   if (g_lo == g_hi) return;   // one CTA owned the block and wrote E itself
   float2 v = make_float2(0.0f, 0.0f);
   for (int cb = g_lo + k; cb <= g_hi; cb += 32) {
@@ -737,6 +824,47 @@ static __global__ void k_tc_forward_reduce(const TcFwdParams p) {
   }
   const int n = (int)(b * kTcRows) + col;
   if (k == 0 && n < p.g.N) p.E[n] = acc[0][threadIdx.x];
+}
+
+static __global__ void k_tc_forward_reduce(const TcFwdParams p) {
+  tc_forward_reduce_block(p, blockIdx.x, blockIdx.y * 32 + threadIdx.x);
+}
+
+// Batched reduction: entry i of `list` is (hologram, spot block).
+static __global__ void k_tc_forward_reduce_batch(const TcFwdParams* __restrict__ ps, const int2* __restrict__ list) {
+  const int2 e = list[blockIdx.x];
+  tc_forward_reduce_block(ps[e.x], e.y, blockIdx.y * 32 + threadIdx.x);
+}
+
+// Nearfield images of a batch (one thread per pixel of the concatenated tiles).
+static __global__ void k_tc_field_img_batch(const TcFieldDesc* __restrict__ ds, const int* __restrict__ tiles0,
+                                            int count, int total_tiles) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)total_tiles * kTilePix) return;
+  const int gt = (int)(e / kTilePix);
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (tiles0[mid] <= gt) lo = mid;
+    else hi = mid - 1;
+  }
+  const TcFieldDesc& d = ds[lo];
+  const long long le = e - (long long)tiles0[lo] * kTilePix;
+  const long long qc = le / kTcChunk;
+  const int r = (int)(le % kTcChunk);
+  const Geometry& G = d.g;
+  const TcPixel px = tc_pixel(G, qc, r);
+  float fr = 0.0f, fi = 0.0f;
+  if (px.i < G.nx && px.j < G.ny) {
+    float sn, cs;
+    sincosf(d.phase[(size_t)px.j * G.nx + px.i], &sn, &cs);
+    const float a = d.amp_img[px.img];
+    fr = a * cs;
+    fi = a * sn;
+  }
+  float* q = reinterpret_cast<float*>(d.fimg) + ((size_t)qc * 32 + (r >> 1)) * 4;
+  q[r & 1] = fr;
+  q[2 + (r & 1)] = fi;
 }
 
 }  // namespace ash

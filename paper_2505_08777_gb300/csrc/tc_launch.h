@@ -136,6 +136,38 @@ struct TcFwdSched {
   }
 };
 
+// CTA whose (non-empty) range [begin[g], begin[g + 1]) contains unit u.
+__host__ __device__ inline int tc_owner(const long long* begin, int G, long long u) {
+  int lo = 0, hi = G - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (begin[mid] <= u) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Batched launches: the units of `count` holograms concatenated (hologram h
+// owns [hu0[h], hu0[h + 1])), cut into G equal CTA ranges; CTA g is local
+// CTA g - g0[h] of every hologram it meets.
+struct TcBatchSched {
+  const long long* hu0;   // [count + 1]
+  const int* g0;          // [count]
+  int count;
+  long long U;
+  int G;
+  __host__ __device__ long long begin(int g) const { return (long long)g * U / G; }
+  __host__ __device__ int holo_of(long long u) const {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (hu0[mid] <= u) lo = mid;
+      else hi = mid - 1;
+    }
+    return lo;
+  }
+};
+
 struct TcAdjParams {
   Geometry g;
   const float* zs;
@@ -145,7 +177,9 @@ struct TcAdjParams {
   const float* amp_img;   // register-image amplitude
   AdjOut out;
   float4* fimg;           // written for kEpiFimg
-  Schedule sched;         // units (group, spot chunk of 64): W = T * 8 * ceil(N / 64)
+  const long long* begin; // [G + 1] CTA range starts over the units (group, spot chunk of 64),
+                          // W = T * 8 * ceil(N / 64) of them
+  int G;
   float2* split;          // [G][2][128] partial sums of groups split between CTAs
   const int* split_groups;   // the groups whose spots span two or more CTA ranges
   unsigned* err;
@@ -172,6 +206,24 @@ cudaError_t tc_launch_adjoint(int NA, const TcAdjParams& p, int grid, cudaStream
 cudaError_t tc_launch_adjoint_fixup(const TcAdjParams& p, int n_split_groups, cudaStream_t s);
 cudaError_t tc_launch_forward(int NA, const TcFwdParams& p, int grid, cudaStream_t s);
 cudaError_t tc_launch_forward_reduce(const TcFwdParams& p, cudaStream_t s);
+// Batched launches over `count` holograms of the same K-atom count NA;
+// device arrays of their parameter blocks, the batch schedule, and the
+// fix-up / reduction work lists (hologram, group) and (hologram, spot block).
+cudaError_t tc_launch_adjoint_batch(int NA, const TcAdjParams* ps, const TcBatchSched& bs, cudaStream_t s);
+cudaError_t tc_launch_adjoint_fixup_batch(const TcAdjParams* ps, const int2* list, int n, cudaStream_t s);
+cudaError_t tc_launch_forward_batch(int NA, const TcFwdParams* ps, const TcBatchSched& bs, cudaStream_t s);
+cudaError_t tc_launch_forward_reduce_batch(const TcFwdParams* ps, const int2* list, int n, cudaStream_t s);
+// Nearfield images of a batch from each hologram's phase (the `phase` of
+// its TcFwdParams-sized descriptor below); tiles0[h] = first global tile.
+struct TcFieldDesc {
+  Geometry g;
+  const float* amp_img;
+  const float* phase;
+  float4* fimg;
+};
+// Resident CTAs per SM of the batched adjoint and forward kernels.
+cudaError_t tc_batch_ctas_per_sm(int NA, int* adj, int* fwd);
+cudaError_t tc_field_img_batch(const TcFieldDesc* ds, const int* tiles0, int count, int total_tiles, cudaStream_t s);
 cudaError_t tc_build_zs(const Geometry& g, const TcLayout& L, const float* dz, float* zs, cudaStream_t s);
 cudaError_t tc_build_coeff(const Geometry& g, const TcLayout& L, const float* coeff, const float2* anchors, float* czs,
                            float2* rot, cudaStream_t s);

@@ -249,6 +249,10 @@ class Batch:
     def set_grid(self, grid: int):
         _lib.check(self._lib.ash_batch_set_grid(self._b, int(grid)), "ash_batch_set_grid")
 
+    def set_variant(self, variant: int):
+        """0 automatic, 1 FMA-pipe kernels, 2 tensor-core kernels."""
+        _lib.check(self._lib.ash_batch_set_variant(self._b, int(variant)), "ash_batch_set_variant")
+
     def launches(self, iters: int) -> int:
         return int(self._lib.ash_batch_wgs_launches(self._b, int(iters)))
 

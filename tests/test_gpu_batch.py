@@ -1,5 +1,7 @@
-"""Batched uneven form (ash_batch_*): parity with the oracle and with the
-per-hologram path, determinism, launch-shape independence, autotuner cache."""
+"""Batched uneven form (ash_batch_*), in both kernel families (1: FMA-pipe
+kernels, 2: tensor-core kernels): parity with the oracle and with the
+per-hologram path of the same family, determinism, launch-shape
+independence, autotuner cache."""
 import os
 
 import numpy as np
@@ -27,9 +29,15 @@ def _problems(seed0=30):
             for k, (nx, ny, N, noll, flat) in enumerate(SHAPES)]
 
 
-def _batch(ps):
+VARIANTS = [1, 2]
+
+
+def _batch(ps, variant=0):
     from paper_2505_08777_gb300 import Batch
-    return Batch([(torch.from_numpy(p.amp).cuda(), torch.from_numpy(p.coeff).cuda(), p.noll) for p in ps])
+    b = Batch([(torch.from_numpy(p.amp).cuda(), torch.from_numpy(p.coeff).cuda(), p.noll) for p in ps])
+    if variant:
+        b.set_variant(variant)
+    return b
 
 
 def _state(ps):
@@ -39,9 +47,10 @@ def _state(ps):
     return ph, w, T
 
 
-def test_batch_wgs_matches_oracle_per_hologram():
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_batch_wgs_matches_oracle_per_hologram(variant):
     ps = _problems()
-    b = _batch(ps)
+    b = _batch(ps, variant)
     ph, w, T = _state(ps)
     met = b.wgs(ph, w, T, 10).cpu().numpy()
     for k, p in enumerate(ps):
@@ -53,15 +62,16 @@ def test_batch_wgs_matches_oracle_per_hologram():
         assert abs(met[k, 0] - wgs.uniformity(E, p.target)) <= 1e-4
 
 
-def test_batch_one_iteration_equals_single_path():
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_batch_one_iteration_equals_single_path(variant):
     from paper_2505_08777_gb300 import Hologram
     ps = _problems(50)
-    b = _batch(ps)
+    b = _batch(ps, variant)
     ph, w, T = _state(ps)
     b.wgs(ph, w, T, 1)
     for k, p in enumerate(ps):
         h = Hologram(torch.from_numpy(p.amp).cuda(), torch.from_numpy(p.coeff).cuda(), noll=p.noll)
-        h.set_variant(1)   # the batched kernels use the FMA-pipe arithmetic: same forward sums, bit for bit
+        h.set_variant(variant)   # same kernel family: the same sums up to summation order
         ph1 = torch.from_numpy(p.phase0).cuda().clone()
         w1 = torch.from_numpy(p.target).cuda().clone()
         h.wgs(ph1, w1, T[k], 1)
@@ -73,9 +83,10 @@ def test_batch_one_iteration_equals_single_path():
         assert np.linalg.norm(amp * (u - u1)) <= 1e-4 * np.linalg.norm(amp)
 
 
-def test_batch_deterministic_and_grid_independent():
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_batch_deterministic_and_grid_independent(variant):
     ps = _problems(70)
-    b = _batch(ps)
+    b = _batch(ps, variant)
     outs = []
     for grid in (None, None, 7, 1, 3 * b.info()["resident_ctas"]):
         if grid is not None:
@@ -95,19 +106,30 @@ def test_batch_deterministic_and_grid_independent():
             assert float(d.abs().norm() / amp.norm()) <= 1e-3
 
 
-def test_batch_autotuner_picks_and_caches(tmp_path):
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_batch_autotuner_picks_and_caches(tmp_path, variant):
     ps = _problems(90)
-    b = _batch(ps)
+    b = _batch(ps, variant)
     ph, _, _ = _state(ps)
     cache = str(tmp_path / "tune.txt")
     g = b.tune(ph, cache)
     assert g >= 1 and os.path.exists(cache)
     lines = open(cache).read().split("\n")
     assert any(line.endswith(f" {g}") for line in lines)
-    b2 = _batch(ps)
+    b2 = _batch(ps, variant)
     assert b2.tune(ph, cache) == g            # read from the cache
     assert b2.info()["grid"] == g
-    assert b.launches(5) in (5 * 4 + 3, 5 * 5 + 3)
+    if variant == 1:   # forward + reduction, update, adjoint (+ fix-up); final forward, metrics
+        assert b.launches(5) in (5 * 4 + 3, 5 * 5 + 3)
+    else:              # nearfield images and forward (+ reduction) once, then update, adjoint (+ fix-up), forward (+ reduction)
+        assert b.launches(5) in [2 + f + 5 * (1 + a + f) for f in (1, 2) for a in (1, 2)]
+
+
+def test_batch_automatic_family_is_tensor_core():
+    b = _batch(_problems(110))
+    info = b.info()
+    b.set_variant(2)
+    assert b.info()["resident_ctas"] == info["resident_ctas"]
 
 
 def test_batch_rejects_large_D():
