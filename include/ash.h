@@ -243,7 +243,11 @@ ash_status ash_wgs_iterate(ash_hologram *h, float *phase, float *w, const float 
  * i dL/dIm(E) for E = forward(phase):
  *   dphase_m = -Im(f_m conj(h_m)),  h = K^H grad_E      (adjoint pass)
  *   dcoeff_nd = Im(conj(grad_E_n) S_nd), S_nd = sum_m Z_dm f_m K_nm
- *               (forward pass with D moments, tiles recomputed).
+ *               (forward pass with D moments, tiles recomputed; the phases
+ *               C_n . Z_m come from the tensor cores when the operand row
+ *               fits one K-atom and D <= 12, else from the FMA pipe).
+ * The tensor-core moment pass overwrites the handle's nearfield image (no
+ * other state of the handle changes).
  *   phase   device float[ny*nx];  grad_E device float[2*N];
  *   dphase  device float[ny*nx] or NULL;  dcoeff device float[N*D] or NULL.
  */
@@ -255,17 +259,21 @@ ash_status ash_grad(ash_hologram *h, const float *phase, const float *grad_E, fl
  *   {CTAs of the FMA-pipe transform launches, their resident CTAs per SM
  *    (forward), (adjoint), CTAs of the tensor-core adjoint (0 if not
  *    available), its resident CTAs per SM, split flags (bit 0: FMA schedule
- *    splits tiles, bit 1: tensor-core schedule splits sub-tiles), kernels in
- *    use (adjoint: 1 FMA or 2 tensor core, plus 4 if the forward uses the
- *    tensor core), pixels per thread}.
+ *    splits tiles, bit 1: tensor-core schedule splits sub-tiles, bit 2:
+ *    the tensor-core forward splits spot blocks), kernels in use (adjoint:
+ *    1 FMA or 2 tensor core, plus 4 if the forward and 8 if the
+ *    coefficient-gradient moments use the tensor core), pixels per thread}.
  */
 ash_status ash_hologram_launch_info(const ash_hologram *h, int *out);
 
 /*
- * Kernel variant of the forward and adjoint transforms: 0 = automatic
- * (the faster measured family per transform: tensor-core forward for
- * D <= 10, FMA-pipe adjoint), 1 = FMA-pipe kernels, 2 = tensor-core kernels
- * (ASH_ERR_UNSUPPORTED if D > 12). Both
+ * Kernel variant of the forward and adjoint transforms and of the
+ * coefficient-gradient moments: 0 = automatic (the faster measured family
+ * per pass: tensor cores when the operand row fits one K-atom, for the
+ * forward and the moments from N = 64 spots, for the adjoint from N = 256),
+ * 1 = FMA-pipe kernels, 2 = tensor-core kernels (ASH_ERR_UNSUPPORTED if
+ * D > 21; the moments stay on the FMA pipe where their tensor-core pass is
+ * not available). Both
  * compute the same sums; the tensor-core variant forms the phases
  * C_n . dZ_m with split-tf32 tcgen05 MMAs into tensor memory. Drops the
  * handle's captured graphs.

@@ -151,6 +151,39 @@ bool use_tc_adj(const ash_hologram* h) {
   if (!h->tc_ok || h->variant == 1) return false;
   return h->variant == 2 || (h->tc_na == 1 && h->g.N >= kTcAdjMinSpots);
 }
+// The coefficient-gradient moments on the tensor cores need one K-atom,
+// D <= 12 and a polynomial basis of degree <= 4 in x (the row polynomials);
+// from N = 64, as the forward whose structure they share.
+bool use_tc_grad(const ash_hologram* h) {
+  if (!h->tgrad_ok || h->variant == 1) return false;
+  return h->variant == 2 || h->g.N >= kTcFwdMinSpots;
+}
+
+TcGradParams tc_grad_params(const ash_hologram* h, const float2* gE, float* dC) {
+  TcGradParams p{};
+  p.g = h->g;
+  p.zs = h->zs;
+  p.czs = h->czs;
+  p.rot = h->rot;
+  p.fimg = h->fimg;
+  p.zrow = h->zrow;
+  p.npow = h->tgrad_npow;
+  p.gE = gE;
+  p.sched = h->tgrad;
+  p.begin = h->tgrad_begin;
+  p.dC = dC;
+  p.part = h->tgrad_part;
+  p.err = h->err_word;
+  return p;
+}
+
+// dC through the tensor-core moment pass: nearfield image of `phase`, then
+// the moments (and the sums of split spot blocks).
+cudaError_t enqueue_tc_gradc(ash_hologram* h, const float* phase, const float2* gE, float* dC, cudaStream_t s) {
+  cudaError_t e = tc_field_img(h->g, h->amp_img, phase, nullptr, h->fimg, s);
+  if (e != cudaSuccess) return e;
+  return tc_launch_gradc(tc_grad_params(h, gE, dC), h->tgrad_split, s);
+}
 
 // Source of a forward: a phase or a complex field in user layout, or the
 // tc-layout nearfield the previous tensor-core adjoint wrote (kEpiFimg).
@@ -432,7 +465,7 @@ ash_status create_impl(ash_hologram** out, int nx, int ny, const float* amp, int
   }
   h->fwd_rows = g.T * (g.NT / 32);
   std::vector<int> tadj_groups;
-  std::vector<long long> tfwd_begin, tadj_begin;
+  std::vector<long long> tfwd_begin, tadj_begin, tgrad_begin;
   if (D <= kTcMaxModes) {
     // tensor-core path: one range of units per resident CTA, at least two
     // MMA chunks per CTA
@@ -467,6 +500,25 @@ ash_status create_impl(ash_hologram** out, int nx, int ny, const float* amp, int
     for (int b = 0; b <= f.G; ++b) tfwd_begin.push_back(f.begin(b));
     for (int b = 1; b < f.G; ++b)
       if (tfwd_begin[b] % f.nq != 0) h->tfwd_split = true;
+    int npow = 2;
+    if (spec)
+      for (const MonoTerm& m : spec->terms) npow = m.px + 1 > npow ? m.px + 1 : npow;
+    if (spec && h->tc_na == 1 && D <= kTcGradMaxModes && npow <= kTcGradMaxPow) {
+      h->tgrad_npow = npow;
+      ce = tc_grad_prepare(npow, D, &h->li.tc_grad_ctas_per_sm);
+      if (ce != cudaSuccess) return fail(cuda_fail(ce, "tensor-core moment pass preparation"));
+      h->tgrad_ok = true;
+      TcFwdSched& m = h->tgrad;
+      m.nb = f.nb;
+      m.nq = f.nq;
+      long long Gm = (long long)sms * h->li.tc_grad_ctas_per_sm;
+      if (Gm > m.units() / 2) Gm = m.units() / 2;
+      if (Gm < 1) Gm = 1;
+      m.G = (int)Gm;
+      for (int b = 0; b <= m.G; ++b) tgrad_begin.push_back(m.begin(b));
+      for (int b = 1; b < m.G; ++b)
+        if (tgrad_begin[b] % m.nq != 0) h->tgrad_split = true;
+    }
   }
   h->gradc_gy = (N + kGradThreads * kGradSpots - 1) / (kGradThreads * kGradSpots);
   {
@@ -495,6 +547,11 @@ ash_status create_impl(ash_hologram** out, int nx, int ny, const float* amp, int
     if ((st = ws(h, &h->tfwd_begin, tfwd_begin.size())) != ASH_OK) return fail(st);
     if ((st = ws(h, &h->tadj_begin, tadj_begin.size())) != ASH_OK) return fail(st);
     if ((st = ws(h, &h->tadj_groups, tadj_groups.size() + 1)) != ASH_OK) return fail(st);
+  }
+  if (h->tgrad_ok) {
+    if ((st = ws(h, &h->zrow, tc_zrow_floats(g, h->tgrad_npow))) != ASH_OK) return fail(st);
+    if ((st = ws(h, &h->tgrad_part, (size_t)h->tgrad.G * 2 * kTcRows * tc_grad_dp(D))) != ASH_OK) return fail(st);
+    if ((st = ws(h, &h->tgrad_begin, tgrad_begin.size())) != ASH_OK) return fail(st);
   }
   if ((st = ws(h, &h->gradc_partial, (size_t)h->gradc_gx * N * D)) != ASH_OK) return fail(st);
   if ((st = ws(h, &h->E, (size_t)N)) != ASH_OK) return fail(st);
@@ -550,6 +607,11 @@ ash_status create_impl(ash_hologram** out, int nx, int ny, const float* amp, int
       CREATE_CUDA(cudaMemcpyAsync(h->tadj_groups, tadj_groups.data(), tadj_groups.size() * sizeof(int),
                                   cudaMemcpyHostToDevice, s));
     CREATE_CUDA(tc_build_zs(g, h->tc_layout, h->dz, h->zs, s));
+    if (h->tgrad_ok) {
+      CREATE_CUDA(cudaMemcpyAsync(h->tgrad_begin, tgrad_begin.data(), tgrad_begin.size() * sizeof(long long),
+                                  cudaMemcpyHostToDevice, s));
+      CREATE_CUDA(tc_build_row_poly(g, h->terms, h->term_off, h->tgrad_npow, h->zrow, s));
+    }
     // pixels outside the grid stay 0 in every nearfield image
     CREATE_CUDA(cudaMemsetAsync(h->fimg, 0, tc_fimg_float4s(g) * sizeof(float4), s));
   }
@@ -724,7 +786,9 @@ ash_status ash_grad(ash_hologram* h, const float* phase, const float* grad_E, fl
     ash_status st = enqueue_adjoint(h, gE, nullptr, nullptr, phase, dphase, kEpiGradPhase, s);
     if (st != ASH_OK) return st;
   }
-  if (dcoeff) {
+  if (dcoeff && use_tc_grad(h)) {
+    ASH_CUDA(enqueue_tc_gradc(h, phase, gE, dcoeff, s));
+  } else if (dcoeff) {
     GradCParams p{};
     p.v = view_of(h);
     p.phase = phase;
@@ -747,7 +811,7 @@ ash_status ash_hologram_launch_info(const ash_hologram* h, int* out) {
   out[3] = h->tc_ok ? h->tadj.G : 0;
   out[4] = h->tc_ok ? h->tfwd.G : 0;
   out[5] = (h->split_tiles ? 1 : 0) | (h->tadj_split ? 2 : 0) | (h->tfwd_split ? 4 : 0);
-  out[6] = (use_tc_adj(h) ? 2 : 1) | (use_tc_fwd(h) ? 4 : 0);
+  out[6] = (use_tc_adj(h) ? 2 : 1) | (use_tc_fwd(h) ? 4 : 0) | (use_tc_grad(h) ? 8 : 0);
   out[7] = h->g.P;
   return ASH_OK;
 }
@@ -856,7 +920,8 @@ ash_status ash_profile(ash_hologram* h, const float* phase, const float* y, floa
     gp.gradE = y2;
     gp.partial = h->gradc_partial;
     cudaEventRecord(ev[10], s);
-    e = launch_gradc(h->g.D, gp, dim3(h->gradc_gx, h->gradc_gy), s);
+    e = use_tc_grad(h) ? tc_launch_gradc(tc_grad_params(h, y2, h->gradc_partial), h->tgrad_split, s)
+                       : launch_gradc(h->g.D, gp, dim3(h->gradc_gx, h->gradc_gy), s);
     cudaEventRecord(ev[11], s);
   }
   if (e != cudaSuccess) st = cuda_fail(e, "profile launch");

@@ -47,6 +47,13 @@ struct ash_hologram {
   long long* tadj_begin = nullptr;   // [tadj.G + 1] CTA range starts of the adjoint
   int* tadj_groups = nullptr;   // groups split between adjoint CTA ranges
   int tadj_nsplit = 0;
+  bool tgrad_ok = false;        // tensor-core moment pass of the coefficient gradient (one K-atom)
+  ash::TcFwdSched tgrad{};      // its units (spot block, pixel chunk)
+  bool tgrad_split = false;     // some spot block's pixels span two CTA ranges
+  long long* tgrad_begin = nullptr;  // [tgrad.G + 1]
+  float* tgrad_part = nullptr;  // [tgrad.G][2][128][DC]
+  int tgrad_npow = 0;           // powers of the basis row polynomials
+  float* zrow = nullptr;        // row polynomials of the basis per chunk
   float2* split = nullptr;
   float* gradc_partial = nullptr;
   float2* E = nullptr;

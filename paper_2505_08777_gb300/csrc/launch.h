@@ -15,6 +15,7 @@ struct LaunchInfo {
   int gradc_ctas_per_sm;
   int tc_adj_ctas_per_sm;   // 0 if the tensor-core path is not available for this D
   int tc_fwd_ctas_per_sm;
+  int tc_grad_ctas_per_sm;   // 0 if the tensor-core moment pass is not available
 };
 
 // Each returns cudaErrorInvalidValue when D is outside its range.

@@ -4,11 +4,9 @@
 
 namespace ash {
 
-namespace {
-
 // Resident CTAs per SM from the kernel's registers, shared memory and TMEM
 // columns (the runtime's occupancy query does not account for TMEM).
-cudaError_t ctas_per_sm(const void* fn, size_t smem, int tmem_cols, int* out) {
+cudaError_t tc_ctas_per_sm(const void* fn, size_t smem, int tmem_cols, int* out) {
   cudaFuncAttributes fa;
   cudaError_t e = cudaFuncGetAttributes(&fa, fn);
   if (e != cudaSuccess) return e;
@@ -27,6 +25,8 @@ cudaError_t ctas_per_sm(const void* fn, size_t smem, int tmem_cols, int* out) {
   *out = n < 1 ? 1 : n;
   return cudaSuccess;
 }
+
+namespace {
 
 template <int NA>
 cudaError_t prepare_na(int* adj, int* fwd) {
@@ -51,8 +51,8 @@ cudaError_t prepare_na(int* adj, int* fwd) {
   if ((e = cudaFuncSetAttribute(kf, cudaFuncAttributePreferredSharedMemoryCarveout,
                                 (int)cudaSharedmemCarveoutMaxShared)))
     return e;
-  if ((e = ctas_per_sm(ka, TcAdjShape<NA>::SMEM, 2 * kTcChunk, adj))) return e;
-  return ctas_per_sm(kf, TcFwdShape<NA>::SMEM, 2 * kTcChunk, fwd);
+  if ((e = tc_ctas_per_sm(ka, TcAdjShape<NA>::SMEM, 2 * kTcChunk, adj))) return e;
+  return tc_ctas_per_sm(kf, TcFwdShape<NA>::SMEM, 2 * kTcChunk, fwd);
 }
 
 unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
@@ -68,12 +68,12 @@ cudaError_t tc_prepare(int NA, int* adj_ctas_per_sm, int* fwd_ctas_per_sm) {
 cudaError_t tc_batch_ctas_per_sm(int NA, int* adj, int* fwd) {
   cudaError_t e;
   if (NA == 1) {
-    if ((e = ctas_per_sm((const void*)k_tc_adjoint_batch<1>, TcAdjShape<1>::SMEM, 2 * kTcChunk, adj))) return e;
-    return ctas_per_sm((const void*)k_tc_forward_batch<1>, TcFwdShape<1>::SMEM, 2 * kTcChunk, fwd);
+    if ((e = tc_ctas_per_sm((const void*)k_tc_adjoint_batch<1>, TcAdjShape<1>::SMEM, 2 * kTcChunk, adj))) return e;
+    return tc_ctas_per_sm((const void*)k_tc_forward_batch<1>, TcFwdShape<1>::SMEM, 2 * kTcChunk, fwd);
   }
   if (NA == 2) {
-    if ((e = ctas_per_sm((const void*)k_tc_adjoint_batch<2>, TcAdjShape<2>::SMEM, 2 * kTcChunk, adj))) return e;
-    return ctas_per_sm((const void*)k_tc_forward_batch<2>, TcFwdShape<2>::SMEM, 2 * kTcChunk, fwd);
+    if ((e = tc_ctas_per_sm((const void*)k_tc_adjoint_batch<2>, TcAdjShape<2>::SMEM, 2 * kTcChunk, adj))) return e;
+    return tc_ctas_per_sm((const void*)k_tc_forward_batch<2>, TcFwdShape<2>::SMEM, 2 * kTcChunk, fwd);
   }
   return cudaErrorInvalidValue;
 }

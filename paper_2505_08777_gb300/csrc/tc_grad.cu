@@ -1,0 +1,365 @@
+// Coefficient gradient on the tensor cores: the spot-stationary moment pass
+// dL/dC_nd = Im(conj(dL/dE_n) sum_m Z_dm f_m exp(-i C_n . Z_m)) (paper
+// Methods, gradients of the spot field), with the phases C_n . dZ_m from the
+// same split-tf32 MMA as the forward transform.
+#include "tc_kernels.cuh"
+
+namespace ash {
+
+namespace {
+
+// --- coefficient-gradient moments -----------------------------------------------
+
+// Row polynomials of the basis: along the 32 pixels of one row of a tile,
+// x = x_c + s u with u = (col - 15.5) / 16, so a basis polynomial
+// sum coef x^a y^b is sum_k a_k u^k, a_k = sum coef y^b binom(a, k) x_c^(a-k)
+// s^k, exact in fp64 and rounded once. One thread per (chunk, row, mode);
+// zrow[chunk][row][k][DP], modes D..DP-1 and powers beyond a term's a are 0.
+__global__ void k_tc_row_poly(const Geometry G, const MonoTerm* __restrict__ terms, const int* __restrict__ term_off,
+                              int npow, int DP, float* __restrict__ zrow) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nq = (long long)G.T * kTcChunksPerTile;
+  if (e >= nq * 2 * DP) return;
+  const int d = (int)(e % DP);
+  const int hr = (int)((e / DP) % 2);
+  const long long qc = e / (2 * DP);
+  const TcPixel px = tc_pixel(G, qc, 32 * hr);   // column 0 of the row
+  const double R = 0.5 * (double)min(G.nx, G.ny);
+  const double cx = 0.5 * (double)(G.nx - 1), cy = 0.5 * (double)(G.ny - 1);
+  const double xc = ((double)px.i + 15.5 - cx) / R, sc = 16.0 / R, y = ((double)px.j - cy) / R;
+  double a[kTcGradMaxPow] = {};
+  if (d < G.D) {
+    for (int k = term_off[d]; k < term_off[d + 1]; ++k) {
+      const MonoTerm m = terms[k];
+      double yb = 1.0;
+      for (int b = 0; b < m.py; ++b) yb *= y;
+      // (x_c + s u)^a = sum_k binom(a, k) x_c^(a - k) s^k u^k
+      double binom = 1.0;
+      for (int kk = 0; kk <= m.px && kk < kTcGradMaxPow; ++kk) {
+        double xp = 1.0, sp = 1.0;
+        for (int r = 0; r < m.px - kk; ++r) xp *= xc;
+        for (int r = 0; r < kk; ++r) sp *= sc;
+        a[kk] += m.coef * yb * binom * xp * sp;
+        binom = binom * (double)(m.px - kk) / (double)(kk + 1);
+      }
+    }
+  }
+  float* dst = zrow + ((size_t)qc * 2 + hr) * npow * DP + d;
+  for (int kk = 0; kk < npow; ++kk) dst[(size_t)kk * DP] = (float)a[kk];
+}
+
+// Shared memory of the moment kernel: A (spot block), B ring, and a ring of
+// [f (64 pixels) | row polynomials (2 rows x NPOW x DP)] slots.
+template <int NPOW, int DP>
+struct TcGradShape {
+  static constexpr int NBB = 4, NF = 4;
+  static constexpr uint32_t A_BYTES = 16384, B_BYTES = 8192, F_BYTES = 512, Z_BYTES = 2 * NPOW * DP * 4;
+  static constexpr uint32_t FSLOT = F_BYTES + Z_BYTES;
+  static constexpr int NBARS = 3 + NBB + NF;
+  static constexpr size_t SMEM = 1024 + A_BYTES + NBB * B_BYTES + NF * FSLOT + NBARS * 12 + 8 + 32;
+};
+
+// S_nd = sum_m Z_dm f_m exp(-i C_n . Z_m) and dL/dC_nd = Im(conj(gE_n) S_nd)
+// (paper Methods, gradients through the kernels). With C_n . Z_m = 2 pi base
+// + x (x the local phase from the tensor core) and w = conj(gE_n exp(+i 2 pi
+// base)), constant over a tile, each term adds q Z_dm with q = Im(w f_m
+// exp(-i x)). Along a row of 32 pixels Z_dm = sum_k a_dk u^k (u the pixel's
+// column offset, a compile-time constant here), so thread t (spot t of the
+// block) accumulates the NPOW power moments sum q u^k of the row and adds
+// sum_k a_dk (moment k) to its D gradients at the row's end.
+template <int NPOW, int DP>
+__global__ void __launch_bounds__(kTcThreads, 3) k_tc_gradc(const TcGradParams p) {
+  using S = TcGradShape<NPOW, DP>;
+  constexpr int NA = 1, NBB = S::NBB, NF = S::NF, NBARS = S::NBARS;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = tc_smem_base(smem_raw);
+  float* sA = reinterpret_cast<float*>(base);
+  float* sB = sA + 4096;
+  uint8_t* sFZ = reinterpret_cast<uint8_t*>(sB + NBB * 2048);     // [NF][f | dz pairs]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sFZ + NF * S::FSLOT);
+  uint64_t* full = bars;
+  uint64_t* bfull = bars + 2;
+  uint64_t* ffull = bars + 2 + NBB;
+  uint64_t* afull = bars + 2 + NBB + NF;
+  uint32_t* armed = reinterpret_cast<uint32_t*>(bars + NBARS);
+  uint32_t* cnt = armed + NBARS;
+  uint32_t* tslot = cnt + 2;
+  int* pst = reinterpret_cast<int*>(tslot + 1);
+  const uint32_t tmem = tc_tmem_alloc(tslot);
+
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  const Geometry& G = p.g;
+  const int N = G.N, D = G.D;
+  const int nq = G.T * kTcChunksPerTile;
+  const long long u0 = p.begin[blockIdx.x], u1 = p.begin[blockIdx.x + 1];
+  const int nc = (int)(u1 - u0);
+  const int b0 = (int)(u0 / nq), q0 = (int)(u0 % nq);
+  tc_range_begin(bars, armed, cnt, NBARS, true);
+  const uint32_t tlane = (uint32_t)(w * 32) << 16;
+  bool ok = true;
+
+  auto load_a = [&](int b) {
+    mbar_expect_tx(afull, S::A_BYTES);
+    ++armed[NBARS - 1];
+    tc_copy_rows128<NA>(sA, p.czs + (size_t)(2 * b) * 2048, afull);
+  };
+  auto load_b = [&](int c, int q) {
+    const int slot = c % NBB;
+    mbar_expect_tx(&bfull[slot], S::B_BYTES);
+    ++armed[2 + slot];
+    bulk_g2s(sB + slot * 2048, p.zs + (size_t)q * 2048, S::B_BYTES, &bfull[slot]);
+  };
+  auto load_f = [&](int c, int q) {
+    const int slot = c % NF;
+    uint8_t* dst = sFZ + slot * S::FSLOT;
+    mbar_expect_tx(&ffull[slot], S::F_BYTES + S::Z_BYTES);
+    ++armed[2 + NBB + slot];
+    bulk_g2s(dst, p.fimg + (size_t)q * 32, S::F_BYTES, &ffull[slot]);
+    bulk_g2s(dst + S::F_BYTES, p.zrow + (size_t)q * 2 * NPOW * DP, S::Z_BYTES, &ffull[slot]);
+  };
+  auto next_q = [&](int q) { return q + 1 == nq ? 0 : q + 1; };
+  auto issue_upto = [&](int upto, int released) -> bool {
+    bool r = true;
+    int k = pst[0], b = pst[1], q = pst[2], ab = pst[3], fresh = pst[4];
+    for (; k <= upto && k < nc;) {
+      if (b != ab) {
+        if (k - 1 > released) break;
+        load_a(b);
+        ab = b;
+        fresh = 1;
+      }
+      r = mbar_wait(&bfull[k % NBB], (uint32_t)((k / NBB) & 1), kTcWaitPolls) && r;
+      if (fresh) {
+        r = mbar_wait(afull, (uint32_t)((b - b0) & 1), kTcWaitPolls) && r;
+        fresh = 0;
+      }
+      tc_fence_after();
+      ++armed[k & 1];
+      tc_mma_chunk<NA>(tmem + (uint32_t)((k & 1) * kTcChunk), sA, sB + (k % NBB) * 2048, &full[k & 1]);
+      ++k;
+      if (++q == nq) {
+        q = 0;
+        ++b;
+      }
+    }
+    pst[0] = k;
+    pst[1] = b;
+    pst[2] = q;
+    pst[3] = ab;
+    pst[4] = fresh;
+    return r;
+  };
+
+  int qb = q0, qf = q0;
+  for (int k = 0; k < NBB; ++k) qb = next_q(qb);
+  for (int k = 0; k < NF - 1; ++k) qf = next_q(qf);
+  if (t == 0 && nc > 0) {
+    pst[0] = 0;
+    pst[1] = b0;
+    pst[2] = q0;
+    pst[3] = b0;
+    pst[4] = 1;
+    load_a(b0);
+    for (int c = 0, q = q0; c < NBB && c < nc; ++c, q = next_q(q)) load_b(c, q);
+    for (int c = 0, q = q0; c < NF - 1 && c < nc; ++c, q = next_q(q)) load_f(c, q);
+    ok = issue_upto(1, -1);
+  }
+
+  float dc[DP];
+#pragma unroll
+  for (int d = 0; d < DP; ++d) dc[d] = 0.0f;
+  float2 gh = make_float2(0.0f, 0.0f), wr2 = gh, wi2 = gh;
+  int b = b0, q = q0;
+
+  for (int c = 0; c < nc; ++c) {
+    const bool wrap = q + 1 == nq;
+    const int n = b * kTcRows + t;
+    const bool active = b * kTcRows + 32 * w < N;
+    if (c == 0 || q == 0) gh = n < N ? __ldg(p.gE + n) : make_float2(0.0f, 0.0f);   // new spot block
+    if (c == 0 || q % kTcChunksPerTile == 0) {
+      // new tile: w = conj(gE exp(+i 2 pi base(n, tile)))
+      const float2 rt = n < N ? __ldg(p.rot + (size_t)(q / kTcChunksPerTile) * N + n) : make_float2(0.0f, 0.0f);
+      const float wr = gh.x * rt.x - gh.y * rt.y, wi = -(gh.x * rt.y + gh.y * rt.x);
+      wr2 = make_float2(wr, wr);
+      wi2 = make_float2(wi, wi);
+    }
+    // row 0 of the chunk is TMEM columns 0-31, row 1 columns 32-63; the
+    // buffer is released once both are in registers
+    const uint32_t taddr = tmem + tlane + (uint32_t)((c & 1) * kTcChunk);
+    const float4* f = reinterpret_cast<const float4*>(sFZ + (c % NF) * S::FSLOT);
+    const float4* a4 = reinterpret_cast<const float4*>(sFZ + (c % NF) * S::FSLOT + S::F_BYTES);
+    auto row = [&](const uint32_t (&x)[2][16], int hr) {
+      float P[NPOW];
+#pragma unroll
+      for (int k = 0; k < NPOW; ++k) P[k] = 0.0f;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const float4 fq = f[16 * hr + k];
+        const float2 fr = make_float2(fq.x, fq.y), fi = make_float2(fq.z, fq.w), nfr = make_float2(-fq.x, -fq.y);
+        float2 sn, cs;
+        sincos2(make_float2(__uint_as_float(x[k / 8][2 * (k % 8)]), __uint_as_float(x[k / 8][2 * (k % 8) + 1])), sn,
+                cs);
+        // p = f exp(-i x) = (fr cs + fi sn) + i (fi cs - fr sn); q = Im(w p)
+        const float2 pre = fma2(fr, cs, mul2(fi, sn));
+        const float2 pim = fma2(fi, cs, mul2(nfr, sn));
+        const float2 qv = fma2(wr2, pim, mul2(wi2, pre));
+        // columns 2k, 2k + 1 of the row
+        const float u0 = (2.0f * k - 15.5f) * 0.0625f, u1 = (2.0f * k + 1.0f - 15.5f) * 0.0625f;
+        float p0 = 1.0f, p1 = 1.0f;
+#pragma unroll
+        for (int e = 0; e < NPOW; ++e) {
+          P[e] = fmaf(qv.x, p0, P[e]);
+          P[e] = fmaf(qv.y, p1, P[e]);
+          p0 *= u0;
+          p1 *= u1;
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < NPOW; ++e) {
+#pragma unroll
+        for (int j = 0; j < DP / 4; ++j) {
+          const float4 av = a4[(hr * NPOW + e) * (DP / 4) + j];
+          dc[4 * j] = fmaf(av.x, P[e], dc[4 * j]);
+          dc[4 * j + 1] = fmaf(av.y, P[e], dc[4 * j + 1]);
+          dc[4 * j + 2] = fmaf(av.z, P[e], dc[4 * j + 2]);
+          dc[4 * j + 3] = fmaf(av.w, P[e], dc[4 * j + 3]);
+        }
+      }
+    };
+    uint32_t x[2][16];
+    ok = ok && mbar_wait(&full[c & 1], (uint32_t)((c >> 1) & 1), kTcWaitPolls);
+    tc_fence_after();
+    tmem_ld16_nowait(taddr, x[0]);
+    tmem_ld16_nowait(taddr + 16, x[1]);
+    tmem_wait();
+    if (active) {
+      ok = ok && mbar_wait(&ffull[c % NF], (uint32_t)((c / NF) & 1), kTcWaitPolls);
+      row(x, 0);
+    }
+    tmem_ld16_nowait(taddr + 32, x[0]);
+    tmem_ld16_nowait(taddr + 48, x[1]);
+    tmem_wait();
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0 && (atom_add_acq_rel_smem(&cnt[c & 1], 1u) & 3u) == 3u) {
+      // every warp is done with TMEM buffer c & 1 and with the ring slot of
+      // chunk c - 1; MMA(c) has completed
+      tc_fence_after();
+      if (c + NBB < nc) load_b(c + NBB, qb);
+      if (c + NF - 1 < nc) load_f(c + NF - 1, qf);
+      ok = issue_upto(c + 2, c) && ok;
+    }
+    __syncwarp();
+    qb = next_q(qb);
+    qf = next_q(qf);
+    if (active) row(x, 1);
+    if (wrap || c == nc - 1) {
+      // end of spot block b in this range
+      const bool whole = (long long)b * nq >= u0 && (long long)(b + 1) * nq <= u1;
+#pragma unroll
+      for (int d = 0; d < DP; ++d) {
+        if (whole) {
+          if (n < N && d < D) p.dC[(size_t)n * D + d] = dc[d];
+        } else {
+          p.part[(((size_t)blockIdx.x * 2 + (b == b0 ? 0 : 1)) * kTcRows + t) * DP + d] = dc[d];
+        }
+        dc[d] = 0.0f;
+      }
+    }
+    if (wrap) {
+      q = 0;
+      ++b;
+    } else {
+      ++q;
+    }
+  }
+  tc_range_end(bars, armed, NBARS);
+  if (!ok && t == 0) atomicOr(p.err, kErrTimeout);
+  tc_tmem_free(tmem);
+}
+
+// Spot blocks of k_tc_gradc split between CTAs: dC_nd is the sum of the
+// partial sums. CTA (b, spot group of 32, mode d): as k_tc_forward_reduce.
+__global__ void k_tc_gradc_reduce(const TcGradParams p) {
+  __shared__ float acc[32][33];
+  const int nq = p.g.T * kTcChunksPerTile, DP = tc_grad_dp(p.g.D);
+  const long long b = blockIdx.x, ulo = b * nq, uhi = ulo + nq - 1;
+  const int col = blockIdx.y * 32 + threadIdx.x, d = blockIdx.z, k = threadIdx.y;
+  const int g_lo = tc_owner(p.begin, p.sched.G, ulo), g_hi = tc_owner(p.begin, p.sched.G, uhi);
+  if (g_lo == g_hi) return;
+  float v = 0.0f;
+  for (int cb = g_lo + k; cb <= g_hi; cb += 32) {
+    const long long beg = p.begin[cb];
+    if (p.begin[cb + 1] <= beg) continue;
+    v += p.part[(((size_t)cb * 2 + (beg >= ulo ? 0 : 1)) * kTcRows + col) * DP + d];
+  }
+  acc[k][threadIdx.x] = v;
+  __syncthreads();
+  for (int h = 16; h > 0; h >>= 1) {
+    if (k < h) acc[k][threadIdx.x] += acc[k + h][threadIdx.x];
+    __syncthreads();
+  }
+  const int n = (int)(b * kTcRows) + col;
+  if (k == 0 && n < p.g.N) p.dC[(size_t)n * p.g.D + d] = acc[0][threadIdx.x];
+}
+
+}  // namespace
+
+template <int NPOW, int DP>
+static cudaError_t launch_np(const TcGradParams& p, cudaStream_t s) {
+  k_tc_gradc<NPOW, DP><<<p.sched.G, kTcThreads, TcGradShape<NPOW, DP>::SMEM, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <int NPOW, int DP>
+static cudaError_t prepare_np(int* n) {
+  const void* k = (const void*)k_tc_gradc<NPOW, DP>;
+  constexpr int smem = (int)TcGradShape<NPOW, DP>::SMEM;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
+  if ((e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared)))
+    return e;
+  return tc_ctas_per_sm(k, smem, 2 * kTcChunk, n);
+}
+
+// Instantiations: NPOW in 2..5, DP in {4, 8, 12}.
+template <int NPOW>
+static cudaError_t dispatch_dp(int DP, bool prep, const TcGradParams* p, int* n, cudaStream_t s) {
+  switch (DP) {
+    case 4: return prep ? prepare_np<NPOW, 4>(n) : launch_np<NPOW, 4>(*p, s);
+    case 8: return prep ? prepare_np<NPOW, 8>(n) : launch_np<NPOW, 8>(*p, s);
+    case 12: return prep ? prepare_np<NPOW, 12>(n) : launch_np<NPOW, 12>(*p, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+static cudaError_t dispatch(int npow, int DP, bool prep, const TcGradParams* p, int* n, cudaStream_t s) {
+  switch (npow) {
+    case 2: return dispatch_dp<2>(DP, prep, p, n, s);
+    case 3: return dispatch_dp<3>(DP, prep, p, n, s);
+    case 4: return dispatch_dp<4>(DP, prep, p, n, s);
+    case 5: return dispatch_dp<5>(DP, prep, p, n, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t tc_grad_prepare(int npow, int D, int* ctas_per_sm) {
+  return dispatch(npow, tc_grad_dp(D), true, nullptr, ctas_per_sm, nullptr);
+}
+
+cudaError_t tc_build_row_poly(const Geometry& g, const MonoTerm* terms, const int* term_off, int npow, float* zrow,
+                              cudaStream_t s) {
+  const int DP = tc_grad_dp(g.D);
+  const long long n = (long long)g.T * kTcChunksPerTile * 2 * DP;
+  k_tc_row_poly<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, terms, term_off, npow, DP, zrow);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_launch_gradc(const TcGradParams& p, bool split, cudaStream_t s) {
+  cudaError_t e = dispatch(p.npow, tc_grad_dp(p.g.D), false, &p, nullptr, s);
+  if (e != cudaSuccess || !split) return e;
+  k_tc_gradc_reduce<<<dim3(p.sched.nb, kTcRows / 32, p.g.D), dim3(32, 32), 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace ash

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "mono.h"
 
 namespace ash {
 
@@ -198,6 +199,37 @@ struct TcFwdParams {
   float2* part;           // [G][2][128] partial sums of spot blocks split between CTAs
   unsigned* err;
 };
+
+// Coefficient-gradient moments on the tensor cores (one K-atom, D <= 12,
+// polynomial basis of degree <= 4 in x): spot-stationary like the forward.
+// zrow holds, per 64-pixel chunk, the row polynomials of its two rows:
+// [2 rows][NPOW powers][DP modes] floats, DP = D rounded up to 4.
+constexpr int kTcGradMaxModes = 12, kTcGradMaxPow = 5;
+__host__ __device__ constexpr int tc_grad_dp(int D) { return (D + 3) & ~3; }
+inline size_t tc_zrow_floats(const Geometry& g, int npow) {
+  return (size_t)g.T * kTcChunksPerTile * 2 * npow * tc_grad_dp(g.D);
+}
+struct TcGradParams {
+  Geometry g;
+  const float* zs;
+  const float* czs;
+  const float2* rot;
+  const float4* fimg;
+  const float* zrow;
+  const float2* gE;       // [N] dL/dE
+  TcFwdSched sched;       // units (spot block, pixel chunk), as the forward
+  const long long* begin; // [G + 1]
+  int npow;               // powers of the row polynomials (2..5)
+  float* dC;              // [N][D] output
+  float* part;            // [G][2][128][DP] partial sums of spot blocks split between CTAs
+  unsigned* err;
+};
+cudaError_t tc_grad_prepare(int npow, int D, int* ctas_per_sm);
+cudaError_t tc_build_row_poly(const Geometry& g, const MonoTerm* terms, const int* term_off, int npow, float* zrow,
+                              cudaStream_t s);
+cudaError_t tc_launch_gradc(const TcGradParams& p, bool split, cudaStream_t s);   // kernel (+ reduction of split blocks)
+// Resident CTAs per SM from registers, shared memory and TMEM columns.
+cudaError_t tc_ctas_per_sm(const void* fn, size_t smem, int tmem_cols, int* out);
 
 // Kernel set-up for operand rows of NA K-atoms: shared-memory limits, and
 // resident CTAs per SM from registers, shared memory and TMEM columns.

@@ -98,8 +98,27 @@ def test_wgs_resume_is_bitwise():
 @pytest.mark.parametrize("nx,ny,N,noll", [(72, 56, 40, list(range(2, 12))), (130, 97, 600, list(range(2, 13))),
                                           (64, 64, 9, [2, 3, 4, 5, 6])])
 def test_grad_matches_oracle(nx, ny, N, noll):
+    _check_grad(nx, ny, N, noll)
+
+
+# Both kernel families of the coefficient-gradient moments: odd and even D
+# (the tensor-core pass packs modes in pairs), the tilt-exact operand layout
+# (D = 11 with Noll 2, 3), a partial last block of 128 spots, spot blocks
+# split between CTAs (many units) and tiny ranges (2 units per CTA).
+@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("nx,ny,N,noll", [(96, 80, 200, list(range(2, 12))), (130, 97, 600, list(range(2, 13))),
+                                          (32, 32, 64, [4, 5, 6, 7]), (100, 70, 130, [2, 3, 4, 5, 6]),
+                                          (200, 150, 1000, [4, 5])])
+def test_grad_coeff_both_families(nx, ny, N, noll, variant):
+    tc = _check_grad(nx, ny, N, noll, variant=variant)
+    assert tc == (variant == 2)
+
+
+def _check_grad(nx, ny, N, noll, variant=0):
     p = random_problem(nx + N, nx, ny, N, noll, defocus_max=5.0, target_range=(0.5, 1.5))
     h = _holo(p)
+    if variant:
+        h.set_variant(variant)
     Z, C, A = oracle_inputs(p)
     phase = p.phase0.astype(np.float64).ravel()
     E = transform.forward(transform.field(A, phase), C, Z)
@@ -111,3 +130,4 @@ def test_grad_matches_oracle(nx, ny, N, noll):
     r1 = np.linalg.norm(dph - dph_ref) / np.linalg.norm(dph_ref)
     r2 = np.linalg.norm(dC - dC_ref) / np.linalg.norm(dC_ref)
     assert r1 <= GRAD_TOL and r2 <= GRAD_TOL, (r1, r2)
+    return bool(h.launch_info()["adjoint_variant"] & 8)
