@@ -68,7 +68,7 @@ struct TcGradShape {
 // block) accumulates the NPOW power moments sum q u^k of the row and adds
 // sum_k a_dk (moment k) to its D gradients at the row's end.
 template <int NPOW, int DP>
-__global__ void __launch_bounds__(kTcThreads, 3) k_tc_gradc(const TcGradParams p) {
+__global__ void __launch_bounds__(kTcThreads, 4) k_tc_gradc(const TcGradParams p) {
   using S = TcGradShape<NPOW, DP>;
   constexpr int NA = 1, NBB = S::NBB, NF = S::NF, NBARS = S::NBARS;
   extern __shared__ uint8_t smem_raw[];
