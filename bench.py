@@ -33,11 +33,28 @@ UNIT = "Gterm/s"
 L2_FLUSH_BYTES = 256 << 20
 MUFU_PER_CLK_PER_SM = 16          # measured: sin.approx / cos.approx throughput per SM per clock
 MUFU_PER_TERM = 2                 # one sin and one cos per term
+FP32_PER_CLK_PER_SM = 128         # FP32 lanes per SM (an FFMA2 occupies two lane-slots)
+# FP32 lane-operations per term: on the MUFU path the argument scaling (1)
+# and the complex multiply-accumulate (4); on the FP32 path the sin / cos
+# polynomial with its reduction (16) and the same multiply-accumulate (4)
+FP32_PER_TERM_MUFU_PATH = 5
+FP32_PER_TERM_POLY_PATH = 20
 MAX_SM_MHZ = 2070.0
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
 # ncu capture of the named kernel on this workload; see profiles/. Reported as
 # roofline.traffic only for the kernel build these counters were taken on.
-NCU_TRAFFIC_BYTES = {"k_tc_forward<1>": 146.449408e6 + 3.635200e6, "k_tc_adjoint<1>": 151.372544e6 + 7.582208e6}
+NCU_TRAFFIC_BYTES = {"k_tc_forward<1>": 146.574592e6 + 3.318272e6, "k_tc_adjoint<1>": 151.150080e6 + 8.044544e6}
+
+
+def alu_terms_per_clk_per_sm():
+    """Two-pipe ceiling of a term (sin, cos, complex MAC): a share a of the
+    terms takes its sin / cos on the FP32 pipe, the rest on the MUFU pipe;
+    the best a equalises the two pipes' times,
+    MUFU_PER_TERM (1 - a) / MUFU rate = (f_m (1 - a) + f_p a) / FP32 rate."""
+    m, F = MUFU_PER_TERM / MUFU_PER_CLK_PER_SM, 1.0 / FP32_PER_CLK_PER_SM
+    fm, fp = FP32_PER_TERM_MUFU_PATH, FP32_PER_TERM_POLY_PATH
+    a = (m - F * fm) / (m + F * (fp - fm))
+    return 1.0 / (m * (1.0 - a))
 
 
 WORKLOAD_TEXT = {
@@ -308,7 +325,8 @@ def main():
 
     clk = clocks.summary()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = sms * (MUFU_PER_CLK_PER_SM / MUFU_PER_TERM) * MAX_SM_MHZ * 1e6 / 1e9
+    peak = sms * alu_terms_per_clk_per_sm() * MAX_SM_MHZ * 1e6 / 1e9
+    mufu_peak = sms * (MUFU_PER_CLK_PER_SM / MUFU_PER_TERM) * MAX_SM_MHZ * 1e6 / 1e9
     dom = "forward" if kms["forward"] >= kms["adjoint"] else "adjoint"
     P = 8 if p.D <= 12 else 4
     linfo = h.launch_info()
@@ -327,8 +345,11 @@ def main():
     roofline = {
         "bound": "alu", "kernel": kernel_names[dom],
         "achieved": achieved, "peak": peak, "unit": "Gterm/s", "frac": achieved / peak,
-        "peak_basis": f"MUFU pipe: {MUFU_PER_CLK_PER_SM} sin/cos per clk per SM (measured), 2 per term, "
-                      f"{sms} SMs x {MAX_SM_MHZ:.0f} MHz max clock",
+        "peak_basis": f"two-pipe ALU ceiling: {MUFU_PER_CLK_PER_SM} sin/cos per clk per SM (MUFU, measured) and "
+                      f"{FP32_PER_CLK_PER_SM} FP32 lanes per SM; a term costs 2 MUFU + {FP32_PER_TERM_MUFU_PATH} FP32 "
+                      f"or {FP32_PER_TERM_POLY_PATH} FP32 (polynomial sin/cos), best split "
+                      f"{alu_terms_per_clk_per_sm():.2f} terms/clk/SM; {sms} SMs x {MAX_SM_MHZ:.0f} MHz max clock",
+        "mufu_only_peak": mufu_peak,
         "algorithmic_per_launch": f"N*M = {NM} terms",
         "traffic": NCU_TRAFFIC_BYTES.get(kernel_names[dom].split(" ")[0]) if args.config == "c2" else None,
         "frac_at_sampled_clock": (achieved / (peak * clk["sm_mhz"] / MAX_SM_MHZ)) if clk.get("sm_mhz") else None,
@@ -365,7 +386,7 @@ def main():
 
 def _peak_gterm(torch, dev):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    return sms * (MUFU_PER_CLK_PER_SM / MUFU_PER_TERM) * MAX_SM_MHZ * 1e6 / 1e9
+    return sms * alu_terms_per_clk_per_sm() * MAX_SM_MHZ * 1e6 / 1e9
 
 
 def bench_autograd(args):

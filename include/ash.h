@@ -106,6 +106,15 @@ ash_status ash_set_allocator(ash_alloc_fn alloc, ash_free_fn free_fn, void *ctx)
 ash_status ash_debug_fail_after(int n_calls);
 
 /*
+ * The transforms' two sin / cos evaluations, for accuracy tests: path 0 the
+ * MUFU approximations (sin.approx / cos.approx), path 1 the FP32-pipe
+ * polynomial (half-angle reduction, degree-4 polynomials in r^2). x, s, c
+ * are device float[n] (n >= 0); s_i = sin(x_i), c_i = cos(x_i). Enqueued on
+ * `stream`; ASH_ERR_INVALID_ARG for a NULL pointer, n < 0 or another path.
+ */
+ash_status ash_debug_sincos(const float *x, int n, float *s, float *c, int path, void *stream);
+
+/*
  * Create a hologram (paper Sec. II: kernels K_n built from the N x D matrix
  * w_d^(n) and the per-pixel basis, Methods "Computational Scaling").
  *   out     host: receives the handle.

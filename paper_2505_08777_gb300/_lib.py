@@ -25,6 +25,7 @@ SIGNATURES = {
     "ash_last_error": (ctypes.c_char_p, []),
     "ash_set_allocator": (c_int, [ALLOC_FN, FREE_FN, c_void_p]),
     "ash_debug_fail_after": (c_int, [c_int]),
+    "ash_debug_sincos": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int, c_void_p]),
     "ash_hologram_create": (c_int, [ctypes.POINTER(c_void_p), c_int, c_int, c_void_p, c_int, c_int_p, c_void_p,
                                     c_int, c_void_p, c_void_p]),
     "ash_hologram_create_mixed": (c_int, [ctypes.POINTER(c_void_p), c_int, c_int, c_void_p, c_int, c_int_p, c_int,

@@ -335,6 +335,26 @@ bool bad_ptr(const void* p) { return p == nullptr; }
 
 }  // namespace
 
+// Two pixels per thread, as in the transforms' pair loops.
+static __global__ void k_debug_sincos(const float* __restrict__ x, int n, float* __restrict__ s, float* __restrict__ c,
+                               int path) {
+  const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (i >= n) return;
+  const float2 v = make_float2(x[i], i + 1 < n ? x[i + 1] : 0.0f);
+  float2 sn, cs;
+  if (path == 1) {
+    sincos2_poly(v, sn, cs);
+  } else {
+    sincos2(v, sn, cs);
+  }
+  s[i] = sn.x;
+  c[i] = cs.x;
+  if (i + 1 < n) {
+    s[i + 1] = sn.y;
+    c[i + 1] = cs.y;
+  }
+}
+
 extern "C" {
 
 int ash_abi_version(void) { return ASH_ABI_VERSION; }
@@ -362,6 +382,14 @@ ash_status ash_set_allocator(ash_alloc_fn alloc, ash_free_fn free_fn, void* ctx)
   g_alloc = alloc;
   g_free = free_fn;
   g_alloc_ctx = ctx;
+  return ASH_OK;
+}
+
+ash_status ash_debug_sincos(const float* x, int n, float* s, float* c, int path, void* stream) {
+  if (!x || !s || !c || n < 0 || path < 0 || path > 1) return set_error(ASH_ERR_INVALID_ARG, "invalid argument");
+  if (n == 0) return ASH_OK;
+  k_debug_sincos<<<(n + 255) / 256, 256, 0, as_stream(stream)>>>(x, n, s, c, path);
+  ASH_CUDA(cudaGetLastError());
   return ASH_OK;
 }
 

@@ -134,11 +134,71 @@ __host__ __device__ inline void tile_anchor(const Geometry& g, int tile, int& ia
 
 // sin and cos of two local phases on the MUFU pipe (the phases are kept
 // small by the tile anchoring, where sin.approx / cos.approx are accurate).
+// Polynomial coefficients of sincos2_poly (gen_sincos_poly.py, degree 4 / 4).
+__device__ constexpr float kSinPoly[5] = {4.442883015e+00f, -7.308241367e+00f, 3.606288671e+00f, -8.457621932e-01f, 1.092032865e-01f};
+__device__ constexpr float kCosPoly[5] = {1.414213538e+00f, -6.978850842e+00f, 5.739460468e+00f, -1.883557916e+00f, 3.106880188e-01f};
+
 __device__ __forceinline__ void sincos2(float2 x, float2& s, float2& c) {
   s.x = __sinf(x.x);
   c.x = __cosf(x.x);
   s.y = __sinf(x.y);
   c.y = __cosf(x.y);
+}
+
+// sin and cos of two arguments on the FP32 pipe (packed FFMA2), to share the
+// transforms' sincos load between the MUFU and the FP32 pipes. Reduction to
+// the half angle: t = x / (2 pi), r = t - rint(t) in [-1/2, 1/2] (rint by
+// adding and subtracting 1.5 * 2^23, exact for |t| < 2^22), u = r^2; S(u) ~
+// sqrt(2) sin(pi r) / r and C(u) ~ sqrt(2) cos(pi r) are polynomials of
+// degree 4 in u, so sin x = 2 sin(pi r) cos(pi r) = (r S) C and
+// cos x = 2 cos^2(pi r) - 1 = C^2 - 1. Coefficients: a weighted
+// least-squares fit on Chebyshev nodes, written by gen_sincos_poly.py;
+// absolute error below 5e-7 on both (that script's float32 bound; the GPU
+// test checks the device function against float64).
+__device__ __forceinline__ void sincos2_poly(float2 x, float2& s, float2& c) {
+  const float2 one = make_float2(1.0f, 1.0f), mone = make_float2(-1.0f, -1.0f);
+  const float2 magic = make_float2(12582912.0f, 12582912.0f), nmagic = make_float2(-12582912.0f, -12582912.0f);
+  const float2 t = mul2(x, make_float2(0.159154943091895336f, 0.159154943091895336f));
+  const float2 k = fma2(fma2(t, one, magic), one, nmagic);   // rint(t)
+  const float2 r = fma2(k, mone, t);
+  const float2 u = mul2(r, r);
+  float2 S = fma2(u, make_float2(kSinPoly[4], kSinPoly[4]), make_float2(kSinPoly[3], kSinPoly[3]));
+  S = fma2(S, u, make_float2(kSinPoly[2], kSinPoly[2]));
+  S = fma2(S, u, make_float2(kSinPoly[1], kSinPoly[1]));
+  S = fma2(S, u, make_float2(kSinPoly[0], kSinPoly[0]));
+  float2 C = fma2(u, make_float2(kCosPoly[4], kCosPoly[4]), make_float2(kCosPoly[3], kCosPoly[3]));
+  C = fma2(C, u, make_float2(kCosPoly[2], kCosPoly[2]));
+  C = fma2(C, u, make_float2(kCosPoly[1], kCosPoly[1]));
+  C = fma2(C, u, make_float2(kCosPoly[0], kCosPoly[0]));
+  s = mul2(mul2(r, S), C);
+  c = fma2(C, C, mone);
+}
+
+// Which pixel pairs of an unrolled loop take the FP32-pipe sincos: NUM of
+// every 9, spread evenly. Per pair the MUFU path costs 32 MUFU-pipe cycles
+// per warp (4 sin/cos at 16 per clk per SM) and ~10 FP32-pipe cycles, the
+// FP32 path ~40 FP32-pipe cycles; the measured best share is lower than the
+// pipe balance (the polynomial's dependent chains add latency) and depends
+// on the kernel's own FP32 work: ASH_POLY_FWD / _ADJ / _GRAD of 9. Measured
+// on GB300 (1024^2, D = 10): 2 / 9 in the tensor-core forward and adjoint
+// (5-9 % faster than 0 / 9; 3 / 9 and 4 / 9 gain less, 5 / 9 is slower),
+// 0 / 9 in the moment pass (its FP32 pipe also carries the moments).
+#ifndef ASH_POLY_FWD
+#define ASH_POLY_FWD 2
+#endif
+#ifndef ASH_POLY_ADJ
+#define ASH_POLY_ADJ 2
+#endif
+#ifndef ASH_POLY_GRAD
+#define ASH_POLY_GRAD 0
+#endif
+template <int NUM>
+__device__ __forceinline__ void sincos2_mixed(int k, float2 x, float2& s, float2& c) {
+  if (NUM > 0 && (k * NUM) % 9 < NUM) {
+    sincos2_poly(x, s, c);
+  } else {
+    sincos2(x, s, c);
+  }
 }
 
 // Balanced static schedule: the T * N (tile, spot) work units, tile-major,

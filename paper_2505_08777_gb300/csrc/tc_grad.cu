@@ -197,8 +197,9 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_tc_gradc(const TcGradParams p
         const float4 fq = f[16 * hr + k];
         const float2 fr = make_float2(fq.x, fq.y), fi = make_float2(fq.z, fq.w), nfr = make_float2(-fq.x, -fq.y);
         float2 sn, cs;
-        sincos2(make_float2(__uint_as_float(x[k / 8][2 * (k % 8)]), __uint_as_float(x[k / 8][2 * (k % 8) + 1])), sn,
-                cs);
+        sincos2_mixed<ASH_POLY_GRAD>(16 * hr + k,
+                      make_float2(__uint_as_float(x[k / 8][2 * (k % 8)]), __uint_as_float(x[k / 8][2 * (k % 8) + 1])),
+                      sn, cs);
         // p = f exp(-i x) = (fr cs + fi sn) + i (fi cs - fr sn); q = Im(w p)
         const float2 pre = fma2(fr, cs, mul2(fi, sn));
         const float2 pim = fma2(fi, cs, mul2(nfr, sn));

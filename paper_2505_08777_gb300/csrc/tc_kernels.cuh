@@ -440,7 +440,8 @@ __device__ __forceinline__ void tc_adjoint_range(const TcAdjParams& p, long long
           const float4 yq = yw[8 * q + pp];
           const float2 yr = make_float2(yq.x, yq.y), yi = make_float2(yq.z, yq.w);
           float2 sn, cs;
-          sincos2(make_float2(__uint_as_float(x[q][2 * pp]), __uint_as_float(x[q][2 * pp + 1])), sn, cs);
+          sincos2_mixed<ASH_POLY_ADJ>(8 * q + pp, make_float2(__uint_as_float(x[q][2 * pp]), __uint_as_float(x[q][2 * pp + 1])),
+                        sn, cs);
           // y exp(+i x) = (yr cs - yi sn) + i (yi cs + yr sn)
           B1 = fma2(yr, cs, B1);
           B2 = fma2(yi, sn, B2);
@@ -691,7 +692,8 @@ __device__ __forceinline__ void tc_forward_range(const TcFwdParams& p, long long
             const float4 fq = f[8 * qq + pp];
             const float2 fr = make_float2(fq.x, fq.y), fi = make_float2(fq.z, fq.w);
             float2 sn, cs;
-            sincos2(make_float2(__uint_as_float(x[qq][2 * pp]), __uint_as_float(x[qq][2 * pp + 1])), sn, cs);
+            sincos2_mixed<ASH_POLY_FWD>(8 * qq + pp,
+                          make_float2(__uint_as_float(x[qq][2 * pp]), __uint_as_float(x[qq][2 * pp + 1])), sn, cs);
             // f exp(-i x) = (fr cs + fi sn) + i (fi cs - fr sn)
             A1 = fma2(fr, cs, A1);
             A2 = fma2(fi, sn, A2);
