@@ -20,9 +20,12 @@ paper's definitions:
               through the transform), closed form and finite differences.
   svd       : principal isoplanatic modes W = U Sigma V^dagger (Methods,
               "Anisoplanatic Singular Value Decomposition").
+  zsub      : simulated Zernike-subtraction calibration (Sec. III,
+              calibration by swept global Zernike orders and per-spot
+              subtraction) on a synthetic system matrix.
 
 Readings where the paper is silent (coordinates, Zernike normalisation,
 transform normalisation, WGS update rule, metrics) are stated in each
 module's docstring.
 """
-from . import zernike, transform, wgs, grad, svd  # noqa: F401
+from . import zernike, transform, wgs, grad, svd, zsub  # noqa: F401

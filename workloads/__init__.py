@@ -205,6 +205,30 @@ def config_c4(seed: int = 1, nx: int = 1024, ny: int = 1024, grid: int = 32) -> 
     return p
 
 
+def config_zsub(seed: int = 1, nx: int = 1024, ny: int = 1024, grid: int = 20) -> Problem:
+    """Simulated Zernike-subtraction calibration: the c2 system (its
+    coefficient matrix is the synthetic optical system's, with the smooth
+    anisoplanatic aberration in Noll 4-11) seen by a model that knows only
+    the spot positions (zsub_model0). Sweep: 7 offsets in [-1.5, 1.5] rad
+    over Noll 4-11, one round, superposition baseline."""
+    p = config_c2(seed, nx, ny, grid)
+    p.name = f"zsub_{nx}x{ny}_N{p.N}_D10"
+    p.iters = 0
+    return p
+
+
+def zsub_model0(p: Problem) -> np.ndarray:
+    """The model's starting coefficients: the system's tilts, no aberration."""
+    C = np.zeros_like(p.coeff)
+    for k, j in enumerate(p.noll):
+        if j in (2, 3):
+            C[:, k] = p.coeff[:, k]
+    return C
+
+
+ZSUB_DELTAS = np.linspace(-1.5, 1.5, 7)
+
+
 C5_SIZES = [(512, 512), (1024, 1024), (1920, 1152)]
 
 
