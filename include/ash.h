@@ -212,6 +212,41 @@ ash_status ash_forward(ash_hologram *h, const float *phase, float *E, void *stre
 ash_status ash_forward_field(ash_hologram *h, const float *field, float *E, void *stream);
 
 /*
+ * Simulated Zernike-subtraction calibration (paper Sec. III: a global
+ * Zernike order is superimposed on the SLM with a swept amplitude, a
+ * per-spot figure of merit gives each site's local contribution, which is
+ * then subtracted spot by spot in aberration space). The handle `h` plays
+ * the optical system (its coefficient matrix is the system's kernels).
+ *
+ * ash_zsub_sweep: for k = 0..K-1,
+ *   intensity[k*N + n] = |E_n|^2,  E = K_h (A exp(i (phase + deltas[k] Z_mode))),
+ * evaluated as the forward of `phase` through the coefficients with column
+ * `mode` shifted by -deltas[k] for every spot (the same sum).
+ *   phase      device float[ny*nx];  deltas  HOST float[K], 1 <= K <= 32;
+ *   mode       column of the coefficient matrix, 0 <= mode < D;
+ *   intensity  device float[K*N].
+ * The handle's coefficients and operand images are restored afterwards (on
+ * the stream), also when a launch fails.
+ */
+ash_status ash_zsub_sweep(ash_hologram *h, const float *phase, int mode, const float *deltas, int K,
+                          float *intensity, void *stream);
+
+/*
+ * Per-spot estimate from a sweep: the least-squares parabola through
+ * (deltas[k], ln max(intensity[k*N + n], 1e-37)) -- a Gaussian peak -- and
+ * its vertex -b / (2 c), clipped to [min deltas, max deltas]; if the fitted
+ * curvature c is not negative, the offset of the largest sample (the first
+ * one on ties). Arithmetic in fp64.
+ *   intensity  device float[K*N];  deltas HOST float[K], 3 <= K <= 32, at
+ *              least three distinct values (else ASH_ERR_INVALID_ARG);
+ *   delta_star device float[N], the estimates;
+ *   coeff      device float[N*D] or NULL: if given, coeff[n*D + mode] +=
+ *              delta_star[n] (the subtraction into the model's matrix).
+ */
+ash_status ash_zsub_estimate(const float *intensity, const float *deltas, int K, int N, float *delta_star,
+                             float *coeff, int D, int mode, void *stream);
+
+/*
  * Adjoint transform (Sec. II, f = F_c^-1{F}, the merge of all N kernels):
  *   g_m = sum_n y_n exp(+i C_n . Z_m).
  *   y          device float[2*N] (complex64).

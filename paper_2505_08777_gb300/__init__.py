@@ -7,7 +7,7 @@ Hologram does, and fails loudly if it is missing.
 """
 from __future__ import annotations
 
-__all__ = ["Hologram", "Batch", "principal_modes", "build", "load_library"]
+__all__ = ["Hologram", "Batch", "principal_modes", "zsub_estimate", "zernike_subtraction", "build", "load_library"]
 
 
 def load_library():
@@ -27,9 +27,9 @@ def __getattr__(name):
     if name == "Batch":
         from .hologram import Batch
         return Batch
-    if name == "principal_modes":
-        from .hologram import principal_modes
-        return principal_modes
+    if name in ("principal_modes", "zsub_estimate", "zernike_subtraction"):
+        from . import hologram
+        return getattr(hologram, name)
     if name == "autograd":
         from . import autograd
         return autograd

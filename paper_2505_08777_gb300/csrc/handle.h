@@ -27,6 +27,7 @@ struct ash_hologram {
   float* amp_img = nullptr;
   float2* anchors = nullptr;
   float* coeff = nullptr;
+  float* coeff_bak = nullptr;   // the coefficients during a calibration sweep
   float* partial = nullptr;
   // tensor-core path (D <= 21): operand images, schedules, split buffers
   int variant = 0;              // 0 auto, 1 FMA-pipe kernels, 2 tensor-core kernels

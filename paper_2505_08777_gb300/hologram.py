@@ -15,7 +15,7 @@ import torch
 
 from . import _lib
 
-__all__ = ["Hologram", "Batch"]
+__all__ = ["Hologram", "Batch", "zsub_estimate", "zernike_subtraction"]
 
 
 def _stream_ptr(stream=None) -> ctypes.c_void_p:
@@ -178,6 +178,19 @@ class Hologram:
                    "ash_grad")
         return dph, dC
 
+    def zsub_sweep(self, phase: torch.Tensor, mode: int, deltas, out: torch.Tensor | None = None,
+                   stream=None) -> torch.Tensor:
+        """Calibration sweep with this hologram as the optical system:
+        I[k, n] = |E_n|^2 for the SLM phase phase + deltas[k] Z_mode (K, N)."""
+        _need(phase, torch.float32, (self.ny, self.nx), "phase")
+        d = [float(v) for v in deltas]
+        I = out if out is not None else torch.empty((len(d), self.N), dtype=torch.float32, device=phase.device)
+        _need(I, torch.float32, (len(d), self.N), "out")
+        dk = (ctypes.c_float * len(d))(*d)
+        _lib.check(self._lib.ash_zsub_sweep(self._h, _ptr(phase), int(mode), dk, len(d), _ptr(I),
+                                            _stream_ptr(stream)), "ash_zsub_sweep")
+        return I
+
     def set_wgs_options(self, feedback: float = 1.0, fix_phase: bool = False):
         """WGS variants for later wgs() calls: weight-update exponent p
         (w <- w (T^/E^)^p) and phase fixing (hold each spot's phase at its value
@@ -308,3 +321,55 @@ def principal_modes(coeff, cols, K: int):
                                  sigma.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     _lib.check(st, "ash_principal_modes")
     return mix, out, sigma
+
+
+def zsub_estimate(intensity: torch.Tensor, deltas, coeff: torch.Tensor | None = None, mode: int = 0,
+                  stream=None) -> torch.Tensor:
+    """Per-spot vertex of the log-parabola through a sweep (K, N); with
+    `coeff` (N, D) the estimates are also added to its column `mode`."""
+    d = [float(v) for v in deltas]
+    K = len(d)
+    if intensity.dim() != 2 or intensity.shape[0] != K:
+        raise ValueError("intensity must have shape (K, N)")
+    N = int(intensity.shape[1])
+    _need(intensity, torch.float32, (K, N), "intensity")
+    D = 0
+    if coeff is not None:
+        D = int(coeff.shape[1]) if coeff.dim() == 2 else 0
+        _need(coeff, torch.float32, (N, D), "coeff")
+    out = torch.empty(N, dtype=torch.float32, device=intensity.device)
+    dk = (ctypes.c_float * K)(*d)
+    lib = _lib.load()
+    _lib.check(lib.ash_zsub_estimate(_ptr(intensity), dk, K, N, _ptr(out), _ptr(coeff), D, int(mode),
+                                     _stream_ptr(stream)), "ash_zsub_estimate")
+    return out
+
+
+def zernike_subtraction(model: Hologram, system: Hologram, target: torch.Tensor, modes, deltas, rounds: int = 1,
+                        wgs_iters: int = 0, shrink: float = 1.0, stream=None):
+    """Simulated Zernike-subtraction calibration (paper Sec. III): for each
+    round and each column d in `modes`, a baseline hologram from the model
+    (superposition arg K^H T, or `wgs_iters` weighted-GS iterations from a
+    zero phase), a sweep of deltas * shrink^round through the system, the
+    per-spot estimates, and their subtraction into the model's column d.
+    Returns the model's final coefficients (N, D) and the estimates of every
+    step [(d, delta_star)]."""
+    _need(target, torch.float32, (model.N,), "target")
+    if (system.nx, system.ny, system.N, system.D) != (model.nx, model.ny, model.N, model.D):
+        raise ValueError("model and system must have the same grid, spots and modes")
+    C = model.coefficients().clone()
+    y = target.to(torch.complex64)
+    steps = []
+    for r in range(rounds):
+        dr = [float(v) * shrink ** r for v in deltas]
+        for d in modes:
+            if wgs_iters > 0:
+                phi = torch.zeros((model.ny, model.nx), dtype=torch.float32, device=target.device)
+                model.wgs(phi, target.clone(), target, wgs_iters, stream=stream)
+            else:
+                _, phi = model.adjoint(y, want_field=False, want_phase=True, stream=stream)
+            I = system.zsub_sweep(phi, d, dr, stream=stream)
+            ds = zsub_estimate(I, dr, C, d, stream=stream)
+            model.set_coefficients(C, stream=stream)
+            steps.append((d, ds))
+    return C, steps
