@@ -82,9 +82,10 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5"],
+    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5", "zsub"],
                     help="c2 (default, the headline): anisoplanatic 2D WGS; c3: 3D volume WGS; "
-                         "c4: autograd + Adam on 8 holograms; c5: 64 uneven holograms, batched vs looped")
+                         "c4: autograd + Adam on 8 holograms; c5: 64 uneven holograms, batched vs looped; "
+                         "zsub: simulated Zernike-subtraction calibration round on the c2 system")
     return ap.parse_args()
 
 
@@ -212,6 +213,8 @@ def main():
         return bench_autograd(args)
     if args.config == "c5":
         return bench_batch(args)
+    if args.config == "zsub":
+        return bench_zsub(args)
     import torch
 
     from paper_2505_08777_gb300 import Hologram
@@ -445,6 +448,98 @@ def bench_autograd(args):
                        "l2": "flushed between steps (256 MiB write)"},
             "adam_steps_per_s": args.steps / (ms * 1e-3),
             "loss_first_step": float(first.item()), "loss_last_step": float(last.item()),
+            "gpu_launches": None, "clocks": clocks.summary()}
+    print(json.dumps(line))
+    return 0
+
+
+def bench_zsub(args):
+    """Simulated Zernike-subtraction calibration (paper Sec. III) on the c2
+    system (1024^2, N = 400, D = 10): one step = one round over Noll 4-11,
+    per order a superposition baseline (one adjoint), a 7-offset sweep (seven
+    forwards through the column-shifted system) and the per-spot estimate and
+    subtraction. Each step starts from the uncalibrated model."""
+    import torch
+
+    from paper_2505_08777_gb300 import Hologram, zernike_subtraction
+    from workloads import ZSUB_DELTAS, config_zsub, zsub_model0
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    p = config_zsub(1)
+    modes = [k for k, j in enumerate(p.noll) if j >= 4]
+    system = Hologram(torch.from_numpy(p.amp).to(dev), torch.from_numpy(p.coeff).to(dev), noll=p.noll)
+    C0 = torch.from_numpy(zsub_model0(p)).to(dev)
+    model = Hologram(torch.from_numpy(p.amp).to(dev), C0.clone(), noll=p.noll)
+    T = torch.from_numpy(p.target).to(dev)
+    stream = torch.cuda.current_stream()
+    mid = len(ZSUB_DELTAS) // 2      # the zero offset
+
+    def step():
+        model.set_coefficients(C0)
+        return zernike_subtraction(model, system, T, modes, ZSUB_DELTAS, rounds=1)
+
+    def brightness(C):
+        model.set_coefficients(C)
+        _, phi = model.adjoint(T.to(torch.complex64), want_field=False, want_phase=True)
+        return float(system.zsub_sweep(phi, modes[0], [0.0]).mean().item())
+
+    b0 = brightness(C0)
+    for _ in range(max(args.warmup, 3)):
+        C1, _ = step()
+    b1 = brightness(C1.clone())
+    torch.cuda.synchronize()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    ms = 0.0
+    with ClockSampler(0) as clocks:
+        for _ in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step()
+            b.record(stream)
+            b.synchronize()
+            ms += a.elapsed_time(b)
+    # end to end through the public API: coefficients and targets from host
+    # memory, the calibrated coefficients back to the host, every step
+    C0_host = torch.from_numpy(zsub_model0(p)).pin_memory()
+    T_host = torch.from_numpy(p.target).pin_memory()
+    C_out = torch.empty_like(C0_host).pin_memory()
+    torch.cuda.synchronize()
+    e2e_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        Cd = C0_host.to(dev, non_blocking=True)
+        Td = T_host.to(dev, non_blocking=True)
+        model.set_coefficients(Cd)
+        Cr, _ = zernike_subtraction(model, system, Td, modes, ZSUB_DELTAS, rounds=1)
+        C_out.copy_(Cr, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        e2e_ms += a.elapsed_time(b)
+    per_order = 1 + len(ZSUB_DELTAS)               # one adjoint + K forwards
+    terms = len(modes) * per_order * p.N * p.nx * p.ny
+    value = terms * args.steps / (ms * 1e-3) / 1e9
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * alu_terms_per_clk_per_sm() * MAX_SM_MHZ * 1e6 / 1e9
+    line = {"metric": "Zernike-subtraction calibration Gterm/s (baseline adjoint + 7-offset sweep per order), "
+                      "rounds/s, workload zsub",
+            "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "c2 system as the optical system: SLM 1024x1024, N=400, D=10 (Noll 2-11); model "
+                                   "starts with the spot tilts only; one round over Noll 4-11, offsets "
+                                   "linspace(-1.5, 1.5, 7) rad, superposition baseline",
+                       "l2": "flushed between steps (256 MiB write)"},
+            "rounds_per_s": args.steps / (ms * 1e-3),
+            "mean_spot_intensity_at_zero_offset": {"before": b0, "after_one_round": b1},
+            "e2e": {"value": terms * args.steps / (e2e_ms * 1e-3) / 1e9, "unit": UNIT,
+                    "h2d_bytes_per_step": C0_host.numel() * 4 + T_host.numel() * 4,
+                    "d2h_bytes_per_step": C_out.numel() * 4},
+            "roofline": {"bound": "alu", "kernel": "whole round (forwards and adjoints, with the small kernels)",
+                         "achieved": value, "peak": peak, "unit": UNIT, "frac": value / peak, "traffic": None},
             "gpu_launches": None, "clocks": clocks.summary()}
     print(json.dumps(line))
     return 0
