@@ -20,6 +20,9 @@ paper's definitions:
               through the transform), closed form and finite differences.
   svd       : principal isoplanatic modes W = U Sigma V^dagger (Methods,
               "Anisoplanatic Singular Value Decomposition").
+  cg        : conjugate-gradient refinement of the SLM phase on that loss
+              (Methods: precision top hats refined by CG through the
+              transform's gradients).
   zsub      : simulated Zernike-subtraction calibration (Sec. III,
               calibration by swept global Zernike orders and per-spot
               subtraction) on a synthetic system matrix.
@@ -28,4 +31,4 @@ Readings where the paper is silent (coordinates, Zernike normalisation,
 transform normalisation, WGS update rule, metrics) are stated in each
 module's docstring.
 """
-from . import zernike, transform, wgs, grad, svd, zsub  # noqa: F401
+from . import zernike, transform, wgs, grad, svd, zsub, cg  # noqa: F401
