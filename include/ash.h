@@ -212,6 +212,26 @@ ash_status ash_forward(ash_hologram *h, const float *phase, float *E, void *stre
 ash_status ash_forward_field(ash_hologram *h, const float *field, float *E, void *stream);
 
 /*
+ * Conjugate-gradient refinement of the SLM phase (paper Methods: precision
+ * targets such as uniform top hats are refined by conjugate-gradient
+ * descent through the transform's gradients). Loss: the spot-intensity
+ * loss L = sum_n (I_n / mean I - t_n)^2, I = |E|^2 (the ash_grad loss).
+ * Nonlinear CG with the Polak-Ribiere+ coefficient (restart to -g when the
+ * direction does not descend) and a one-trial line search: the trial step
+ * changes no pixel's phase by more than `theta`, and the step is the
+ * minimum of the quadratic through L, its slope and the trial loss (twice
+ * the trial step if that quadratic has no minimum). Each iteration runs two
+ * forwards and one gradient adjoint; the loop is one CUDA graph per
+ * iteration count. A call starts a fresh CG sequence (d = -g).
+ *   phase     device float[ny*nx], in/out;  t  device float[N] loss targets;
+ *   iters     0..1024;  theta  in (0, 3.2] rad;
+ *   loss_out  device float[iters+1] or NULL: L before the first and after
+ *             every iteration.
+ */
+ash_status ash_cg_refine(ash_hologram *h, float *phase, const float *t, int iters, float theta,
+                         float *loss_out, void *stream);
+
+/*
  * Simulated Zernike-subtraction calibration (paper Sec. III: a global
  * Zernike order is superimposed on the SLM with a swept amplitude, a
  * per-spot figure of merit gives each site's local contribution, which is

@@ -27,6 +27,7 @@ SIGNATURES = {
     "ash_debug_fail_after": (c_int, [c_int]),
     "ash_debug_sincos": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int, c_void_p]),
     "ash_zsub_sweep": (c_int, [c_void_p, c_void_p, c_int, c_float_p, c_int, c_void_p, c_void_p]),
+    "ash_cg_refine": (c_int, [c_void_p, c_void_p, c_void_p, c_int, ctypes.c_float, c_void_p, c_void_p]),
     "ash_zsub_estimate": (c_int, [c_void_p, c_float_p, c_int, c_int, c_void_p, c_void_p, c_int, c_int, c_void_p]),
     "ash_hologram_create": (c_int, [ctypes.POINTER(c_void_p), c_int, c_int, c_void_p, c_int, c_int_p, c_void_p,
                                     c_int, c_void_p, c_void_p]),

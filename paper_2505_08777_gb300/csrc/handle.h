@@ -67,6 +67,16 @@ struct ash_hologram {
   float wgs_feedback = 1.0f;    // feedback exponent p of the weight update
   bool wgs_fix = false;         // phase fixing: hold the spot phases at wgs_u
   float* wgs_metrics = nullptr;
+  // conjugate-gradient refinement: phase, targets, gradients, direction,
+  // trial phase, fp64 scalars, reduction partials, loss history
+  float* cg_phase = nullptr;
+  float* cg_t = nullptr;
+  float* cg_g = nullptr;        // [2][M]
+  float* cg_d = nullptr;
+  float* cg_trial = nullptr;
+  double* cg_scal = nullptr;
+  double* cg_part = nullptr;
+  float* cg_loss = nullptr;     // [kCgMaxIters + 1]
   double* sum_a2 = nullptr;
   ash::MonoTerm* terms = nullptr;
   int* term_off = nullptr;
@@ -74,7 +84,7 @@ struct ash_hologram {
   std::vector<void*> allocs;
   size_t bytes = 0;
   cudaStream_t capture = nullptr;
-  std::map<int, cudaGraphExec_t> graphs;
+  std::map<int, cudaGraphExec_t> graphs;   // WGS loops by iteration count; CG loops under -iters
 };
 
 namespace ash {

@@ -178,6 +178,18 @@ class Hologram:
                    "ash_grad")
         return dph, dC
 
+    def cg_refine(self, phase: torch.Tensor, t: torch.Tensor, iters: int, theta: float = 0.05,
+                  loss_out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Conjugate-gradient refinement of `phase` (in place) on the spot-intensity
+        loss with targets t; returns the losses (iters + 1,)."""
+        _need(phase, torch.float32, (self.ny, self.nx), "phase")
+        _need(t, torch.float32, (self.N,), "t")
+        L = loss_out if loss_out is not None else torch.empty(iters + 1, dtype=torch.float32, device=phase.device)
+        _need(L, torch.float32, (iters + 1,), "loss_out")
+        _lib.check(self._lib.ash_cg_refine(self._h, _ptr(phase), _ptr(t), int(iters), float(theta), _ptr(L),
+                                           _stream_ptr(stream)), "ash_cg_refine")
+        return L
+
     def zsub_sweep(self, phase: torch.Tensor, mode: int, deltas, out: torch.Tensor | None = None,
                    stream=None) -> torch.Tensor:
         """Calibration sweep with this hologram as the optical system:
