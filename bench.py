@@ -82,10 +82,11 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5", "zsub"],
+    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5", "zsub", "cg"],
                     help="c2 (default, the headline): anisoplanatic 2D WGS; c3: 3D volume WGS; "
                          "c4: autograd + Adam on 8 holograms; c5: 64 uneven holograms, batched vs looped; "
-                         "zsub: simulated Zernike-subtraction calibration round on the c2 system")
+                         "zsub: simulated Zernike-subtraction calibration round on the c2 system; "
+                         "cg: conjugate-gradient top-hat refinement after WGS on c2")
     return ap.parse_args()
 
 
@@ -215,6 +216,8 @@ def main():
         return bench_batch(args)
     if args.config == "zsub":
         return bench_zsub(args)
+    if args.config == "cg":
+        return bench_cg(args)
     import torch
 
     from paper_2505_08777_gb300 import Hologram
@@ -448,6 +451,92 @@ def bench_autograd(args):
                        "l2": "flushed between steps (256 MiB write)"},
             "adam_steps_per_s": args.steps / (ms * 1e-3),
             "loss_first_step": float(first.item()), "loss_last_step": float(last.item()),
+            "gpu_launches": None, "clocks": clocks.summary()}
+    print(json.dumps(line))
+    return 0
+
+
+def bench_cg(args):
+    """Conjugate-gradient top-hat refinement (paper Methods) on the c2
+    workload (1024^2, N = 400, D = 10): from the phase of 50 WGS iterations,
+    one step = 20 CG iterations on the spot-intensity loss with flat targets
+    (two forwards and one gradient adjoint each, one CUDA graph)."""
+    import torch
+
+    from paper_2505_08777_gb300 import Hologram
+    from workloads import config_c2
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    p = config_c2(1)
+    h = Hologram(torch.from_numpy(p.amp).to(dev), torch.from_numpy(p.coeff).to(dev), noll=p.noll)
+    T = torch.from_numpy(p.target).to(dev)
+    ph0 = torch.from_numpy(p.phase0).to(dev)
+    w = T.clone()
+    _, met = h.wgs(ph0, w, T, p.iters)
+    t = (T * T / torch.mean(T * T)).contiguous()
+    iters = 20
+    stream = torch.cuda.current_stream()
+    ph = ph0.clone()
+    L = h.cg_refine(ph, t, iters)
+    E = h.forward(ph)
+    I = (E.abs() ** 2) / (T * T)
+    unif_after = float(1.0 - (I.max() - I.min()) / (I.max() + I.min()))
+    for _ in range(max(args.warmup, 3) - 1):
+        ph.copy_(ph0)
+        h.cg_refine(ph, t, iters)
+    torch.cuda.synchronize()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    ms = 0.0
+    with ClockSampler(0) as clocks:
+        for _ in range(args.steps):
+            ph.copy_(ph0)
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            h.cg_refine(ph, t, iters)
+            b.record(stream)
+            b.synchronize()
+            ms += a.elapsed_time(b)
+    # end to end: the start phase and targets from pinned host memory, the
+    # refined phase and the losses back
+    ph_host = ph0.cpu().pin_memory()
+    t_host = t.cpu().pin_memory()
+    out_host = torch.empty_like(ph_host).pin_memory()
+    L_host = torch.empty(iters + 1, dtype=torch.float32).pin_memory()
+    e2e_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        phd = ph_host.to(dev, non_blocking=True)
+        td = t_host.to(dev, non_blocking=True)
+        Ld = h.cg_refine(phd, td, iters)
+        out_host.copy_(phd, non_blocking=True)
+        L_host.copy_(Ld, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        e2e_ms += a.elapsed_time(b)
+    terms = iters * 3 * p.N * p.nx * p.ny + 2 * p.N * p.nx * p.ny    # 3 transforms per iteration + the start
+    value = terms * args.steps / (ms * 1e-3) / 1e9
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * alu_terms_per_clk_per_sm() * MAX_SM_MHZ * 1e6 / 1e9
+    line = {"metric": "conjugate-gradient refinement Gterm/s (2 forwards + 1 gradient adjoint per iteration), "
+                      "CG iterations/s, workload cg",
+            "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "c2 (SLM 1024x1024, N=400, D=10) after 50 WGS iterations; 20 CG iterations on "
+                                   "L = sum (I/mean I - t)^2, t = T^2/mean T^2 (flat), theta 0.05 rad",
+                       "l2": "flushed between steps (256 MiB write)"},
+            "cg_iterations_per_s": iters * args.steps / (ms * 1e-3),
+            "loss": {"after_wgs": float(L[0].item()), "after_cg": float(L[-1].item())},
+            "uniformity": {"after_wgs": float(met[0].item()), "after_cg": unif_after},
+            "e2e": {"value": terms * args.steps / (e2e_ms * 1e-3) / 1e9, "unit": UNIT,
+                    "h2d_bytes_per_step": ph_host.numel() * 4 + t_host.numel() * 4,
+                    "d2h_bytes_per_step": out_host.numel() * 4 + L_host.numel() * 4},
+            "roofline": {"bound": "alu", "kernel": "whole CG step (transforms with the vector and scalar kernels)",
+                         "achieved": value, "peak": peak, "unit": UNIT, "frac": value / peak, "traffic": None},
             "gpu_launches": None, "clocks": clocks.summary()}
     print(json.dumps(line))
     return 0
