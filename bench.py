@@ -82,6 +82,9 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-solo-terms", type=int, default=None,
+                    help="c5: N*M threshold above which a batch member runs standalone in the batch's graph "
+                         "(default: the library's)")
     ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5", "zsub", "cg"],
                     help="c2 (default, the headline): anisoplanatic 2D WGS; c3: 3D volume WGS; "
                          "c4: autograd + Adam on 8 holograms; c5: 64 uneven holograms, batched vs looped; "
@@ -650,7 +653,7 @@ def bench_batch(args):
     iters = ps[0].iters
     amps = [torch.from_numpy(p.amp).to(dev) for p in ps]
     coeffs = [torch.from_numpy(p.coeff).to(dev) for p in ps]
-    b = Batch([(a, c, p.noll) for a, c, p in zip(amps, coeffs, ps)])
+    b = Batch([(a, c, p.noll) for a, c, p in zip(amps, coeffs, ps)], solo_terms=args.batch_solo_terms)
     hs = [Hologram(a, c, noll=p.noll) for a, c, p in zip(amps, coeffs, ps)]
     ph0 = [torch.from_numpy(p.phase0).to(dev) for p in ps]
     T = [torch.from_numpy(p.target).to(dev) for p in ps]
@@ -702,7 +705,8 @@ def bench_batch(args):
             "config": {"workload": "64 holograms, sizes {512^2, 1024^2, 1920x1152}, N log-uniform [10, 5000], "
                                    "D in {5, 10, 11}, 50 WGS iterations each; one step = the whole batch",
                        "terms_per_step": terms, "l2": "flushed between steps (256 MiB write)",
-                       "tuned_grid": tuned, "resident_ctas": info["resident_ctas"]},
+                       "tuned_grid": tuned, "resident_ctas": info["resident_ctas"],
+                       "standalone_members": info["standalone"]},
             "looped_gterm_s": terms / (ms_l * 1e-3) / 1e9, "looped_ms_per_step": ms_l,
             "batched_speedup_vs_loop": ms_l / ms_b,
             "gpu_launches": b.launches(iters) * args.steps,

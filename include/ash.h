@@ -408,8 +408,24 @@ typedef struct {
 
 /* Create a batch of `count` holograms (descs: host array). Allocates one
  * handle workspace per hologram plus the batch's descriptor table and split
- * scratch; synchronises `stream`. ASH_ERR_UNSUPPORTED if some D > 12. */
+ * scratch; synchronises `stream`. Members with N * nx * ny >= 2^22 terms
+ * run standalone (see ash_batch_create_ex); ASH_ERR_UNSUPPORTED if a member
+ * of the persistent group has D > 12. */
 ash_status ash_batch_create(ash_batch **out, int count, const ash_hologram_desc *descs, void *stream);
+
+/* As ash_batch_create, with the standalone threshold given: a member with
+ * N * nx * ny >= solo_terms runs its own single-hologram WGS loop (the
+ * kernels and launch shapes ash_wgs_iterate would use) inside the batch's
+ * CUDA graph; the others share the persistent launches. solo_terms = 0 makes
+ * every member standalone, a value above every member's N * nx * ny none.
+ * ASH_ERR_INVALID_ARG if solo_terms < 0. The grid, autotuner and resident
+ * CTAs of ash_batch_info / _set_grid / _tune refer to the persistent group
+ * (grid 0 when it is empty). */
+ash_status ash_batch_create_ex(ash_batch **out, int count, const ash_hologram_desc *descs, long long solo_terms,
+                               void *stream);
+
+/* Number of standalone members (-1 for NULL). */
+int ash_batch_standalone(const ash_batch *b);
 
 /* Destroy (synchronises the device first); NULL is ignored. */
 void ash_batch_destroy(ash_batch *b);

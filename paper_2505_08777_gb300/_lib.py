@@ -53,6 +53,8 @@ SIGNATURES = {
     "ash_hologram_launch_info": (c_int, [c_void_p, c_int_p]),
     "ash_profile": (c_int, [c_void_p, c_void_p, c_void_p, c_float_p, c_void_p]),
     "ash_batch_create": (c_int, [ctypes.POINTER(c_void_p), c_int, c_void_p, c_void_p]),
+    "ash_batch_create_ex": (c_int, [ctypes.POINTER(c_void_p), c_int, c_void_p, ctypes.c_longlong, c_void_p]),
+    "ash_batch_standalone": (c_int, [c_void_p]),
     "ash_batch_destroy": (None, [c_void_p]),
     "ash_batch_info": (c_int, [c_void_p, c_int_p, c_int_p, c_int_p, ctypes.POINTER(ctypes.c_longlong)]),
     "ash_batch_set_grid": (c_int, [c_void_p, c_int]),

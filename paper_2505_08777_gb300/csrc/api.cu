@@ -335,6 +335,10 @@ bool bad_ptr(const void* p) { return p == nullptr; }
 
 }  // namespace
 
+namespace ash {
+ash_status wgs_body(ash_hologram* h, int iters, cudaStream_t s) { return enqueue_wgs_body(h, iters, s); }
+}  // namespace ash
+
 // --- conjugate-gradient phase refinement (paper Methods) --------------------
 
 // fp64 scalars of the iteration in h->cg_scal

@@ -35,6 +35,11 @@ constexpr int kBatchP = 8;                 // pixels per thread (D <= 12)
 constexpr int kBatchNT = kTilePix / kBatchP;
 constexpr int kBatchNW = kBatchNT / 32;
 constexpr int kBatchMaxD = 12;
+// Members whose N * M reaches this many terms run standalone inside the
+// batch's graph (their own tuned single-hologram kernels); smaller ones share
+// the persistent launches, where one launch per phase replaces one per
+// hologram.
+constexpr long long kBatchSoloTerms = 1LL << 22;
 constexpr int kGridFactorMax = 4;          // split scratch sized for 4x the resident CTAs
 
 struct BatchHolo {
@@ -233,7 +238,15 @@ BatchKernel adj_kernel(int dmax) {
 }  // namespace
 
 struct ash_batch {
-  int count = 0;
+  // members with N*M >= solo_terms run standalone (their own single-hologram
+  // kernels, in the batch's graph); the others share the persistent batched
+  // launches below, whose fields all refer to that group only
+  int members = 0;
+  std::vector<ash_hologram*> all;    // every member, in the caller's order
+  std::vector<ash_hologram*> solo;   // the standalone members
+  std::vector<int> group_idx;        // member index of each persistent-group hologram
+  long long solo_terms = 0;
+  int count = 0;                     // members in the persistent group
   std::vector<ash_hologram*> holos;
   std::vector<BatchHolo> host;
   BatchHolo* dev = nullptr;
@@ -395,6 +408,7 @@ ash_status build_tc(ash_batch* b) {
 }
 
 ash_status set_grid(ash_batch* b, int G) {
+  if (b->count == 0) return ASH_OK;   // every member is standalone
   const int slots = b->use_tc() ? b->tc_slots : b->slots;
   if (G < 1) G = 1;
   if (G > kGridFactorMax * slots) G = kGridFactorMax * slots;
@@ -506,7 +520,7 @@ void destroy_batch(ash_batch* b) {
                   (void*)b->d_tsplit, (void*)b->d_lists, (void*)b->d_field, (void*)b->d_tiles0})
     if (q) cudaFree(q);
   if (b->capture) cudaStreamDestroy(b->capture);
-  for (ash_hologram* h : b->holos) ash_hologram_destroy(h);
+  for (ash_hologram* h : b->all) ash_hologram_destroy(h);
   delete b;
 }
 
@@ -538,29 +552,46 @@ void cache_store(const char* path, const std::string& key, int G) {
 extern "C" {
 
 ash_status ash_batch_create(ash_batch** out, int count, const ash_hologram_desc* descs, void* stream) {
+  return ash_batch_create_ex(out, count, descs, kBatchSoloTerms, stream);
+}
+
+ash_status ash_batch_create_ex(ash_batch** out, int count, const ash_hologram_desc* descs, long long solo_terms,
+                               void* stream) {
   if (!out) return fail(ASH_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (count < 1 || count > 65535 || !descs) return fail(ASH_ERR_INVALID_ARG, "count outside [1, 65535] or NULL descs");
+  if (solo_terms < 0) return fail(ASH_ERR_INVALID_ARG, "solo_terms < 0");
+  auto is_solo = [&](const ash_hologram_desc& d) { return (long long)d.N * d.nx * d.ny >= solo_terms; };
   for (int i = 0; i < count; ++i)
-    if (descs[i].D < 1 || descs[i].D > kBatchMaxD)
+    if (!is_solo(descs[i]) && (descs[i].D < 1 || descs[i].D > kBatchMaxD))
       return fail(ASH_ERR_UNSUPPORTED, "batched holograms need 1 <= D <= 12 (hologram " + std::to_string(i) + ")");
   if (consume_injected_failure()) return fail(ASH_ERR_INJECTED, "injected failure");
   ash_batch* b = new ash_batch();
-  b->count = count;
+  b->members = count;
+  b->solo_terms = solo_terms;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   auto bail = [&](ash_status st) {
     destroy_batch(b);
     return st;
   };
   int dev = 0, sms = 0;
+  cudaError_t e0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  std::string key = "sm" + std::to_string(sms) + "_n" + std::to_string(count);
+  std::vector<int> grouped;
+  for (int i = 0; i < count; ++i)
+    if (!is_solo(descs[i])) grouped.push_back(i);
+  std::string key = "sm" + std::to_string(sms) + "_n" + std::to_string(grouped.size());
   for (int i = 0; i < count; ++i) {
     const ash_hologram_desc& d = descs[i];
     ash_hologram* h = nullptr;
     ash_status st = ash_hologram_create(&h, d.nx, d.ny, d.amp, d.D, d.noll, d.basis, d.N, d.coeff, stream);
     if (st != ASH_OK) return bail(st);
+    b->all.push_back(h);
+    if (is_solo(d)) {
+      b->solo.push_back(h);
+      continue;
+    }
     b->holos.push_back(h);
     BatchHolo bh{};
     bh.v = view_of(h);
@@ -583,8 +614,17 @@ ash_status ash_batch_create(ash_batch** out, int count, const ash_hologram_desc*
     if (key.size() > 300) key = key.substr(0, 300);
   }
   b->key = key;
+  b->count = (int)grouped.size();
+  b->group_idx = grouped;
+  if ((e0 = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking)) != cudaSuccess)
+    return bail(status_cuda(e0, "batch capture stream"));
+  if (b->count == 0) {   // every member standalone: no persistent group
+    *out = b;
+    return ASH_OK;
+  }
+  count = b->count;
   int dmax = 1;
-  for (int i = 0; i < count; ++i) dmax = descs[i].D > dmax ? descs[i].D : dmax;
+  for (int i : grouped) dmax = descs[i].D > dmax ? descs[i].D : dmax;
   for (int c : kDClasses)
     if (c >= dmax) {
       b->dclass = c;
@@ -617,8 +657,6 @@ ash_status ash_batch_create(ash_batch** out, int count, const ash_hologram_desc*
   if ((e = cudaMemcpyAsync(b->dev, b->host.data(), sizeof(BatchHolo) * count, cudaMemcpyHostToDevice, s)) !=
       cudaSuccess)
     return bail(status_cuda(e, "batch descriptor upload"));
-  if ((e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking)) != cudaSuccess)
-    return bail(status_cuda(e, "batch capture stream"));
   // tensor-core path: every hologram has the operand images, one K-atom count
   b->tc_ok = true;
   for (const ash_hologram* h : b->holos)
@@ -668,7 +706,7 @@ void ash_batch_destroy(ash_batch* b) {
 
 ash_status ash_batch_info(const ash_batch* b, int* count, int* grid, int* resident_ctas, long long* units) {
   if (!b) return fail(ASH_ERR_INVALID_ARG, "batch is NULL");
-  if (count) *count = b->count;
+  if (count) *count = b->members;
   if (grid) *grid = b->G;
   if (resident_ctas) *resident_ctas = b->use_tc() ? b->tc_slots : b->slots;
   if (units) *units = b->U;
@@ -682,8 +720,15 @@ ash_status ash_batch_set_grid(ash_batch* b, int grid) {
 
 ash_status ash_batch_set_variant(ash_batch* b, int variant) {
   if (!b || variant < 0 || variant > 2) return fail(ASH_ERR_INVALID_ARG, "variant must be 0, 1 or 2");
-  if (variant == 2 && !b->tc_ok)
+  if (variant == 2 && b->count > 0 && !b->tc_ok)
     return fail(ASH_ERR_UNSUPPORTED, "tensor-core batch needs every hologram with the same K-atom count (D <= 21)");
+  for (ash_hologram* h : b->solo)
+    if (variant == 2 && !h->tc_ok)
+      return fail(ASH_ERR_UNSUPPORTED, "a standalone member has no tensor-core path (D > 21)");
+  for (ash_hologram* h : b->solo) {
+    const ash_status st = ash_set_kernel_variant(h, variant);
+    if (st != ASH_OK) return st;
+  }
   b->variant = variant;
   for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
   b->graphs.clear();
@@ -691,26 +736,31 @@ ash_status ash_batch_set_variant(ash_batch* b, int variant) {
   return set_grid(b, b->use_tc() ? b->tc_slots : b->slots);
 }
 
+int ash_batch_standalone(const ash_batch* b) { return b ? (int)b->solo.size() : -1; }
+
 int ash_batch_wgs_launches(const ash_batch* b, int iters) {
   if (!b || iters < 0) return -1;
+  int solo = 0;
+  for (const ash_hologram* h : b->solo) solo += ash_wgs_launches(h, iters);
+  if (b->count == 0) return solo;
   if (b->use_tc()) {
     const int fwd = 1 + (b->n_red > 0 ? 1 : 0), adj = 1 + (b->n_fix > 0 ? 1 : 0);
-    return 1 + fwd + iters * (1 + adj + fwd) + 1;   // nearfield images, forward, iterations, metrics
+    return solo + 1 + fwd + iters * (1 + adj + fwd) + 1;   // nearfield images, forward, iterations, metrics
   }
   const int fwd = 2, adj = b->split ? 2 : 1;
-  return iters * (fwd + 1 + adj) + fwd + 1;
+  return solo + iters * (fwd + 1 + adj) + fwd + 1;
 }
 
 ash_status ash_batch_wgs(ash_batch* b, float* const* phases, float* const* weights, const float* const* targets,
                          int iters, float* metrics_out, void* stream) {
   if (!b || !phases || !weights || !targets) return fail(ASH_ERR_INVALID_ARG, "NULL argument");
   if (iters < 0 || iters > 1000000) return fail(ASH_ERR_INVALID_ARG, "iters outside [0, 1e6]");
-  for (int i = 0; i < b->count; ++i)
+  for (int i = 0; i < b->members; ++i)
     if (!phases[i] || !weights[i] || !targets[i]) return fail(ASH_ERR_INVALID_ARG, "NULL per-hologram buffer");
   if (consume_injected_failure()) return fail(ASH_ERR_INJECTED, "injected failure");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  for (int i = 0; i < b->count; ++i) {
-    const ash_hologram* h = b->holos[i];
+  for (int i = 0; i < b->members; ++i) {
+    const ash_hologram* h = b->all[i];
     const size_t M = (size_t)h->g.nx * h->g.ny, N = (size_t)h->g.N;
     BCUDA(cudaMemcpyAsync(h->wgs_phase, phases[i], M * 4, cudaMemcpyDeviceToDevice, s));
     BCUDA(cudaMemcpyAsync(h->wgs_w, weights[i], N * 4, cudaMemcpyDeviceToDevice, s));
@@ -723,7 +773,10 @@ ash_status ash_batch_wgs(ash_batch* b, float* const* phases, float* const* weigh
   } else {
     cudaGraph_t graph = nullptr;
     BCUDA(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal));
-    ash_status st = enqueue_batch_body(b, iters, b->capture);
+    ash_status st = ASH_OK;
+    for (ash_hologram* h : b->solo)
+      if (st == ASH_OK) st = wgs_body(h, iters, b->capture);
+    if (st == ASH_OK && b->count > 0) st = enqueue_batch_body(b, iters, b->capture);
     cudaError_t ce = cudaStreamEndCapture(b->capture, &graph);
     if (st != ASH_OK) {
       if (graph) cudaGraphDestroy(graph);
@@ -736,8 +789,8 @@ ash_status ash_batch_wgs(ash_batch* b, float* const* phases, float* const* weigh
     b->graphs[iters] = exec;
   }
   BCUDA(cudaGraphLaunch(exec, s));
-  for (int i = 0; i < b->count; ++i) {
-    const ash_hologram* h = b->holos[i];
+  for (int i = 0; i < b->members; ++i) {
+    const ash_hologram* h = b->all[i];
     const size_t M = (size_t)h->g.nx * h->g.ny, N = (size_t)h->g.N;
     BCUDA(cudaMemcpyAsync(phases[i], h->wgs_phase, M * 4, cudaMemcpyDeviceToDevice, s));
     BCUDA(cudaMemcpyAsync(weights[i], h->wgs_w, N * 4, cudaMemcpyDeviceToDevice, s));
@@ -760,9 +813,14 @@ ash_status ash_batch_tune(ash_batch* b, const float* const* phases, const char* 
   }
   if (consume_injected_failure()) return fail(ASH_ERR_INJECTED, "injected failure");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (b->count == 0) {   // nothing to tune: every member runs standalone
+    if (grid_out) *grid_out = 0;
+    return ASH_OK;
+  }
   for (int i = 0; i < b->count; ++i) {
     const ash_hologram* h = b->holos[i];
-    BCUDA(cudaMemcpyAsync(h->wgs_phase, phases[i], (size_t)h->g.nx * h->g.ny * 4, cudaMemcpyDeviceToDevice, s));
+    BCUDA(cudaMemcpyAsync(h->wgs_phase, phases[b->group_idx[i]], (size_t)h->g.nx * h->g.ny * 4,
+                          cudaMemcpyDeviceToDevice, s));
     BCUDA(cudaMemsetAsync(h->y, 0, (size_t)h->g.N * sizeof(float2), s));
   }
   if (b->use_tc()) BCUDA(tc_field_img_batch(b->d_field, b->d_tiles0, b->count, b->total_tiles, s));

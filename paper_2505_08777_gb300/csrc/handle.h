@@ -95,6 +95,11 @@ void record_error(const char* msg);
 ash_status status_cuda(cudaError_t e, const char* where);
 // Host-side fault injection counter (ash_debug_fail_after).
 bool consume_injected_failure();
+// The single-hologram WGS loop on the handle's state buffers (wgs_phase,
+// wgs_w, wgs_T; metrics to wgs_metrics), enqueued on `s`: for callers that
+// capture it into a graph of their own (the batched form's standalone
+// members).
+ash_status wgs_body(ash_hologram* h, int iters, cudaStream_t s);
 
 inline HoloView view_of(const ash_hologram* h) {
   HoloView v{};

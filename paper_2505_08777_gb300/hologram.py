@@ -225,11 +225,14 @@ class Hologram:
 
 
 class Batch:
-    """Many holograms solved together (ash_batch_*): one launch per WGS phase
-    over all holograms' (tile, spot) work units, the loop as one CUDA graph."""
+    """Many holograms solved together (ash_batch_*): the loop as one CUDA
+    graph; members with N*M below `solo_terms` share one launch per WGS phase
+    over their (tile, spot) work units, larger ones run their own
+    single-hologram kernels inside the graph."""
 
-    def __init__(self, problems, stream=None):
-        """problems: list of (amp (ny, nx), coeff (N, D), noll list) CUDA tensors / lists."""
+    def __init__(self, problems, stream=None, solo_terms: int | None = None):
+        """problems: list of (amp (ny, nx), coeff (N, D), noll list) CUDA tensors / lists;
+        solo_terms: the standalone threshold (None: the library default)."""
         self._lib = _lib.load()
         self._b = ctypes.c_void_p(0)
         self.shapes = []
@@ -245,8 +248,12 @@ class Batch:
             descs[i] = _lib.HologramDesc(nx, ny, amp.data_ptr(), D, ctypes.cast(arr, _lib.c_int_p), None, N,
                                          coeff.data_ptr())
             self.shapes.append((ny, nx, N, D))
-        _lib.check(self._lib.ash_batch_create(ctypes.byref(self._b), len(problems), descs, _stream_ptr(stream)),
-                   "ash_batch_create")
+        if solo_terms is None:
+            _lib.check(self._lib.ash_batch_create(ctypes.byref(self._b), len(problems), descs, _stream_ptr(stream)),
+                       "ash_batch_create")
+        else:
+            _lib.check(self._lib.ash_batch_create_ex(ctypes.byref(self._b), len(problems), descs, int(solo_terms),
+                                                     _stream_ptr(stream)), "ash_batch_create_ex")
 
     def close(self):
         if getattr(self, "_b", None) is not None and self._b.value:
@@ -269,7 +276,8 @@ class Batch:
         u = ctypes.c_longlong()
         _lib.check(self._lib.ash_batch_info(self._b, ctypes.byref(c), ctypes.byref(g), ctypes.byref(r),
                                             ctypes.byref(u)), "ash_batch_info")
-        return {"count": c.value, "grid": g.value, "resident_ctas": r.value, "units": u.value}
+        return {"count": c.value, "grid": g.value, "resident_ctas": r.value, "units": u.value,
+                "standalone": int(self._lib.ash_batch_standalone(self._b))}
 
     def set_grid(self, grid: int):
         _lib.check(self._lib.ash_batch_set_grid(self._b, int(grid)), "ash_batch_set_grid")

@@ -137,3 +137,47 @@ def test_batch_rejects_large_D():
     p = random_problem(1, 32, 32, 4, list(range(2, 16)))
     with pytest.raises(Exception):
         Batch([(torch.from_numpy(p.amp).cuda(), torch.from_numpy(p.coeff).cuda(), p.noll)])
+
+
+@pytest.mark.parametrize("solo_terms", [0, 200_000])
+def test_batch_standalone_members(solo_terms):
+    # members at or above the threshold run the single-hologram loop inside
+    # the batch's graph: bit for bit the result of ash_wgs_iterate on their
+    # own handle; the others stay in the persistent group
+    from paper_2505_08777_gb300 import Batch, Hologram, _lib
+    ps = _problems(90)
+    b = Batch([(torch.from_numpy(p.amp).cuda(), torch.from_numpy(p.coeff).cuda(), p.noll) for p in ps],
+              solo_terms=solo_terms)
+    solo = [p.N * p.nx * p.ny >= solo_terms for p in ps]
+    assert 0 < sum(solo) and (solo_terms == 0 or not all(solo))
+    info = b.info()
+    assert info["count"] == len(ps) and info["standalone"] == sum(solo)
+    if all(solo):
+        assert info["grid"] == 0 and b.tune([torch.from_numpy(p.phase0).cuda() for p in ps]) == 0
+    ph, w, T = _state(ps)
+    met = b.wgs(ph, w, T, 4)
+    lib = _lib.load()
+    n_solo_launches = 0
+    for k, p in enumerate(ps):
+        h = Hologram(torch.from_numpy(p.amp).cuda(), torch.from_numpy(p.coeff).cuda(), noll=p.noll)
+        ph1 = torch.from_numpy(p.phase0).cuda().clone()
+        w1 = torch.from_numpy(p.target).cuda().clone()
+        _, met1 = h.wgs(ph1, w1, T[k], 4)
+        torch.cuda.synchronize()
+        if solo[k]:
+            assert torch.equal(ph[k], ph1) and torch.equal(w[k], w1) and torch.equal(met[k], met1)
+            n_solo_launches += int(lib.ash_wgs_launches(h.handle, 4))
+        else:
+            assert abs(float(met[k, 0]) - float(met1[0])) <= UNIF_TOL
+    if all(solo):
+        assert b.launches(4) == n_solo_launches
+    else:
+        assert b.launches(4) > n_solo_launches
+
+
+def test_batch_rejects_negative_threshold():
+    from paper_2505_08777_gb300 import Batch
+    from paper_2505_08777_gb300._lib import AshError
+    p = _problems(95)[0]
+    with pytest.raises(AshError):
+        Batch([(torch.from_numpy(p.amp).cuda(), torch.from_numpy(p.coeff).cuda(), p.noll)], solo_terms=-1)
