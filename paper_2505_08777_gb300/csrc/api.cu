@@ -206,6 +206,7 @@ TcFwdParams tc_fwd_params(const ash_hologram* h, float2* E) {
   p.begin = h->tfwd_begin;
   p.E = E;
   p.part = h->tc_part;
+  p.spans = h->tfwd_spans;
   p.err = h->err_word;
   return p;
 }
@@ -734,7 +735,8 @@ ash_status create_impl(ash_hologram** out, int nx, int ny, const float* amp, int
       if (h->sched.begin(b) % N != 0) h->split_tiles = true;
   }
   h->fwd_rows = g.T * (g.NT / 32);
-  std::vector<int> tadj_groups;
+  std::vector<int4> tadj_groups;
+  std::vector<int2> tfwd_spans;
   std::vector<long long> tfwd_begin, tadj_begin, tgrad_begin;
   if (D <= kTcMaxModes) {
     // tensor-core path: one range of units per resident CTA, at least two
@@ -756,7 +758,11 @@ ash_status create_impl(ash_hologram** out, int nx, int ny, const float* amp, int
       const long long u = h->tadj.begin(b);
       if (u % nch == 0) continue;
       const int grp = (int)(u / nch);
-      if (tadj_groups.empty() || tadj_groups.back() != grp) tadj_groups.push_back(grp);
+      if (tadj_groups.empty() || tadj_groups.back().x != grp) {
+        const long long ulo = (long long)grp * nch;
+        tadj_groups.push_back(make_int4(grp, tc_owner(tadj_begin.data(), h->tadj.G, ulo),
+                                        tc_owner(tadj_begin.data(), h->tadj.G, ulo + nch - 1), 0));
+      }
     }
     h->tadj_split = !tadj_groups.empty();
     h->tadj_nsplit = (int)tadj_groups.size();
@@ -770,6 +776,10 @@ ash_status create_impl(ash_hologram** out, int nx, int ny, const float* amp, int
     for (int b = 0; b <= f.G; ++b) tfwd_begin.push_back(f.begin(b));
     for (int b = 1; b < f.G; ++b)
       if (tfwd_begin[b] % f.nq != 0) h->tfwd_split = true;
+    for (int b = 0; b < f.nb; ++b) {
+      const long long ulo = (long long)b * f.nq;
+      tfwd_spans.push_back(make_int2(tc_owner(tfwd_begin.data(), f.G, ulo), tc_owner(tfwd_begin.data(), f.G, ulo + f.nq - 1)));
+    }
     int npow = 2;
     if (spec)
       for (const MonoTerm& m : spec->terms) npow = m.px + 1 > npow ? m.px + 1 : npow;
@@ -816,6 +826,7 @@ ash_status create_impl(ash_hologram** out, int nx, int ny, const float* amp, int
     if ((st = ws(h, &h->tc_split, (size_t)h->tadj.G * 2 * kTcRows)) != ASH_OK) return fail(st);
     if ((st = ws(h, &h->tc_part, (size_t)h->tfwd.G * 2 * kTcRows)) != ASH_OK) return fail(st);
     if ((st = ws(h, &h->tfwd_begin, tfwd_begin.size())) != ASH_OK) return fail(st);
+    if ((st = ws(h, &h->tfwd_spans, tfwd_spans.size())) != ASH_OK) return fail(st);
     if ((st = ws(h, &h->tadj_begin, tadj_begin.size())) != ASH_OK) return fail(st);
     if ((st = ws(h, &h->tadj_groups, tadj_groups.size() + 1)) != ASH_OK) return fail(st);
   }
@@ -880,10 +891,12 @@ ash_status create_impl(ash_hologram** out, int nx, int ny, const float* amp, int
   if (h->tc_ok) {
     CREATE_CUDA(cudaMemcpyAsync(h->tfwd_begin, tfwd_begin.data(), tfwd_begin.size() * sizeof(long long),
                                 cudaMemcpyHostToDevice, s));
+    CREATE_CUDA(cudaMemcpyAsync(h->tfwd_spans, tfwd_spans.data(), tfwd_spans.size() * sizeof(int2),
+                                cudaMemcpyHostToDevice, s));
     CREATE_CUDA(cudaMemcpyAsync(h->tadj_begin, tadj_begin.data(), tadj_begin.size() * sizeof(long long),
                                 cudaMemcpyHostToDevice, s));
     if (!tadj_groups.empty())
-      CREATE_CUDA(cudaMemcpyAsync(h->tadj_groups, tadj_groups.data(), tadj_groups.size() * sizeof(int),
+      CREATE_CUDA(cudaMemcpyAsync(h->tadj_groups, tadj_groups.data(), tadj_groups.size() * sizeof(int4),
                                   cudaMemcpyHostToDevice, s));
     CREATE_CUDA(tc_build_zs(g, h->tc_layout, h->dz, h->zs, s));
     if (h->tgrad_ok) {

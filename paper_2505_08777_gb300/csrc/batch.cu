@@ -274,7 +274,7 @@ struct ash_batch {
   int* d_g0 = nullptr;             // [2][count] first CTA meeting each hologram
   long long* d_begin = nullptr;    // per-hologram CTA boundary tables
   float2* d_tsplit = nullptr;      // per-hologram split slots
-  int2* d_lists = nullptr;         // adjoint fix-up list, then forward reduction list
+  int4* d_lists = nullptr;         // adjoint fix-up list, then forward reduction list
   TcFieldDesc* d_field = nullptr;
   int* d_tiles0 = nullptr;
   TcBatchSched bs_adj{}, bs_fwd{};
@@ -292,7 +292,7 @@ ash_status build_tc(ash_batch* b) {
   const int count = b->count;
   std::vector<long long> hu0(2 * (count + 1)), begins;
   std::vector<int> g0(2 * count);
-  std::vector<int2> fix, red;
+  std::vector<int4> fix, red;   // (hologram, group or block, first CTA, last CTA) in local CTA numbers
   std::vector<TcAdjParams> adj(count);
   std::vector<TcFwdParams> fwd(count);
   size_t split_off = 0;
@@ -342,7 +342,11 @@ ash_status build_tc(ash_batch* b) {
           const long long u = begins[tab + k];
           if (u % nch == 0) continue;
           const int grp = (int)(u / nch);
-          if (fix.empty() || fix.back().x != h || fix.back().y != grp) fix.push_back(make_int2(h, grp));
+          if (fix.empty() || fix.back().x != h || fix.back().y != grp) {
+            const long long ulo = (long long)grp * nch;
+            fix.push_back(make_int4(h, grp, tc_owner(begins.data() + tab, Gh, ulo),
+                                    tc_owner(begins.data() + tab, Gh, ulo + nch - 1)));
+          }
         }
         TcAdjParams& p = adj[h];
         p.g = g;
@@ -373,7 +377,11 @@ ash_status build_tc(ash_batch* b) {
         p.E = H->wgs_E;
         p.part = reinterpret_cast<float2*>(so);
         p.err = H->err_word;
-        for (int blk = 0; blk < p.sched.nb; ++blk) red.push_back(make_int2(h, blk));
+        for (int blk = 0; blk < p.sched.nb; ++blk) {
+          const long long ulo = (long long)blk * p.sched.nq;
+          red.push_back(make_int4(h, blk, tc_owner(begins.data() + tab, Gh, ulo),
+                                  tc_owner(begins.data() + tab, Gh, ulo + p.sched.nq - 1)));
+        }
       }
     }
   }
@@ -389,7 +397,7 @@ ash_status build_tc(ash_batch* b) {
   }
   b->n_fix = (int)fix.size();
   b->n_red = (int)red.size();
-  std::vector<int2> lists(fix);
+  std::vector<int4> lists(fix);
   lists.insert(lists.end(), red.begin(), red.end());
   b->bs_adj.hu0 = b->d_hu0;
   b->bs_adj.g0 = b->d_g0;
@@ -402,7 +410,7 @@ ash_status build_tc(ash_batch* b) {
       (e = cudaMemcpy(b->d_adj, adj.data(), adj.size() * sizeof(TcAdjParams), cudaMemcpyHostToDevice)) ||
       (e = cudaMemcpy(b->d_fwd, fwd.data(), fwd.size() * sizeof(TcFwdParams), cudaMemcpyHostToDevice)) ||
       (!lists.empty() &&
-       (e = cudaMemcpy(b->d_lists, lists.data(), lists.size() * sizeof(int2), cudaMemcpyHostToDevice))))
+       (e = cudaMemcpy(b->d_lists, lists.data(), lists.size() * sizeof(int4), cudaMemcpyHostToDevice))))
     return status_cuda(e, "batch tensor-core tables");
   return ASH_OK;
 }
@@ -685,7 +693,7 @@ ash_status ash_batch_create_ex(ash_batch** out, int count, const ash_hologram_de
     if (cudaMalloc(&b->d_adj, sizeof(TcAdjParams) * count) || cudaMalloc(&b->d_fwd, sizeof(TcFwdParams) * count) ||
         cudaMalloc(&b->d_hu0, sizeof(long long) * 2 * (count + 1)) || cudaMalloc(&b->d_g0, sizeof(int) * 2 * count) ||
         cudaMalloc(&b->d_begin, sizeof(long long) * b->cap_begin) ||
-        cudaMalloc(&b->d_tsplit, sizeof(float2) * b->cap_split) || cudaMalloc(&b->d_lists, sizeof(int2) * b->cap_fix) ||
+        cudaMalloc(&b->d_tsplit, sizeof(float2) * b->cap_split) || cudaMalloc(&b->d_lists, sizeof(int4) * b->cap_fix) ||
         cudaMalloc(&b->d_field, sizeof(TcFieldDesc) * count) || cudaMalloc(&b->d_tiles0, sizeof(int) * count)) {
       cudaGetLastError();
       return bail(fail(ASH_ERR_OOM, "batch tensor-core table allocation"));

@@ -45,8 +45,9 @@ struct ash_hologram {
   float2* tc_split = nullptr;   // [tadj.G][2][128]
   float2* tc_part = nullptr;    // [tfwd.G][2][128]
   long long* tfwd_begin = nullptr;   // [tfwd.G + 1] CTA range starts of the forward
+  int2* tfwd_spans = nullptr;        // [tfwd.nb] first and last CTA meeting each spot block
   long long* tadj_begin = nullptr;   // [tadj.G + 1] CTA range starts of the adjoint
-  int* tadj_groups = nullptr;   // groups split between adjoint CTA ranges
+  int4* tadj_groups = nullptr;  // (group, first CTA, last CTA, -) of the groups split between adjoint CTA ranges
   int tadj_nsplit = 0;
   bool tgrad_ok = false;        // tensor-core moment pass of the coefficient gradient (one K-atom)
   ash::TcFwdSched tgrad{};      // its units (spot block, pixel chunk)

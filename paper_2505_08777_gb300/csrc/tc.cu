@@ -92,7 +92,7 @@ cudaError_t tc_launch_adjoint_batch(int NA, const TcAdjParams* ps, const TcBatch
   return cudaGetLastError();
 }
 
-cudaError_t tc_launch_adjoint_fixup_batch(const TcAdjParams* ps, const int2* list, int n, cudaStream_t s) {
+cudaError_t tc_launch_adjoint_fixup_batch(const TcAdjParams* ps, const int4* list, int n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   k_tc_adjoint_fixup_batch<<<n, kTcThreads, 0, s>>>(ps, list);
   return cudaGetLastError();
@@ -105,7 +105,7 @@ cudaError_t tc_launch_forward_batch(int NA, const TcFwdParams* ps, const TcBatch
   return cudaGetLastError();
 }
 
-cudaError_t tc_launch_forward_reduce_batch(const TcFwdParams* ps, const int2* list, int n, cudaStream_t s) {
+cudaError_t tc_launch_forward_reduce_batch(const TcFwdParams* ps, const int4* list, int n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   k_tc_forward_reduce_batch<<<dim3(n, kTcRows / 32), dim3(32, 32), 0, s>>>(ps, list);
   return cudaGetLastError();

@@ -505,11 +505,11 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_tc_adjoint_batch(const TcAdjP
 
 // Groups whose spots were split between CTAs of k_tc_adjoint: the partial
 // sums in CTA order, then the epilogue. One CTA of 128 threads per split group.
-__device__ __forceinline__ void tc_adjoint_fixup_group(const TcAdjParams& p, long long s) {
+// Group s, split over CTAs b_lo..b_hi (tabulated on the host).
+__device__ __forceinline__ void tc_adjoint_fixup_group(const TcAdjParams& p, long long s, int b_lo, int b_hi) {
   const int nch = (p.g.N + kTcChunk - 1) / kTcChunk;
-  const long long ulo = s * nch, uhi = ulo + nch - 1;
+  const long long ulo = s * nch;
   const int t = threadIdx.x;
-  const int b_lo = tc_owner(p.begin, p.G, ulo), b_hi = tc_owner(p.begin, p.G, uhi);
   float gr = 0.0f, gi = 0.0f;
   for (int cb = b_lo; cb <= b_hi; ++cb) {
     const long long beg = p.begin[cb];
@@ -521,12 +521,15 @@ __device__ __forceinline__ void tc_adjoint_fixup_group(const TcAdjParams& p, lon
   tc_adjoint_epilogue(p, 2 * s + (t >> 6), t & 63, gr, gi);
 }
 
-static __global__ void k_tc_adjoint_fixup(const TcAdjParams p) { tc_adjoint_fixup_group(p, p.split_groups[blockIdx.x]); }
+static __global__ void k_tc_adjoint_fixup(const TcAdjParams p) {
+  const int4 e = p.split_groups[blockIdx.x];
+  tc_adjoint_fixup_group(p, e.x, e.y, e.z);
+}
 
-// Batched fix-up: entry i of `list` is (hologram, split group).
-static __global__ void k_tc_adjoint_fixup_batch(const TcAdjParams* __restrict__ ps, const int2* __restrict__ list) {
-  const int2 e = list[blockIdx.x];
-  tc_adjoint_fixup_group(ps[e.x], e.y);
+// Batched fix-up: entry i of `list` is (hologram, split group, first CTA, last CTA).
+static __global__ void k_tc_adjoint_fixup_batch(const TcAdjParams* __restrict__ ps, const int4* __restrict__ list) {
+  const int4 e = list[blockIdx.x];
+  tc_adjoint_fixup_group(ps[e.x], e.y, e.z, e.w);
 }
 
 // --- forward ------------------------------------------------------------------
@@ -800,12 +803,12 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_tc_forward_batch(const TcFwdP
 // the sum of the CTAs' partial sums. CTA (b, y) sums 32 spots of block b:
 // row-lane k of the 32 x 32 threads adds the partials of CTAs g_lo + k,
 // g_lo + k + 32, ..., then a fixed-shape tree combines the row-lanes.
-__device__ __forceinline__ void tc_forward_reduce_block(const TcFwdParams& p, long long b, int col) {
+__device__ __forceinline__ void tc_forward_reduce_block(const TcFwdParams& p, long long b, int col, int g_lo,
+                                                        int g_hi) {
   __shared__ float2 acc[32][33];
   const int nq = p.g.T * kTcChunksPerTile;
-  const long long ulo = b * nq, uhi = ulo + nq - 1;
+  const long long ulo = b * nq;
   const int k = threadIdx.y;
-  const int g_lo = tc_owner(p.begin, p.sched.G, ulo), g_hi = tc_owner(p.begin, p.sched.G, uhi);
   if (g_lo == g_hi) return;   // one CTA owned the block and wrote E itself
   float2 v = make_float2(0.0f, 0.0f);
   for (int cb = g_lo + k; cb <= g_hi; cb += 32) {
@@ -829,13 +832,14 @@ __device__ __forceinline__ void tc_forward_reduce_block(const TcFwdParams& p, lo
 }
 
 static __global__ void k_tc_forward_reduce(const TcFwdParams p) {
-  tc_forward_reduce_block(p, blockIdx.x, blockIdx.y * 32 + threadIdx.x);
+  const int2 sp = p.spans[blockIdx.x];
+  tc_forward_reduce_block(p, blockIdx.x, blockIdx.y * 32 + threadIdx.x, sp.x, sp.y);
 }
 
-// Batched reduction: entry i of `list` is (hologram, spot block).
-static __global__ void k_tc_forward_reduce_batch(const TcFwdParams* __restrict__ ps, const int2* __restrict__ list) {
-  const int2 e = list[blockIdx.x];
-  tc_forward_reduce_block(ps[e.x], e.y, blockIdx.y * 32 + threadIdx.x);
+// Batched reduction: entry i of `list` is (hologram, spot block, first CTA, last CTA).
+static __global__ void k_tc_forward_reduce_batch(const TcFwdParams* __restrict__ ps, const int4* __restrict__ list) {
+  const int4 e = list[blockIdx.x];
+  tc_forward_reduce_block(ps[e.x], e.y, blockIdx.y * 32 + threadIdx.x, e.z, e.w);
 }
 
 // Nearfield images of a batch (one thread per pixel of the concatenated tiles).

@@ -182,7 +182,7 @@ struct TcAdjParams {
                           // W = T * 8 * ceil(N / 64) of them
   int G;
   float2* split;          // [G][2][128] partial sums of groups split between CTAs
-  const int* split_groups;   // the groups whose spots span two or more CTA ranges
+  const int4* split_groups;  // (group, first CTA, last CTA, -) of the groups whose spots span two or more CTA ranges
   unsigned* err;
 };
 
@@ -197,6 +197,7 @@ struct TcFwdParams {
   const long long* begin; // [G + 1] sched.begin(g), tabulated on the host
   float2* E;              // [N]
   float2* part;           // [G][2][128] partial sums of spot blocks split between CTAs
+  const int2* spans;      // [nb] first and last CTA meeting each spot block (host-tabulated)
   unsigned* err;
 };
 
@@ -242,9 +243,9 @@ cudaError_t tc_launch_forward_reduce(const TcFwdParams& p, cudaStream_t s);
 // device arrays of their parameter blocks, the batch schedule, and the
 // fix-up / reduction work lists (hologram, group) and (hologram, spot block).
 cudaError_t tc_launch_adjoint_batch(int NA, const TcAdjParams* ps, const TcBatchSched& bs, cudaStream_t s);
-cudaError_t tc_launch_adjoint_fixup_batch(const TcAdjParams* ps, const int2* list, int n, cudaStream_t s);
+cudaError_t tc_launch_adjoint_fixup_batch(const TcAdjParams* ps, const int4* list, int n, cudaStream_t s);
 cudaError_t tc_launch_forward_batch(int NA, const TcFwdParams* ps, const TcBatchSched& bs, cudaStream_t s);
-cudaError_t tc_launch_forward_reduce_batch(const TcFwdParams* ps, const int2* list, int n, cudaStream_t s);
+cudaError_t tc_launch_forward_reduce_batch(const TcFwdParams* ps, const int4* list, int n, cudaStream_t s);
 // Nearfield images of a batch from each hologram's phase (the `phase` of
 // its TcFwdParams-sized descriptor below); tiles0[h] = first global tile.
 struct TcFieldDesc {
