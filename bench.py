@@ -100,6 +100,15 @@ def _dist():
     return rank, world, local
 
 
+def _scratch_dir() -> str:
+    """Where the clock samples and the batch autotuner cache go
+    (ASH_BENCH_DIR, else the system temporary directory)."""
+    import tempfile
+    d = os.environ.get("ASH_BENCH_DIR") or tempfile.gettempdir()
+    os.makedirs(d, exist_ok=True)
+    return d
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
 
@@ -110,7 +119,7 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.path = os.path.join(_scratch_dir(), f"clocks_rank{gpu_index}.csv")
 
     def __enter__(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
@@ -659,7 +668,7 @@ def bench_batch(args):
     T = [torch.from_numpy(p.target).to(dev) for p in ps]
     ph = [x.clone() for x in ph0]
     w = [t.clone() for t in T]
-    tuned = b.tune(ph0, os.path.join(ROOT, "gpurun_out", "ash_tune.txt"))
+    tuned = b.tune(ph0, os.path.join(_scratch_dir(), "ash_tune.txt"))
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 

@@ -18,7 +18,7 @@ weighted GS, scale-invariant form, feedback exponent 1, no phase fixing):
      phi = arg g   (0 where g == 0 exactly)
   finally E = K (A exp(i phi)) is the reported field.
 
-Variants (SURVEY's next step on WGS; Kim et al. is only cited): the weight
+Variants (the paper only cites Kim et al. for its WGS): the weight
 update with a feedback exponent p, w = w * (T^ / max(E^, 1e-30))^p (p = 1
 above; p = 0 keeps w = T^, plain GS), and phase fixing, where psi is held
 at given values instead of arg E.

@@ -171,6 +171,7 @@ TcGradParams tc_grad_params(const ash_hologram* h, const float2* gE, float* dC) 
   p.gE = gE;
   p.sched = h->tgrad;
   p.begin = h->tgrad_begin;
+  p.spans = h->tgrad_spans;
   p.dC = dC;
   p.part = h->tgrad_part;
   p.err = h->err_word;
@@ -736,7 +737,7 @@ ash_status create_impl(ash_hologram** out, int nx, int ny, const float* amp, int
   }
   h->fwd_rows = g.T * (g.NT / 32);
   std::vector<int4> tadj_groups;
-  std::vector<int2> tfwd_spans;
+  std::vector<int2> tfwd_spans, tgrad_spans;
   std::vector<long long> tfwd_begin, tadj_begin, tgrad_begin;
   if (D <= kTcMaxModes) {
     // tensor-core path: one range of units per resident CTA, at least two
@@ -798,6 +799,11 @@ ash_status create_impl(ash_hologram** out, int nx, int ny, const float* amp, int
       for (int b = 0; b <= m.G; ++b) tgrad_begin.push_back(m.begin(b));
       for (int b = 1; b < m.G; ++b)
         if (tgrad_begin[b] % m.nq != 0) h->tgrad_split = true;
+      for (int b = 0; b < m.nb; ++b) {
+        const long long ulo = (long long)b * m.nq;
+        tgrad_spans.push_back(
+            make_int2(tc_owner(tgrad_begin.data(), m.G, ulo), tc_owner(tgrad_begin.data(), m.G, ulo + m.nq - 1)));
+      }
     }
   }
   h->gradc_gy = (N + kGradThreads * kGradSpots - 1) / (kGradThreads * kGradSpots);
@@ -834,6 +840,7 @@ ash_status create_impl(ash_hologram** out, int nx, int ny, const float* amp, int
     if ((st = ws(h, &h->zrow, tc_zrow_floats(g, h->tgrad_npow))) != ASH_OK) return fail(st);
     if ((st = ws(h, &h->tgrad_part, (size_t)h->tgrad.G * 2 * kTcRows * tc_grad_dp(D))) != ASH_OK) return fail(st);
     if ((st = ws(h, &h->tgrad_begin, tgrad_begin.size())) != ASH_OK) return fail(st);
+    if ((st = ws(h, &h->tgrad_spans, tgrad_spans.size())) != ASH_OK) return fail(st);
   }
   if ((st = ws(h, &h->gradc_partial, (size_t)h->gradc_gx * N * D)) != ASH_OK) return fail(st);
   if ((st = ws(h, &h->E, (size_t)N)) != ASH_OK) return fail(st);
@@ -901,6 +908,8 @@ ash_status create_impl(ash_hologram** out, int nx, int ny, const float* amp, int
     CREATE_CUDA(tc_build_zs(g, h->tc_layout, h->dz, h->zs, s));
     if (h->tgrad_ok) {
       CREATE_CUDA(cudaMemcpyAsync(h->tgrad_begin, tgrad_begin.data(), tgrad_begin.size() * sizeof(long long),
+                                  cudaMemcpyHostToDevice, s));
+      CREATE_CUDA(cudaMemcpyAsync(h->tgrad_spans, tgrad_spans.data(), tgrad_spans.size() * sizeof(int2),
                                   cudaMemcpyHostToDevice, s));
       CREATE_CUDA(tc_build_row_poly(g, h->terms, h->term_off, h->tgrad_npow, h->zrow, s));
     }

@@ -53,6 +53,7 @@ struct ash_hologram {
   ash::TcFwdSched tgrad{};      // its units (spot block, pixel chunk)
   bool tgrad_split = false;     // some spot block's pixels span two CTA ranges
   long long* tgrad_begin = nullptr;  // [tgrad.G + 1]
+  int2* tgrad_spans = nullptr;       // [tgrad.nb] first and last CTA meeting each spot block
   float* tgrad_part = nullptr;  // [tgrad.G][2][128][DC]
   int tgrad_npow = 0;           // powers of the basis row polynomials
   float* zrow = nullptr;        // row polynomials of the basis per chunk

@@ -284,9 +284,9 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_tc_gradc(const TcGradParams p
 __global__ void k_tc_gradc_reduce(const TcGradParams p) {
   __shared__ float acc[32][33];
   const int nq = p.g.T * kTcChunksPerTile, DP = tc_grad_dp(p.g.D);
-  const long long b = blockIdx.x, ulo = b * nq, uhi = ulo + nq - 1;
+  const long long b = blockIdx.x, ulo = b * nq;
   const int col = blockIdx.y * 32 + threadIdx.x, d = blockIdx.z, k = threadIdx.y;
-  const int g_lo = tc_owner(p.begin, p.sched.G, ulo), g_hi = tc_owner(p.begin, p.sched.G, uhi);
+  const int g_lo = p.spans[b].x, g_hi = p.spans[b].y;
   if (g_lo == g_hi) return;
   float v = 0.0f;
   for (int cb = g_lo + k; cb <= g_hi; cb += 32) {

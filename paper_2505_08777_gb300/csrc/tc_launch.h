@@ -220,6 +220,7 @@ struct TcGradParams {
   const float2* gE;       // [N] dL/dE
   TcFwdSched sched;       // units (spot block, pixel chunk), as the forward
   const long long* begin; // [G + 1]
+  const int2* spans;      // [nb] first and last CTA meeting each spot block (host-tabulated)
   int npow;               // powers of the row polynomials (2..5)
   float* dC;              // [N][D] output
   float* part;            // [G][2][128][DP] partial sums of spot blocks split between CTAs

@@ -1,7 +1,7 @@
 """Pins for the oracle's forward / adjoint spot transform (CPU only).
 
-Pinned against: the spec closed form (unaberrated spot, flat-phase
-hologram: E = sum A), the phase-conjugate hologram, numpy's FFT for
+Pinned against: the closed form of an unaberrated spot under a flat-phase
+hologram (E = sum A), the phase-conjugate hologram, numpy's FFT for
 integer-bin tilts (the DFT special case of the compressed transform,
 Sec. II), brute-force pure-Python sums on tiny grids, the adjoint identity
 <Kx, y> = <x, K^H y>, and unitarity (Parseval) when all M bins are targeted.
