@@ -339,245 +339,16 @@ bool bad_ptr(const void* p) { return p == nullptr; }
 
 namespace ash {
 ash_status wgs_body(ash_hologram* h, int iters, cudaStream_t s) { return enqueue_wgs_body(h, iters, s); }
+ash_status forward_enqueue(ash_hologram* h, int source, const float* phase, const float2* field, float2* E,
+                           cudaStream_t s) {
+  return enqueue_forward(h, source, phase, field, E, s);
+}
+ash_status adjoint_enqueue(ash_hologram* h, const float2* y, float2* g_out, float* phase_out, const float* phase_in,
+                           float* dphase, int epilogue, cudaStream_t s) {
+  return enqueue_adjoint(h, y, g_out, phase_out, phase_in, dphase, epilogue, s);
+}
+cudaError_t coeff_images_enqueue(ash_hologram* h, cudaStream_t s) { return enqueue_tc_coeff(h, s); }
 }  // namespace ash
-
-// --- conjugate-gradient phase refinement (paper Methods) --------------------
-
-// fp64 scalars of the iteration in h->cg_scal
-enum CgSlot : int { kCgL = 0, kCgS, kCgA0, kCgL1, kCgA, kCgGG, kCgGN, kCgGX, kCgBeta, kCgMax, kCgTheta, kCgRestart,
-                    kCgZero, kCgSlots };
-constexpr int kCgRedBlocks = 512, kCgMaxIters = 1024;
-
-// Sum of a double over the block (blockDim.x a multiple of 32, <= 1024) in a
-// fixed order; the result is valid in every thread.
-static __device__ double block_sum(double v, double* sh) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  __syncthreads();
-  if (lane == 0) sh[w] = v;
-  __syncthreads();
-  double t = 0.0;
-  for (int k = 0; k < nw; ++k) t += sh[k];
-  return t;
-}
-
-// Spot-intensity loss from E (fp64): I = |E|^2, mu = mean I, r = I/mu - t,
-// L = sum r^2; with gE, its complex gradient gE = 2 G E,
-// G = (2/mu) (r - sum_n(r_n I_n / mu) / N).
-static __global__ void k_cg_loss(const float2* __restrict__ E, const float* __restrict__ t, int N,
-                                 float2* __restrict__ gE, double* __restrict__ scal, int slot,
-                                 float* __restrict__ loss_out) {
-  __shared__ double sh[32];
-  double sI = 0.0;
-  for (int n = threadIdx.x; n < N; n += blockDim.x) {
-    const double ex = E[n].x, ey = E[n].y;
-    sI += ex * ex + ey * ey;
-  }
-  const double mu = block_sum(sI, sh) / N;
-  double sL = 0.0, sX = 0.0;
-  for (int n = threadIdx.x; n < N; n += blockDim.x) {
-    const double ex = E[n].x, ey = E[n].y, I = ex * ex + ey * ey, r = I / mu - (double)t[n];
-    sL += r * r;
-    sX += r * I / mu;
-  }
-  const double L = block_sum(sL, sh), X = block_sum(sX, sh) / N;
-  if (gE) {
-    for (int n = threadIdx.x; n < N; n += blockDim.x) {
-      const double ex = E[n].x, ey = E[n].y, I = ex * ex + ey * ey, r = I / mu - (double)t[n];
-      const double G = (2.0 / mu) * (r - X);
-      gE[n] = make_float2((float)(2.0 * G * ex), (float)(2.0 * G * ey));
-    }
-  }
-  if (threadIdx.x == 0) {
-    scal[slot] = L;
-    if (loss_out) *loss_out = (float)L;
-  }
-}
-
-// Partial reductions over M in a fixed block order: mode 0 sum a b, mode 1
-// max |a|.
-static __global__ void k_cg_reduce(const float* __restrict__ a, const float* __restrict__ b, long long M, int mode,
-                                   double* __restrict__ part) {
-  __shared__ double sh[32];
-  double v = 0.0;
-  for (long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x; m < M; m += (long long)gridDim.x * blockDim.x)
-    v = mode == 0 ? v + (double)a[m] * (double)b[m] : fmax(v, fabs((double)a[m]));
-  if (mode == 0) {
-    v = block_sum(v, sh);
-  } else {
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) sh[w] = v;
-    __syncthreads();
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) v = fmax(v, sh[k]);
-  }
-  if (threadIdx.x == 0) part[blockIdx.x] = v;
-}
-
-static __global__ void k_cg_finish(const double* __restrict__ part, int nparts, int mode, double* __restrict__ scal,
-                                   int slot) {
-  __shared__ double sh[32];
-  double v = 0.0;
-  for (int k = threadIdx.x; k < nparts; k += blockDim.x) v = mode == 0 ? v + part[k] : fmax(v, part[k]);
-  if (mode == 0) {
-    v = block_sum(v, sh);
-  } else {
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) sh[w] = v;
-    __syncthreads();
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) v = fmax(v, sh[k]);
-  }
-  if (threadIdx.x == 0) scal[slot] = v;
-}
-
-// The scalar steps of one CG iteration (one thread), in the order of the
-// iteration: 0 restart test on s = g.d; 1 trial step a0 = theta / max|d|;
-// 2 step a from the quadratic through L, s and L(a0); 3 beta (PR+).
-static __global__ void k_cg_step(double* scal, int op) {
-  double* c = scal;
-  if (op == 0) {
-    c[kCgRestart] = c[kCgS] >= 0.0 ? 1.0 : 0.0;
-    if (c[kCgS] >= 0.0) c[kCgS] = -c[kCgGG];
-  } else if (op == 1) {
-    c[kCgA0] = c[kCgMax] > 0.0 ? c[kCgTheta] / c[kCgMax] : 0.0;
-  } else if (op == 2) {
-    const double a0 = c[kCgA0];
-    if (a0 > 0.0) {
-      const double curv = (c[kCgL1] - c[kCgL] - c[kCgS] * a0) / (a0 * a0);
-      c[kCgA] = curv > 0.0 ? -c[kCgS] / (2.0 * curv) : 2.0 * a0;
-    } else {
-      c[kCgA] = 0.0;
-    }
-  } else {
-    c[kCgBeta] = c[kCgGG] > 0.0 ? fmax(0.0, (c[kCgGN] - c[kCgGX]) / c[kCgGG]) : 0.0;
-    c[kCgGG] = c[kCgGN];
-  }
-}
-
-// out = x + scal[slot] d
-static __global__ void k_cg_axpy(float* out, const float* x, const float* __restrict__ d, long long M,
-                                 const double* __restrict__ scal, int slot) {
-  const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= M) return;
-  out[m] = (float)((double)x[m] + scal[slot] * (double)d[m]);
-}
-
-// d = -g + scal[slot] d; with `if_restart`, only when the restart flag is set
-static __global__ void k_cg_dir(float* __restrict__ d, const float* __restrict__ g, long long M,
-                                const double* __restrict__ scal, int slot, int if_restart) {
-  const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= M || (if_restart && scal[kCgRestart] == 0.0)) return;
-  d[m] = (float)(-(double)g[m] + scal[slot] * (double)d[m]);
-}
-
-// The CG loop on the handle's buffers (phase cg_phase, targets cg_t; scalars
-// kCgTheta and kCgZero set by the caller): the loss and gradient at the
-// start, then `iters` iterations; loss k in cg_loss[k].
-static ash_status enqueue_cg_body(ash_hologram* h, int iters, cudaStream_t s) {
-  const long long M = (long long)h->g.nx * h->g.ny;
-  const int N = h->g.N;
-  const unsigned vb = (unsigned)((M + 255) / 256);
-  float* g[2] = {h->cg_g, h->cg_g + M};
-  double* sc = h->cg_scal;
-  auto chk = [&](const char* where) -> ash_status {
-    const cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? ASH_OK : cuda_fail(e, where);
-  };
-  auto dot = [&](const float* a, const float* b, int mode, int slot) {
-    k_cg_reduce<<<kCgRedBlocks, 256, 0, s>>>(a, b, M, mode, h->cg_part);
-    k_cg_finish<<<1, 512, 0, s>>>(h->cg_part, kCgRedBlocks, mode, sc, slot);
-  };
-  ash_status st;
-  if ((st = enqueue_forward(h, kSrcPhase, h->cg_phase, nullptr, h->E, s)) != ASH_OK) return st;
-  k_cg_loss<<<1, 1024, 0, s>>>(h->E, h->cg_t, N, h->y, sc, kCgL, h->cg_loss);
-  if ((st = chk("CG loss launch")) != ASH_OK) return st;
-  if ((st = enqueue_adjoint(h, h->y, nullptr, nullptr, h->cg_phase, g[0], kEpiGradPhase, s)) != ASH_OK) return st;
-  dot(g[0], g[0], 0, kCgGG);
-  k_cg_dir<<<vb, 256, 0, s>>>(h->cg_d, g[0], M, sc, kCgZero, 0);   // d = -g
-  if ((st = chk("CG start launch")) != ASH_OK) return st;
-  int cur = 0;
-  for (int k = 0; k < iters; ++k) {
-    dot(g[cur], h->cg_d, 0, kCgS);
-    k_cg_step<<<1, 1, 0, s>>>(sc, 0);
-    k_cg_dir<<<vb, 256, 0, s>>>(h->cg_d, g[cur], M, sc, kCgZero, 1);   // restart: d = -g
-    dot(h->cg_d, nullptr, 1, kCgMax);
-    k_cg_step<<<1, 1, 0, s>>>(sc, 1);
-    k_cg_axpy<<<vb, 256, 0, s>>>(h->cg_trial, h->cg_phase, h->cg_d, M, sc, kCgA0);
-    if ((st = chk("CG trial launch")) != ASH_OK) return st;
-    if ((st = enqueue_forward(h, kSrcPhase, h->cg_trial, nullptr, h->E, s)) != ASH_OK) return st;
-    k_cg_loss<<<1, 1024, 0, s>>>(h->E, h->cg_t, N, nullptr, sc, kCgL1, nullptr);
-    k_cg_step<<<1, 1, 0, s>>>(sc, 2);
-    k_cg_axpy<<<vb, 256, 0, s>>>(h->cg_phase, h->cg_phase, h->cg_d, M, sc, kCgA);
-    if ((st = chk("CG step launch")) != ASH_OK) return st;
-    if ((st = enqueue_forward(h, kSrcPhase, h->cg_phase, nullptr, h->E, s)) != ASH_OK) return st;
-    k_cg_loss<<<1, 1024, 0, s>>>(h->E, h->cg_t, N, h->y, sc, kCgL, h->cg_loss + k + 1);
-    if ((st = chk("CG loss launch")) != ASH_OK) return st;
-    if ((st = enqueue_adjoint(h, h->y, nullptr, nullptr, h->cg_phase, g[cur ^ 1], kEpiGradPhase, s)) != ASH_OK)
-      return st;
-    dot(g[cur ^ 1], g[cur ^ 1], 0, kCgGN);
-    dot(g[cur ^ 1], g[cur], 0, kCgGX);
-    k_cg_step<<<1, 1, 0, s>>>(sc, 3);
-    k_cg_dir<<<vb, 256, 0, s>>>(h->cg_d, g[cur ^ 1], M, sc, kCgBeta, 0);
-    if ((st = chk("CG direction launch")) != ASH_OK) return st;
-    cur ^= 1;
-  }
-  return ASH_OK;
-}
-
-// --- simulated Zernike-subtraction calibration (paper Sec. III) -----------
-
-// coeff = base - delta e_mode for every spot: the system seen through the
-// SLM phase phi + delta Z_mode, since exp(i delta Z_d) exp(-i C . Z) =
-// exp(-i (C - delta e_d) . Z).
-static __global__ void k_zsub_shift(const float* __restrict__ base, float* __restrict__ coeff, int N, int D, int mode,
-                                    float delta) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (long long)N * D) return;
-  coeff[i] = base[i] - ((int)(i % D) == mode ? delta : 0.0f);
-}
-
-static __global__ void k_abs2(const float2* __restrict__ E, float* __restrict__ I, int N) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= N) return;
-  const float2 e = E[n];
-  I[n] = e.x * e.x + e.y * e.y;
-}
-
-// Least-squares parabola through (delta_k, ln I_k): P = (X^T X)^-1 X^T with
-// rows X_k = (1, delta_k, delta_k^2), from the host in fp64.
-constexpr int kZsubMaxK = 32;
-struct ZsubFit {
-  int K;
-  double dmin, dmax;
-  double P[3][kZsubMaxK];
-  double delta[kZsubMaxK];
-};
-
-// Per spot (fp64): (a, b, c) = P ln max(I, 1e-37); the vertex -b / (2 c)
-// clipped to the sweep range if c < 0, else the offset of the largest sample.
-static __global__ void k_zsub_estimate(const float* __restrict__ I, int N, const ZsubFit fit,
-                                       float* __restrict__ out, float* __restrict__ coeff, int D, int mode) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= N) return;
-  double b = 0.0, c = 0.0, best = -1e300;
-  int kbest = 0;
-  for (int k = 0; k < fit.K; ++k) {
-    const double L = log((double)fmaxf(I[(size_t)k * N + n], 1e-37f));
-    b += fit.P[1][k] * L;
-    c += fit.P[2][k] * L;
-    if (L > best) {
-      best = L;
-      kbest = k;
-    }
-  }
-  double v = fit.delta[kbest];
-  if (c < 0.0) v = fmin(fmax(-b / (2.0 * c), fit.dmin), fit.dmax);
-  out[n] = (float)v;
-  if (coeff) coeff[(size_t)n * D + mode] += (float)v;
-}
 
 // Two pixels per thread, as in the transforms' pair loops.
 static __global__ void k_debug_sincos(const float* __restrict__ x, int n, float* __restrict__ s, float* __restrict__ c,
@@ -1021,122 +792,8 @@ ash_status ash_forward_field(ash_hologram* h, const float* field, float* E, void
                          as_stream(stream));
 }
 
-ash_status ash_zsub_sweep(ash_hologram* h, const float* phase, int mode, const float* deltas, int K, float* intensity,
-                          void* stream) {
-  if (!h || !phase || !deltas || !intensity) return set_error(ASH_ERR_INVALID_ARG, "NULL argument");
-  if (mode < 0 || mode >= h->g.D) return set_error(ASH_ERR_INVALID_ARG, "mode %d outside [0, %d)", mode, h->g.D);
-  if (K < 1 || K > kZsubMaxK) return set_error(ASH_ERR_INVALID_ARG, "K = %d outside [1, %d]", K, kZsubMaxK);
-  if (injected_failure()) return set_error(ASH_ERR_INJECTED, "injected failure");
-  cudaStream_t s = as_stream(stream);
-  const int N = h->g.N, D = h->g.D;
-  const size_t bytes = (size_t)N * D * sizeof(float);
-  const unsigned blocks = (unsigned)(((size_t)N * D + 255) / 256);
-  ASH_CUDA(cudaMemcpyAsync(h->coeff_bak, h->coeff, bytes, cudaMemcpyDeviceToDevice, s));
-  ash_status st = ASH_OK;
-  for (int k = 0; k < K && st == ASH_OK; ++k) {
-    k_zsub_shift<<<blocks, 256, 0, s>>>(h->coeff_bak, h->coeff, N, D, mode, deltas[k]);
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = enqueue_tc_coeff(h, s);
-    if (e != cudaSuccess) {
-      st = cuda_fail(e, "calibration sweep");
-      break;
-    }
-    st = enqueue_forward(h, kSrcPhase, phase, nullptr, h->E, s);
-    if (st != ASH_OK) break;
-    k_abs2<<<(N + 255) / 256, 256, 0, s>>>(h->E, intensity + (size_t)k * N, N);
-    if ((e = cudaGetLastError()) != cudaSuccess) st = cuda_fail(e, "calibration sweep");
-  }
-  // the handle's coefficients and operand images are restored in every case
-  cudaError_t e = cudaMemcpyAsync(h->coeff, h->coeff_bak, bytes, cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess) e = enqueue_tc_coeff(h, s);
-  if (st == ASH_OK && e != cudaSuccess) st = cuda_fail(e, "calibration sweep restore");
-  return st;
-}
 
-ash_status ash_zsub_estimate(const float* intensity, const float* deltas, int K, int N, float* delta_star,
-                             float* coeff, int D, int mode, void* stream) {
-  if (!intensity || !deltas || !delta_star) return set_error(ASH_ERR_INVALID_ARG, "NULL argument");
-  if (K < 3 || K > kZsubMaxK) return set_error(ASH_ERR_INVALID_ARG, "K = %d outside [3, %d]", K, kZsubMaxK);
-  if (N < 0) return set_error(ASH_ERR_INVALID_ARG, "N < 0");
-  if (coeff && (D < 1 || mode < 0 || mode >= D)) return set_error(ASH_ERR_INVALID_ARG, "mode outside [0, D)");
-  ZsubFit fit{};
-  fit.K = K;
-  fit.dmin = fit.dmax = deltas[0];
-  double G[3][3] = {};
-  for (int k = 0; k < K; ++k) {
-    const double d = deltas[k], x[3] = {1.0, d, d * d};
-    fit.delta[k] = d;
-    fit.dmin = d < fit.dmin ? d : fit.dmin;
-    fit.dmax = d > fit.dmax ? d : fit.dmax;
-    for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j) G[i][j] += x[i] * x[j];
-  }
-  // (X^T X)^-1 by cofactors; fewer than three distinct offsets make it singular
-  const double det = G[0][0] * (G[1][1] * G[2][2] - G[1][2] * G[2][1]) -
-                     G[0][1] * (G[1][0] * G[2][2] - G[1][2] * G[2][0]) +
-                     G[0][2] * (G[1][0] * G[2][1] - G[1][1] * G[2][0]);
-  const double scale = G[0][0] * G[1][1] * G[2][2];
-  if (!(fabs(det) > 1e-12 * scale)) return set_error(ASH_ERR_INVALID_ARG, "need three distinct offsets");
-  double Gi[3][3];
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) {
-      const int i1 = (j + 1) % 3, i2 = (j + 2) % 3, j1 = (i + 1) % 3, j2 = (i + 2) % 3;
-      Gi[i][j] = (G[i1][j1] * G[i2][j2] - G[i1][j2] * G[i2][j1]) / det;
-    }
-  for (int r = 0; r < 3; ++r)
-    for (int k = 0; k < K; ++k) {
-      const double d = deltas[k], x[3] = {1.0, d, d * d};
-      fit.P[r][k] = Gi[r][0] * x[0] + Gi[r][1] * x[1] + Gi[r][2] * x[2];
-    }
-  if (injected_failure()) return set_error(ASH_ERR_INJECTED, "injected failure");
-  if (N == 0) return ASH_OK;
-  k_zsub_estimate<<<(N + 255) / 256, 256, 0, as_stream(stream)>>>(intensity, N, fit, delta_star, coeff, D, mode);
-  ASH_CUDA(cudaGetLastError());
-  return ASH_OK;
-}
 
-ash_status ash_cg_refine(ash_hologram* h, float* phase, const float* t, int iters, float theta, float* loss_out,
-                         void* stream) {
-  if (!h || !phase || !t) return set_error(ASH_ERR_INVALID_ARG, "NULL argument");
-  if (iters < 0 || iters > kCgMaxIters) return set_error(ASH_ERR_INVALID_ARG, "iters outside [0, %d]", kCgMaxIters);
-  if (!(theta > 0.0f && theta <= 3.2f)) return set_error(ASH_ERR_INVALID_ARG, "theta outside (0, 3.2]");
-  if (injected_failure()) return set_error(ASH_ERR_INJECTED, "injected failure");
-  cudaStream_t s = as_stream(stream);
-  const size_t M = (size_t)h->g.nx * h->g.ny;
-  double init[kCgSlots] = {};
-  init[kCgTheta] = theta;
-  ASH_CUDA(cudaMemcpyAsync(h->cg_phase, phase, M * 4, cudaMemcpyDeviceToDevice, s));
-  ASH_CUDA(cudaMemcpyAsync(h->cg_t, t, (size_t)h->g.N * 4, cudaMemcpyDeviceToDevice, s));
-  ASH_CUDA(cudaMemcpyAsync(h->cg_scal, init, sizeof init, cudaMemcpyHostToDevice, s));
-  if (iters >= 1) {
-    auto it = h->graphs.find(-iters);
-    cudaGraphExec_t exec = nullptr;
-    if (it != h->graphs.end()) {
-      exec = it->second;
-    } else {
-      cudaGraph_t graph = nullptr;
-      ASH_CUDA(cudaStreamBeginCapture(h->capture, cudaStreamCaptureModeThreadLocal));
-      ash_status st = enqueue_cg_body(h, iters, h->capture);
-      cudaError_t ce = cudaStreamEndCapture(h->capture, &graph);
-      if (st != ASH_OK) {
-        if (graph) cudaGraphDestroy(graph);
-        return st;
-      }
-      if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
-      ce = cudaGraphInstantiate(&exec, graph, 0);
-      cudaGraphDestroy(graph);
-      if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
-      h->graphs[-iters] = exec;
-    }
-    ASH_CUDA(cudaGraphLaunch(exec, s));
-  } else {
-    ash_status st = enqueue_cg_body(h, 0, s);
-    if (st != ASH_OK) return st;
-  }
-  ASH_CUDA(cudaMemcpyAsync(phase, h->cg_phase, M * 4, cudaMemcpyDeviceToDevice, s));
-  if (loss_out) ASH_CUDA(cudaMemcpyAsync(loss_out, h->cg_loss, (size_t)(iters + 1) * 4, cudaMemcpyDeviceToDevice, s));
-  return ASH_OK;
-}
 
 ash_status ash_adjoint(ash_hologram* h, const float* y, float* g, float* phase_out, void* stream) {
   if (!h || !y) return set_error(ASH_ERR_INVALID_ARG, "NULL argument");

@@ -102,6 +102,15 @@ bool consume_injected_failure();
 // capture it into a graph of their own (the batched form's standalone
 // members).
 ash_status wgs_body(ash_hologram* h, int iters, cudaStream_t s);
+// The transforms and the coefficient images of a handle, enqueued on `s`
+// (for the translation units of the loops built on them).
+ash_status forward_enqueue(ash_hologram* h, int source, const float* phase, const float2* field, float2* E,
+                           cudaStream_t s);
+ash_status adjoint_enqueue(ash_hologram* h, const float2* y, float2* g_out, float* phase_out, const float* phase_in,
+                           float* dphase, int epilogue, cudaStream_t s);
+cudaError_t coeff_images_enqueue(ash_hologram* h, cudaStream_t s);
+// CG workspace: fp64 scalar slots, reduction partials, iterations per call.
+constexpr int kCgSlots = 13, kCgRedBlocks = 512, kCgMaxIters = 1024;
 
 inline HoloView view_of(const ash_hologram* h) {
   HoloView v{};
