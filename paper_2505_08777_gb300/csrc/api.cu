@@ -152,7 +152,7 @@ bool use_tc_adj(const ash_hologram* h) {
   return h->variant == 2 || (h->tc_na == 1 && h->g.N >= kTcAdjMinSpots);
 }
 // The coefficient-gradient moments on the tensor cores need one K-atom,
-// D <= 12 and a polynomial basis of degree <= 4 in x (the row polynomials);
+// D <= 12 and a polynomial basis of total degree <= 4 (the tile polynomials);
 // from N = 64, as the forward whose structure they share.
 bool use_tc_grad(const ash_hologram* h) {
   if (!h->tgrad_ok || h->variant == 1) return false;
@@ -166,8 +166,8 @@ TcGradParams tc_grad_params(const ash_hologram* h, const float2* gE, float* dC) 
   p.czs = h->czs;
   p.rot = h->rot;
   p.fimg = h->fimg;
-  p.zrow = h->zrow;
-  p.npow = h->tgrad_npow;
+  p.tpoly = h->tpoly;
+  p.ord = h->tgrad_ord;
   p.gE = gE;
   p.sched = h->tgrad;
   p.begin = h->tgrad_begin;
@@ -552,12 +552,12 @@ ash_status create_impl(ash_hologram** out, int nx, int ny, const float* amp, int
       const long long ulo = (long long)b * f.nq;
       tfwd_spans.push_back(make_int2(tc_owner(tfwd_begin.data(), f.G, ulo), tc_owner(tfwd_begin.data(), f.G, ulo + f.nq - 1)));
     }
-    int npow = 2;
+    int ord = 1;
     if (spec)
-      for (const MonoTerm& m : spec->terms) npow = m.px + 1 > npow ? m.px + 1 : npow;
-    if (spec && h->tc_na == 1 && D <= kTcGradMaxModes && npow <= kTcGradMaxPow) {
-      h->tgrad_npow = npow;
-      ce = tc_grad_prepare(npow, D, &h->li.tc_grad_ctas_per_sm);
+      for (const MonoTerm& m : spec->terms) ord = m.px + m.py > ord ? m.px + m.py : ord;
+    if (spec && h->tc_na == 1 && D <= kTcGradMaxModes && ord <= kTcGradMaxOrd) {
+      h->tgrad_ord = ord;
+      ce = tc_grad_prepare(ord, D, &h->li.tc_grad_ctas_per_sm);
       if (ce != cudaSuccess) return fail(cuda_fail(ce, "tensor-core moment pass preparation"));
       h->tgrad_ok = true;
       TcFwdSched& m = h->tgrad;
@@ -608,7 +608,7 @@ ash_status create_impl(ash_hologram** out, int nx, int ny, const float* amp, int
     if ((st = ws(h, &h->tadj_groups, tadj_groups.size() + 1)) != ASH_OK) return fail(st);
   }
   if (h->tgrad_ok) {
-    if ((st = ws(h, &h->zrow, tc_zrow_floats(g, h->tgrad_npow))) != ASH_OK) return fail(st);
+    if ((st = ws(h, &h->tpoly, tc_tpoly_floats(g, h->tgrad_ord))) != ASH_OK) return fail(st);
     if ((st = ws(h, &h->tgrad_part, (size_t)h->tgrad.G * 2 * kTcRows * tc_grad_dp(D))) != ASH_OK) return fail(st);
     if ((st = ws(h, &h->tgrad_begin, tgrad_begin.size())) != ASH_OK) return fail(st);
     if ((st = ws(h, &h->tgrad_spans, tgrad_spans.size())) != ASH_OK) return fail(st);
@@ -682,7 +682,7 @@ ash_status create_impl(ash_hologram** out, int nx, int ny, const float* amp, int
                                   cudaMemcpyHostToDevice, s));
       CREATE_CUDA(cudaMemcpyAsync(h->tgrad_spans, tgrad_spans.data(), tgrad_spans.size() * sizeof(int2),
                                   cudaMemcpyHostToDevice, s));
-      CREATE_CUDA(tc_build_row_poly(g, h->terms, h->term_off, h->tgrad_npow, h->zrow, s));
+      CREATE_CUDA(tc_build_tile_poly(g, h->terms, h->term_off, h->tgrad_ord, h->tpoly, s));
     }
     // pixels outside the grid stay 0 in every nearfield image
     CREATE_CUDA(cudaMemsetAsync(h->fimg, 0, tc_fimg_float4s(g) * sizeof(float4), s));

@@ -55,8 +55,8 @@ struct ash_hologram {
   long long* tgrad_begin = nullptr;  // [tgrad.G + 1]
   int2* tgrad_spans = nullptr;       // [tgrad.nb] first and last CTA meeting each spot block
   float* tgrad_part = nullptr;  // [tgrad.G][2][128][DC]
-  int tgrad_npow = 0;           // powers of the basis row polynomials
-  float* zrow = nullptr;        // row polynomials of the basis per chunk
+  int tgrad_ord = 0;            // total degree of the basis polynomials
+  float* tpoly = nullptr;       // tile polynomials of the basis
   float2* split = nullptr;
   float* gradc_partial = nullptr;
   float2* E = nullptr;

@@ -10,51 +10,54 @@ namespace {
 
 // --- coefficient-gradient moments -----------------------------------------------
 
-// Row polynomials of the basis: along the 32 pixels of one row of a tile,
-// x = x_c + s u with u = (col - 15.5) / 16, so a basis polynomial
-// sum coef x^a y^b is sum_k a_k u^k, a_k = sum coef y^b binom(a, k) x_c^(a-k)
-// s^k, exact in fp64 and rounded once. One thread per (chunk, row, mode);
-// zrow[chunk][row][k][DP], modes D..DP-1 and powers beyond a term's a are 0.
-__global__ void k_tc_row_poly(const Geometry G, const MonoTerm* __restrict__ terms, const int* __restrict__ term_off,
-                              int npow, int DP, float* __restrict__ zrow) {
+// Tile polynomials of the basis: over a 32 x 32 tile, x = x_c + s u and
+// y = y_c + s v with u = (col - 15.5) / 16, v = (row - 15.5) / 16 and
+// s = 16 / R, so a basis polynomial sum coef x^a y^b is
+// sum_{k + l <= ORD} b_kl u^k v^l with
+// b_kl = sum coef binom(a, k) x_c^(a-k) s^k binom(b, l) y_c^(b-l) s^l,
+// exact in fp64 and rounded once. One thread per (tile, (k, l), mode);
+// tpoly[tile][pair][DP], pairs in the order k = 0..ORD, l = 0..ORD-k; modes
+// D..DP-1 are 0.
+__global__ void k_tc_tile_poly(const Geometry G, const MonoTerm* __restrict__ terms, const int* __restrict__ term_off,
+                               int ord, int DP, float* __restrict__ tpoly) {
+  const int npair = (ord + 1) * (ord + 2) / 2;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long nq = (long long)G.T * kTcChunksPerTile;
-  if (e >= nq * 2 * DP) return;
+  if (e >= (long long)G.T * npair * DP) return;
   const int d = (int)(e % DP);
-  const int hr = (int)((e / DP) % 2);
-  const long long qc = e / (2 * DP);
-  const TcPixel px = tc_pixel(G, qc, 32 * hr);   // column 0 of the row
+  const int pr = (int)((e / DP) % npair);
+  const int tile = (int)(e / ((long long)DP * npair));
+  int k = 0, l = pr;
+  while (l > ord - k) {
+    l -= ord - k + 1;
+    ++k;
+  }
   const double R = 0.5 * (double)min(G.nx, G.ny);
   const double cx = 0.5 * (double)(G.nx - 1), cy = 0.5 * (double)(G.ny - 1);
-  const double xc = ((double)px.i + 15.5 - cx) / R, sc = 16.0 / R, y = ((double)px.j - cy) / R;
-  double a[kTcGradMaxPow] = {};
+  const double xc = ((double)((tile % G.tiles_x) * kTileX) + 15.5 - cx) / R;
+  const double yc = ((double)((tile / G.tiles_x) * kTileY) + 15.5 - cy) / R;
+  const double sc = 16.0 / R;
+  double acc = 0.0;
   if (d < G.D) {
-    for (int k = term_off[d]; k < term_off[d + 1]; ++k) {
-      const MonoTerm m = terms[k];
-      double yb = 1.0;
-      for (int b = 0; b < m.py; ++b) yb *= y;
-      // (x_c + s u)^a = sum_k binom(a, k) x_c^(a - k) s^k u^k
-      double binom = 1.0;
-      for (int kk = 0; kk <= m.px && kk < kTcGradMaxPow; ++kk) {
-        double xp = 1.0, sp = 1.0;
-        for (int r = 0; r < m.px - kk; ++r) xp *= xc;
-        for (int r = 0; r < kk; ++r) sp *= sc;
-        a[kk] += m.coef * yb * binom * xp * sp;
-        binom = binom * (double)(m.px - kk) / (double)(kk + 1);
-      }
+    for (int t = term_off[d]; t < term_off[d + 1]; ++t) {
+      const MonoTerm m = terms[t];
+      if (k > m.px || l > m.py) continue;
+      // binom(a, k) x_c^(a-k) s^k and binom(b, l) y_c^(b-l) s^l
+      double fx = 1.0, fy = 1.0;
+      for (int r = 0; r < k; ++r) fx = fx * (double)(m.px - r) / (double)(r + 1) * sc;
+      for (int r = 0; r < m.px - k; ++r) fx *= xc;
+      for (int r = 0; r < l; ++r) fy = fy * (double)(m.py - r) / (double)(r + 1) * sc;
+      for (int r = 0; r < m.py - l; ++r) fy *= yc;
+      acc += m.coef * fx * fy;
     }
   }
-  float* dst = zrow + ((size_t)qc * 2 + hr) * npow * DP + d;
-  for (int kk = 0; kk < npow; ++kk) dst[(size_t)kk * DP] = (float)a[kk];
+  tpoly[((size_t)tile * npair + pr) * DP + d] = (float)acc;
 }
 
-// Shared memory of the moment kernel: A (spot block), B ring, and a ring of
-// [f (64 pixels) | row polynomials (2 rows x NPOW x DP)] slots.
-template <int NPOW, int DP>
+// Shared memory of the moment kernel: A (spot block), B ring and f ring.
 struct TcGradShape {
   static constexpr int NBB = 4, NF = 4;
-  static constexpr uint32_t A_BYTES = 16384, B_BYTES = 8192, F_BYTES = 512, Z_BYTES = 2 * NPOW * DP * 4;
-  static constexpr uint32_t FSLOT = F_BYTES + Z_BYTES;
+  static constexpr uint32_t A_BYTES = 16384, B_BYTES = 8192, F_BYTES = 512;
+  static constexpr uint32_t FSLOT = F_BYTES;
   static constexpr int NBARS = 3 + NBB + NF;
   static constexpr size_t SMEM = 1024 + A_BYTES + NBB * B_BYTES + NF * FSLOT + NBARS * 12 + 8 + 32;
 };
@@ -63,13 +66,16 @@ struct TcGradShape {
 // (paper Methods, gradients through the kernels). With C_n . Z_m = 2 pi base
 // + x (x the local phase from the tensor core) and w = conj(gE_n exp(+i 2 pi
 // base)), constant over a tile, each term adds q Z_dm with q = Im(w f_m
-// exp(-i x)). Along a row of 32 pixels Z_dm = sum_k a_dk u^k (u the pixel's
-// column offset, a compile-time constant here), so thread t (spot t of the
-// block) accumulates the NPOW power moments sum q u^k of the row and adds
-// sum_k a_dk (moment k) to its D gradients at the row's end.
-template <int NPOW, int DP>
+// exp(-i x)). Over a tile Z_dm = sum_{k + l <= ORD} b_dkl u^k v^l (u, v the
+// pixel's column and row offsets), so thread t (spot t of the block)
+// accumulates along each row the power moments P_k = sum q u^k (u^k
+// compile-time constants here), folds them into the tile moments
+// Q_kl += v^l P_k at the row's end, and adds sum_kl b_dkl Q_kl to its D
+// gradients at the tile's end.
+template <int ORD, int DP>
 __global__ void __launch_bounds__(kTcThreads, 4) k_tc_gradc(const TcGradParams p) {
-  using S = TcGradShape<NPOW, DP>;
+  using S = TcGradShape;
+  constexpr int NPOW = ORD + 1, NPAIR = (ORD + 1) * (ORD + 2) / 2;
   constexpr int NA = 1, NBB = S::NBB, NF = S::NF, NBARS = S::NBARS;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = tc_smem_base(smem_raw);
@@ -112,10 +118,9 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_tc_gradc(const TcGradParams p
   auto load_f = [&](int c, int q) {
     const int slot = c % NF;
     uint8_t* dst = sFZ + slot * S::FSLOT;
-    mbar_expect_tx(&ffull[slot], S::F_BYTES + S::Z_BYTES);
+    mbar_expect_tx(&ffull[slot], S::F_BYTES);
     ++armed[2 + NBB + slot];
     bulk_g2s(dst, p.fimg + (size_t)q * 32, S::F_BYTES, &ffull[slot]);
-    bulk_g2s(dst + S::F_BYTES, p.zrow + (size_t)q * 2 * NPOW * DP, S::Z_BYTES, &ffull[slot]);
   };
   auto next_q = [&](int q) { return q + 1 == nq ? 0 : q + 1; };
   auto issue_upto = [&](int upto, int released) -> bool {
@@ -165,9 +170,11 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_tc_gradc(const TcGradParams p
     ok = issue_upto(1, -1);
   }
 
-  float dc[DP];
+  float dc[DP], Q[NPAIR];
 #pragma unroll
   for (int d = 0; d < DP; ++d) dc[d] = 0.0f;
+#pragma unroll
+  for (int k = 0; k < NPAIR; ++k) Q[k] = 0.0f;
   float2 gh = make_float2(0.0f, 0.0f), wr2 = gh, wi2 = gh;
   int b = b0, q = q0;
 
@@ -187,7 +194,9 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_tc_gradc(const TcGradParams p
     // buffer is released once both are in registers
     const uint32_t taddr = tmem + tlane + (uint32_t)((c & 1) * kTcChunk);
     const float4* f = reinterpret_cast<const float4*>(sFZ + (c % NF) * S::FSLOT);
-    const float4* a4 = reinterpret_cast<const float4*>(sFZ + (c % NF) * S::FSLOT + S::F_BYTES);
+    // rows 4h + 2 half and 4h + 2 half + 1 of the tile (chunk w = 2h + half)
+    const int wq = q % kTcChunksPerTile;
+    const float vr0 = ((float)(4 * (wq >> 1) + 2 * (wq & 1)) - 15.5f) * 0.0625f;
     auto row = [&](const uint32_t (&x)[2][16], int hr) {
       float P[NPOW];
 #pragma unroll
@@ -215,15 +224,19 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_tc_gradc(const TcGradParams p
           p1 *= u1;
         }
       }
+      // Q_kl += v^l P_k (v the row's offset)
+      const float v = vr0 + 0.0625f * (float)hr;
+      float vp[NPOW];
+      vp[0] = 1.0f;
+#pragma unroll
+      for (int e = 1; e < NPOW; ++e) vp[e] = vp[e - 1] * v;
+      int idx = 0;
 #pragma unroll
       for (int e = 0; e < NPOW; ++e) {
 #pragma unroll
-        for (int j = 0; j < DP / 4; ++j) {
-          const float4 av = a4[(hr * NPOW + e) * (DP / 4) + j];
-          dc[4 * j] = fmaf(av.x, P[e], dc[4 * j]);
-          dc[4 * j + 1] = fmaf(av.y, P[e], dc[4 * j + 1]);
-          dc[4 * j + 2] = fmaf(av.z, P[e], dc[4 * j + 2]);
-          dc[4 * j + 3] = fmaf(av.w, P[e], dc[4 * j + 3]);
+        for (int l = 0; l + e < NPOW; ++l) {
+          Q[idx] = fmaf(vp[l], P[e], Q[idx]);
+          ++idx;
         }
       }
     };
@@ -254,6 +267,22 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_tc_gradc(const TcGradParams p
     qb = next_q(qb);
     qf = next_q(qf);
     if (active) row(x, 1);
+    if (active && (q % kTcChunksPerTile == kTcChunksPerTile - 1 || c == nc - 1)) {
+      // end of a tile (or of the range): dC_d += sum_kl b_dkl Q_kl
+      const float4* tb = reinterpret_cast<const float4*>(p.tpoly + (size_t)(q / kTcChunksPerTile) * NPAIR * DP);
+#pragma unroll
+      for (int k = 0; k < NPAIR; ++k) {
+#pragma unroll
+        for (int j = 0; j < DP / 4; ++j) {
+          const float4 bv = __ldg(tb + k * (DP / 4) + j);
+          dc[4 * j] = fmaf(bv.x, Q[k], dc[4 * j]);
+          dc[4 * j + 1] = fmaf(bv.y, Q[k], dc[4 * j + 1]);
+          dc[4 * j + 2] = fmaf(bv.z, Q[k], dc[4 * j + 2]);
+          dc[4 * j + 3] = fmaf(bv.w, Q[k], dc[4 * j + 3]);
+        }
+        Q[k] = 0.0f;
+      }
+    }
     if (wrap || c == nc - 1) {
       // end of spot block b in this range
       const bool whole = (long long)b * nq >= u0 && (long long)(b + 1) * nq <= u1;
@@ -306,16 +335,16 @@ __global__ void k_tc_gradc_reduce(const TcGradParams p) {
 
 }  // namespace
 
-template <int NPOW, int DP>
+template <int ORD, int DP>
 static cudaError_t launch_np(const TcGradParams& p, cudaStream_t s) {
-  k_tc_gradc<NPOW, DP><<<p.sched.G, kTcThreads, TcGradShape<NPOW, DP>::SMEM, s>>>(p);
+  k_tc_gradc<ORD, DP><<<p.sched.G, kTcThreads, TcGradShape::SMEM, s>>>(p);
   return cudaGetLastError();
 }
 
-template <int NPOW, int DP>
+template <int ORD, int DP>
 static cudaError_t prepare_np(int* n) {
-  const void* k = (const void*)k_tc_gradc<NPOW, DP>;
-  constexpr int smem = (int)TcGradShape<NPOW, DP>::SMEM;
+  const void* k = (const void*)k_tc_gradc<ORD, DP>;
+  constexpr int smem = (int)TcGradShape::SMEM;
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
   if ((e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared)))
@@ -323,41 +352,41 @@ static cudaError_t prepare_np(int* n) {
   return tc_ctas_per_sm(k, smem, 2 * kTcChunk, n);
 }
 
-// Instantiations: NPOW in 2..5, DP in {4, 8, 12}.
-template <int NPOW>
+// Instantiations: ORD in 1..4, DP in {4, 8, 12}.
+template <int ORD>
 static cudaError_t dispatch_dp(int DP, bool prep, const TcGradParams* p, int* n, cudaStream_t s) {
   switch (DP) {
-    case 4: return prep ? prepare_np<NPOW, 4>(n) : launch_np<NPOW, 4>(*p, s);
-    case 8: return prep ? prepare_np<NPOW, 8>(n) : launch_np<NPOW, 8>(*p, s);
-    case 12: return prep ? prepare_np<NPOW, 12>(n) : launch_np<NPOW, 12>(*p, s);
+    case 4: return prep ? prepare_np<ORD, 4>(n) : launch_np<ORD, 4>(*p, s);
+    case 8: return prep ? prepare_np<ORD, 8>(n) : launch_np<ORD, 8>(*p, s);
+    case 12: return prep ? prepare_np<ORD, 12>(n) : launch_np<ORD, 12>(*p, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-static cudaError_t dispatch(int npow, int DP, bool prep, const TcGradParams* p, int* n, cudaStream_t s) {
-  switch (npow) {
+static cudaError_t dispatch(int ord, int DP, bool prep, const TcGradParams* p, int* n, cudaStream_t s) {
+  switch (ord) {
+    case 1: return dispatch_dp<1>(DP, prep, p, n, s);
     case 2: return dispatch_dp<2>(DP, prep, p, n, s);
     case 3: return dispatch_dp<3>(DP, prep, p, n, s);
     case 4: return dispatch_dp<4>(DP, prep, p, n, s);
-    case 5: return dispatch_dp<5>(DP, prep, p, n, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t tc_grad_prepare(int npow, int D, int* ctas_per_sm) {
-  return dispatch(npow, tc_grad_dp(D), true, nullptr, ctas_per_sm, nullptr);
+cudaError_t tc_grad_prepare(int ord, int D, int* ctas_per_sm) {
+  return dispatch(ord, tc_grad_dp(D), true, nullptr, ctas_per_sm, nullptr);
 }
 
-cudaError_t tc_build_row_poly(const Geometry& g, const MonoTerm* terms, const int* term_off, int npow, float* zrow,
-                              cudaStream_t s) {
+cudaError_t tc_build_tile_poly(const Geometry& g, const MonoTerm* terms, const int* term_off, int ord, float* tpoly,
+                               cudaStream_t s) {
   const int DP = tc_grad_dp(g.D);
-  const long long n = (long long)g.T * kTcChunksPerTile * 2 * DP;
-  k_tc_row_poly<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, terms, term_off, npow, DP, zrow);
+  const long long n = (long long)g.T * tc_grad_pairs(ord) * DP;
+  k_tc_tile_poly<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, terms, term_off, ord, DP, tpoly);
   return cudaGetLastError();
 }
 
 cudaError_t tc_launch_gradc(const TcGradParams& p, bool split, cudaStream_t s) {
-  cudaError_t e = dispatch(p.npow, tc_grad_dp(p.g.D), false, &p, nullptr, s);
+  cudaError_t e = dispatch(p.ord, tc_grad_dp(p.g.D), false, &p, nullptr, s);
   if (e != cudaSuccess || !split) return e;
   k_tc_gradc_reduce<<<dim3(p.sched.nb, kTcRows / 32, p.g.D), dim3(32, 32), 0, s>>>(p);
   return cudaGetLastError();

@@ -202,13 +202,15 @@ struct TcFwdParams {
 };
 
 // Coefficient-gradient moments on the tensor cores (one K-atom, D <= 12,
-// polynomial basis of degree <= 4 in x): spot-stationary like the forward.
-// zrow holds, per 64-pixel chunk, the row polynomials of its two rows:
-// [2 rows][NPOW powers][DP modes] floats, DP = D rounded up to 4.
-constexpr int kTcGradMaxModes = 12, kTcGradMaxPow = 5;
+// polynomial basis of total degree ORD <= 4): spot-stationary like the
+// forward. tpoly holds, per tile, the basis as polynomials in the pixel's
+// column and row offsets: [pairs (k, l), k + l <= ORD][DP modes] floats,
+// DP = D rounded up to 4.
+constexpr int kTcGradMaxModes = 12, kTcGradMaxOrd = 4;
 __host__ __device__ constexpr int tc_grad_dp(int D) { return (D + 3) & ~3; }
-inline size_t tc_zrow_floats(const Geometry& g, int npow) {
-  return (size_t)g.T * kTcChunksPerTile * 2 * npow * tc_grad_dp(g.D);
+__host__ __device__ constexpr int tc_grad_pairs(int ord) { return (ord + 1) * (ord + 2) / 2; }
+inline size_t tc_tpoly_floats(const Geometry& g, int ord) {
+  return (size_t)g.T * tc_grad_pairs(ord) * tc_grad_dp(g.D);
 }
 struct TcGradParams {
   Geometry g;
@@ -216,19 +218,19 @@ struct TcGradParams {
   const float* czs;
   const float2* rot;
   const float4* fimg;
-  const float* zrow;
+  const float* tpoly;
   const float2* gE;       // [N] dL/dE
   TcFwdSched sched;       // units (spot block, pixel chunk), as the forward
   const long long* begin; // [G + 1]
   const int2* spans;      // [nb] first and last CTA meeting each spot block (host-tabulated)
-  int npow;               // powers of the row polynomials (2..5)
+  int ord;                // total degree of the basis polynomials (1..4)
   float* dC;              // [N][D] output
   float* part;            // [G][2][128][DP] partial sums of spot blocks split between CTAs
   unsigned* err;
 };
-cudaError_t tc_grad_prepare(int npow, int D, int* ctas_per_sm);
-cudaError_t tc_build_row_poly(const Geometry& g, const MonoTerm* terms, const int* term_off, int npow, float* zrow,
-                              cudaStream_t s);
+cudaError_t tc_grad_prepare(int ord, int D, int* ctas_per_sm);
+cudaError_t tc_build_tile_poly(const Geometry& g, const MonoTerm* terms, const int* term_off, int ord, float* tpoly,
+                               cudaStream_t s);
 cudaError_t tc_launch_gradc(const TcGradParams& p, bool split, cudaStream_t s);   // kernel (+ reduction of split blocks)
 // Resident CTAs per SM from registers, shared memory and TMEM columns.
 cudaError_t tc_ctas_per_sm(const void* fn, size_t smem, int tmem_cols, int* out);
