@@ -65,8 +65,9 @@ struct TcGradShape {
 // S_nd = sum_m Z_dm f_m exp(-i C_n . Z_m) and dL/dC_nd = Im(conj(gE_n) S_nd)
 // (paper Methods, gradients through the kernels). With C_n . Z_m = 2 pi base
 // + x (x the local phase from the tensor core) and w = conj(gE_n exp(+i 2 pi
-// base)), constant over a tile, each term adds q Z_dm with q = Im(w f_m
-// exp(-i x)). Over a tile Z_dm = sum_{k + l <= ORD} b_dkl u^k v^l (u, v the
+// base)) = |w| exp(i alpha), constant over a tile, each term adds q Z_dm
+// with q = Im(w f_m exp(-i x)) = |w| (Im f cos(x - alpha) - Re f sin(x -
+// alpha)); |w| is applied once per tile. Over a tile Z_dm = sum_{k + l <= ORD} b_dkl u^k v^l (u, v the
 // pixel's column and row offsets), so thread t (spot t of the block)
 // accumulates along each row the power moments P_k = sum q u^k (u^k
 // compile-time constants here), folds them into the tile moments
@@ -175,7 +176,8 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_tc_gradc(const TcGradParams p
   for (int d = 0; d < DP; ++d) dc[d] = 0.0f;
 #pragma unroll
   for (int k = 0; k < NPAIR; ++k) Q[k] = 0.0f;
-  float2 gh = make_float2(0.0f, 0.0f), wr2 = gh, wi2 = gh;
+  float2 gh = make_float2(0.0f, 0.0f), nalpha2 = gh;
+  float wmag = 0.0f;
   int b = b0, q = q0;
 
   for (int c = 0; c < nc; ++c) {
@@ -186,9 +188,11 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_tc_gradc(const TcGradParams p
     if (c == 0 || q % kTcChunksPerTile == 0) {
       // new tile: w = conj(gE exp(+i 2 pi base(n, tile)))
       const float2 rt = n < N ? __ldg(p.rot + (size_t)(q / kTcChunksPerTile) * N + n) : make_float2(0.0f, 0.0f);
+      // w = |w| exp(i alpha): q = Im(w f exp(-i x)) = |w| Im(f exp(-i (x - alpha)))
       const float wr = gh.x * rt.x - gh.y * rt.y, wi = -(gh.x * rt.y + gh.y * rt.x);
-      wr2 = make_float2(wr, wr);
-      wi2 = make_float2(wi, wi);
+      const float alpha = atan2f(wi, wr);
+      nalpha2 = make_float2(-alpha, -alpha);
+      wmag = sqrtf(wr * wr + wi * wi);
     }
     // row 0 of the chunk is TMEM columns 0-31, row 1 columns 32-63; the
     // buffer is released once both are in registers
@@ -204,15 +208,13 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_tc_gradc(const TcGradParams p
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
         const float4 fq = f[16 * hr + k];
-        const float2 fr = make_float2(fq.x, fq.y), fi = make_float2(fq.z, fq.w), nfr = make_float2(-fq.x, -fq.y);
+        const float2 fi = make_float2(fq.z, fq.w), nfr = make_float2(-fq.x, -fq.y);
         float2 sn, cs;
-        sincos2_mixed<ASH_POLY_GRAD>(16 * hr + k,
-                      make_float2(__uint_as_float(x[k / 8][2 * (k % 8)]), __uint_as_float(x[k / 8][2 * (k % 8) + 1])),
-                      sn, cs);
-        // p = f exp(-i x) = (fr cs + fi sn) + i (fi cs - fr sn); q = Im(w p)
-        const float2 pre = fma2(fr, cs, mul2(fi, sn));
-        const float2 pim = fma2(fi, cs, mul2(nfr, sn));
-        const float2 qv = fma2(wr2, pim, mul2(wi2, pre));
+        const float2 xv =
+            make_float2(__uint_as_float(x[k / 8][2 * (k % 8)]), __uint_as_float(x[k / 8][2 * (k % 8) + 1]));
+        sincos2_mixed<ASH_POLY_GRAD>(16 * hr + k, fma2(xv, make_float2(1.0f, 1.0f), nalpha2), sn, cs);
+        // q / |w| = Im(f exp(-i (x - alpha))) = fi cos - fr sin
+        const float2 qv = fma2(fi, cs, mul2(nfr, sn));
         // columns 2k, 2k + 1 of the row
         const float u0 = (2.0f * k - 15.5f) * 0.0625f, u1 = (2.0f * k + 1.0f - 15.5f) * 0.0625f;
         float p0 = 1.0f, p1 = 1.0f;
@@ -268,7 +270,9 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_tc_gradc(const TcGradParams p
     qf = next_q(qf);
     if (active) row(x, 1);
     if (active && (q % kTcChunksPerTile == kTcChunksPerTile - 1 || c == nc - 1)) {
-      // end of a tile (or of the range): dC_d += sum_kl b_dkl Q_kl
+      // end of a tile (or of the range): dC_d += |w| sum_kl b_dkl Q_kl
+#pragma unroll
+      for (int k = 0; k < NPAIR; ++k) Q[k] *= wmag;
       const float4* tb = reinterpret_cast<const float4*>(p.tpoly + (size_t)(q / kTcChunksPerTile) * NPAIR * DP);
 #pragma unroll
       for (int k = 0; k < NPAIR; ++k) {
