@@ -194,6 +194,17 @@ __device__ __forceinline__ void sincos2_poly(float2 x, float2& s, float2& c) {
 #define ASH_POLY_GRAD 1
 #endif
 template <int NUM>
+__device__ __forceinline__ void sin2_mixed(int k, float2 x, float2& s) {
+  if (NUM > 0 && (k * NUM) % 9 < NUM) {
+    float2 c;
+    sincos2_poly(x, s, c);   // the cosine's last step is dead code here
+  } else {
+    s.x = __sinf(x.x);
+    s.y = __sinf(x.y);
+  }
+}
+
+template <int NUM>
 __device__ __forceinline__ void sincos2_mixed(int k, float2 x, float2& s, float2& c) {
   if (NUM > 0 && (k * NUM) % 9 < NUM) {
     sincos2_poly(x, s, c);

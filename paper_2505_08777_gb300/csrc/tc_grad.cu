@@ -66,8 +66,9 @@ struct TcGradShape {
 // (paper Methods, gradients through the kernels). With C_n . Z_m = 2 pi base
 // + x (x the local phase from the tensor core) and w = conj(gE_n exp(+i 2 pi
 // base)) = |w| exp(i alpha), constant over a tile, each term adds q Z_dm
-// with q = Im(w f_m exp(-i x)) = |w| (Im f cos(x - alpha) - Re f sin(x -
-// alpha)); |w| is applied once per tile. Over a tile Z_dm = sum_{k + l <= ORD} b_dkl u^k v^l (u, v the
+// with q = Im(w f_m exp(-i x)) = |w| A_m sin(phi_m + alpha - x) (the
+// nearfield image holds f = A exp(i phi) as (A, phi)); |w| is applied once
+// per tile. Over a tile Z_dm = sum_{k + l <= ORD} b_dkl u^k v^l (u, v the
 // pixel's column and row offsets), so thread t (spot t of the block)
 // accumulates along each row the power moments P_k = sum q u^k (u^k
 // compile-time constants here), folds them into the tile moments
@@ -176,7 +177,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_tc_gradc(const TcGradParams p
   for (int d = 0; d < DP; ++d) dc[d] = 0.0f;
 #pragma unroll
   for (int k = 0; k < NPAIR; ++k) Q[k] = 0.0f;
-  float2 gh = make_float2(0.0f, 0.0f), nalpha2 = gh;
+  float2 gh = make_float2(0.0f, 0.0f), alpha2 = gh;
   float wmag = 0.0f;
   int b = b0, q = q0;
 
@@ -191,7 +192,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_tc_gradc(const TcGradParams p
       // w = |w| exp(i alpha): q = Im(w f exp(-i x)) = |w| Im(f exp(-i (x - alpha)))
       const float wr = gh.x * rt.x - gh.y * rt.y, wi = -(gh.x * rt.y + gh.y * rt.x);
       const float alpha = atan2f(wi, wr);
-      nalpha2 = make_float2(-alpha, -alpha);
+      alpha2 = make_float2(alpha, alpha);
       wmag = sqrtf(wr * wr + wi * wi);
     }
     // row 0 of the chunk is TMEM columns 0-31, row 1 columns 32-63; the
@@ -208,13 +209,14 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_tc_gradc(const TcGradParams p
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
         const float4 fq = f[16 * hr + k];
-        const float2 fi = make_float2(fq.z, fq.w), nfr = make_float2(-fq.x, -fq.y);
-        float2 sn, cs;
+        const float2 am = make_float2(fq.x, fq.y), ph = make_float2(fq.z, fq.w);
         const float2 xv =
             make_float2(__uint_as_float(x[k / 8][2 * (k % 8)]), __uint_as_float(x[k / 8][2 * (k % 8) + 1]));
-        sincos2_mixed<ASH_POLY_GRAD>(16 * hr + k, fma2(xv, make_float2(1.0f, 1.0f), nalpha2), sn, cs);
-        // q / |w| = Im(f exp(-i (x - alpha))) = fi cos - fr sin
-        const float2 qv = fma2(fi, cs, mul2(nfr, sn));
+        // q / |w| = Im(A exp(i phi) exp(-i (x - alpha))) = A sin(phi + alpha - x)
+        float2 sn;
+        sin2_mixed<ASH_POLY_GRAD>(16 * hr + k, fma2(xv, make_float2(-1.0f, -1.0f), fma2(ph, make_float2(1.0f, 1.0f), alpha2)),
+                                  sn);
+        const float2 qv = mul2(am, sn);
         // columns 2k, 2k + 1 of the row
         const float u0 = (2.0f * k - 15.5f) * 0.0625f, u1 = (2.0f * k + 1.0f - 15.5f) * 0.0625f;
         float p0 = 1.0f, p1 = 1.0f;

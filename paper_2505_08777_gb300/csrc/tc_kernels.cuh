@@ -129,8 +129,16 @@ static __global__ void k_tc_build_czs(const float* __restrict__ coeff, int N, co
     }
 }
 
-// Nearfield in tc layout from a phase (f = A exp(i phase)) or a complex
-// field, both in user layout; pixels outside the grid are 0.
+// A phase reduced to [-pi, pi] (the nearfield image's phases stay small,
+// so that phi - x keeps the accuracy of x).
+__device__ __forceinline__ float wrap_phase(float ph) {
+  return fmaf(-6.283185307179586f, rintf(ph * 0.15915494309189535f), ph);
+}
+
+// Nearfield in tc layout, as amplitude and phase: f = A exp(i phi) from a
+// phase or from a complex field (A = |f|, phi = arg f), both in user layout;
+// pixels outside the grid are 0. Chunk pixel pair p holds (A_2p, A_2p+1,
+// phi_2p, phi_2p+1).
 static __global__ void k_tc_field_img(const Geometry G, const float* __restrict__ amp_img,
                                       const float* __restrict__ phase, const float2* __restrict__ field,
                                       float* __restrict__ fimg) {
@@ -139,24 +147,21 @@ static __global__ void k_tc_field_img(const Geometry G, const float* __restrict_
   const long long qc = e / kTcChunk;
   const int r = (int)(e % kTcChunk);
   const TcPixel px = tc_pixel(G, qc, r);
-  float fr = 0.0f, fi = 0.0f;
+  float a = 0.0f, ph = 0.0f;
   if (px.i < G.nx && px.j < G.ny) {
     const size_t m = (size_t)px.j * G.nx + px.i;
     if (phase) {
-      float s, c;
-      sincosf(phase[m], &s, &c);
-      const float a = amp_img[px.img];
-      fr = a * c;
-      fi = a * s;
+      a = amp_img[px.img];
+      ph = wrap_phase(phase[m]);
     } else {
       const float2 f = field[m];
-      fr = f.x;
-      fi = f.y;
+      a = hypotf(f.x, f.y);
+      ph = (f.x == 0.0f && f.y == 0.0f) ? 0.0f : atan2f(f.y, f.x);
     }
   }
   float* q = fimg + ((size_t)qc * 32 + (r >> 1)) * 4;
-  q[r & 1] = fr;
-  q[2 + (r & 1)] = fi;
+  q[r & 1] = a;
+  q[2 + (r & 1)] = ph;
 }
 
 // rot[tile][n] = exp(+i 2 pi base(n, tile)): the per-(spot, tile) phase of
@@ -275,7 +280,7 @@ __device__ __forceinline__ void tc_range_end(uint64_t* bars, const uint32_t* arm
 }
 
 // Adjoint output of row r of chunk qc (in the pixel's user-layout slot and,
-// for kEpiFimg, in the tc-layout nearfield f = A exp(i arg g)).
+// for kEpiFimg, in the tc-layout nearfield f = A exp(i arg g) as (A, arg g)).
 __device__ __forceinline__ void tc_adjoint_epilogue(const TcAdjParams& p, long long qc, int r, float gr, float gi) {
   const Geometry& G = p.g;
   const TcPixel px = tc_pixel(G, qc, r);
@@ -285,11 +290,9 @@ __device__ __forceinline__ void tc_adjoint_epilogue(const TcAdjParams& p, long l
   adjoint_epilogue(p.out, (size_t)px.j * G.nx + px.i, gr, gi, a);
   if (p.out.epilogue & kEpiFimg) {
     const float ph = (gr == 0.0f && gi == 0.0f) ? 0.0f : atan2f(gi, gr);
-    float s, c;
-    sincosf(ph, &s, &c);
     float* q = reinterpret_cast<float*>(p.fimg + (size_t)qc * 32 + (r >> 1));
-    q[r & 1] = a * c;
-    q[2 + (r & 1)] = a * s;
+    q[r & 1] = a;
+    q[2 + (r & 1)] = ph;
   }
 }
 
@@ -646,7 +649,7 @@ __device__ __forceinline__ void tc_forward_range(const TcFwdParams& p, long long
     ok = issue_upto(1, -1);
   }
 
-  float2 A1 = make_float2(0.0f, 0.0f), A2 = A1, A3 = A1, A4 = A1;
+  float2 A1 = make_float2(0.0f, 0.0f), A2 = A1;   // sums of A cos(phi - x), A sin(phi - x)
   float er = 0.0f, ei = 0.0f;
   int b = b0, q = q0;                // spot block and pixel chunk of chunk c
   // chunks [0, c_rep) belong to full blocks, [c_rep, nc) to the replicated
@@ -693,21 +696,19 @@ __device__ __forceinline__ void tc_forward_range(const TcFwdParams& p, long long
 #pragma unroll
           for (int pp = 0; pp < 8; ++pp) {
             const float4 fq = f[8 * qq + pp];
-            const float2 fr = make_float2(fq.x, fq.y), fi = make_float2(fq.z, fq.w);
+            const float2 am = make_float2(fq.x, fq.y), ph = make_float2(fq.z, fq.w);
+            const float2 xv = make_float2(__uint_as_float(x[qq][2 * pp]), __uint_as_float(x[qq][2 * pp + 1]));
             float2 sn, cs;
-            sincos2_mixed<ASH_POLY_FWD>(8 * qq + pp,
-                          make_float2(__uint_as_float(x[qq][2 * pp]), __uint_as_float(x[qq][2 * pp + 1])), sn, cs);
-            // f exp(-i x) = (fr cs + fi sn) + i (fi cs - fr sn)
-            A1 = fma2(fr, cs, A1);
-            A2 = fma2(fi, sn, A2);
-            A3 = fma2(fi, cs, A3);
-            A4 = fma2(fr, sn, A4);
+            // f exp(-i x) = A exp(i (phi - x))
+            sincos2_mixed<ASH_POLY_FWD>(8 * qq + pp, fma2(xv, make_float2(-1.0f, -1.0f), ph), sn, cs);
+            A1 = fma2(am, cs, A1);
+            A2 = fma2(am, sn, A2);
           }
         }
         if (q % kTcChunksPerTile == kTcChunksPerTile - 1 || c == nc - 1) {
           // end of a tile: rotate by exp(-i 2 pi base(n, tile))
-          const float re = (A1.x + A1.y) + (A2.x + A2.y), im = (A3.x + A3.y) - (A4.x + A4.y);
-          A1 = A2 = A3 = A4 = make_float2(0.0f, 0.0f);
+          const float re = A1.x + A1.y, im = A2.x + A2.y;
+          A1 = A2 = make_float2(0.0f, 0.0f);
           if (n < N) {
             const float2 rt = __ldg(p.rot + (size_t)(q / kTcChunksPerTile) * N + n);
             er += re * rt.x + im * rt.y;
@@ -860,17 +861,14 @@ static __global__ void k_tc_field_img_batch(const TcFieldDesc* __restrict__ ds, 
   const int r = (int)(le % kTcChunk);
   const Geometry& G = d.g;
   const TcPixel px = tc_pixel(G, qc, r);
-  float fr = 0.0f, fi = 0.0f;
+  float a = 0.0f, ph = 0.0f;
   if (px.i < G.nx && px.j < G.ny) {
-    float sn, cs;
-    sincosf(d.phase[(size_t)px.j * G.nx + px.i], &sn, &cs);
-    const float a = d.amp_img[px.img];
-    fr = a * cs;
-    fi = a * sn;
+    a = d.amp_img[px.img];
+    ph = wrap_phase(d.phase[(size_t)px.j * G.nx + px.i]);
   }
   float* q = reinterpret_cast<float*>(d.fimg) + ((size_t)qc * 32 + (r >> 1)) * 4;
-  q[r & 1] = fr;
-  q[2 + (r & 1)] = fi;
+  q[r & 1] = a;
+  q[2 + (r & 1)] = ph;
 }
 
 }  // namespace ash
