@@ -182,8 +182,8 @@ __device__ __forceinline__ void sincos2_poly(float2 x, float2& s, float2& c) {
 // on the kernel's own FP32 work: ASH_POLY_FWD / _ADJ / _GRAD of 9. Measured
 // on GB300 (1024^2, D = 10): 2 / 9 in the tensor-core forward and adjoint
 // (5-9 % faster than 0 / 9; 3 / 9 and 4 / 9 gain less, 5 / 9 is slower),
-// 1 / 9 in the moment pass (its FP32 pipe also carries the moments: 1 % over
-// 0 / 9, 2 / 9 no better).
+// 0 / 9 in the moment pass (it needs one sine per pixel, not a sine and a
+// cosine, and its FP32 pipe also carries the moments: 1 / 9 is 5 % slower).
 #ifndef ASH_POLY_FWD
 #define ASH_POLY_FWD 2
 #endif
@@ -191,7 +191,7 @@ __device__ __forceinline__ void sincos2_poly(float2 x, float2& s, float2& c) {
 #define ASH_POLY_ADJ 2
 #endif
 #ifndef ASH_POLY_GRAD
-#define ASH_POLY_GRAD 1
+#define ASH_POLY_GRAD 0
 #endif
 template <int NUM>
 __device__ __forceinline__ void sin2_mixed(int k, float2 x, float2& s) {
