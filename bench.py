@@ -43,7 +43,7 @@ MAX_SM_MHZ = 2070.0
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
 # ncu capture of the named kernel on this workload; see profiles/. Reported as
 # roofline.traffic only for the kernel build these counters were taken on.
-NCU_TRAFFIC_BYTES = {"k_tc_forward<1>": 146.574592e6 + 3.318272e6, "k_tc_adjoint<1>": 151.150080e6 + 8.044544e6}
+NCU_TRAFFIC_BYTES = {"k_tc_forward<1>": 146.443008e6 + 3.285504e6, "k_tc_adjoint<1>": 151.223040e6 + 7.863296e6}
 
 
 def alu_terms_per_clk_per_sm():
