@@ -79,3 +79,37 @@ def test_gradient_only_for_requested_inputs():
     E = spot_field(h, phase)        # coefficients fixed
     (E.abs() ** 2).sum().backward()
     assert phase.grad is not None and torch.isfinite(phase.grad).all()
+
+
+def test_step_is_graph_capturable_and_bitwise_eager():
+    # every library call is stream-ordered and allocation-free, so a whole
+    # forward + backward captures as one CUDA graph; the kernels are
+    # deterministic, so a replay gives the eager gradients bit for bit
+    from paper_2505_08777_gb300.autograd import spot_field, spot_intensity_loss
+    p, h = _setup(seed=9, nx=96, ny=80, N=150)
+    ph = torch.from_numpy(p.phase0).cuda().requires_grad_(True)
+    C = torch.from_numpy(p.coeff).cuda().requires_grad_(True)
+    t = torch.from_numpy(p.target).cuda()
+
+    def step():
+        ph.grad = None if ph.grad is None else ph.grad.zero_()
+        C.grad = None if C.grad is None else C.grad.zero_()
+        loss = spot_intensity_loss(spot_field(h, ph, C), t)
+        loss.backward()
+        return loss.detach()
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            step()
+    torch.cuda.current_stream().wait_stream(side)
+    L_eager = step().clone()
+    g_ph, g_C = ph.grad.clone(), C.grad.clone()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        L_static = step()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(L_static, L_eager)
+    assert torch.equal(ph.grad, g_ph) and torch.equal(C.grad, g_C)
