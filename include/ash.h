@@ -309,7 +309,8 @@ ash_status ash_wgs_iterate(ash_hologram *h, float *phase, float *w, const float 
  *   dcoeff_nd = Im(conj(grad_E_n) S_nd), S_nd = sum_m Z_dm f_m K_nm
  *               (forward pass with D moments, tiles recomputed; the phases
  *               C_n . Z_m come from the tensor cores when the operand row
- *               fits one K-atom and D <= 12, else from the FMA pipe).
+ *               fits one K-atom, D <= 12 and the basis is a polynomial of
+ *               total degree <= 4, else from the FMA pipe).
  * The tensor-core moment pass overwrites the handle's nearfield image (no
  * other state of the handle changes).
  *   phase   device float[ny*nx];  grad_E device float[2*N];
@@ -395,7 +396,8 @@ ash_status ash_hologram_check(ash_hologram *h, void *stream);
 typedef struct ash_batch ash_batch;
 
 /* One hologram of a batch: same meaning as the ash_hologram_create
- * arguments; 1 <= D <= 12. */
+ * arguments; 1 <= D <= 12 for the members of the persistent group (see
+ * ash_batch_create_ex). */
 typedef struct {
   int nx, ny;
   const float *amp;     /* device float[ny*nx] */

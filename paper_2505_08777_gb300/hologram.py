@@ -217,7 +217,7 @@ class Hologram:
         return dict(zip(keys, list(out)))
 
     def set_variant(self, variant: int):
-        """0 = automatic, 1 = FMA-pipe kernels, 2 = tensor-core phase contraction (D <= 12)."""
+        """0 = automatic, 1 = FMA-pipe kernels, 2 = tensor-core phase contraction (D <= 21)."""
         _lib.check(self._lib.ash_set_kernel_variant(self._h, int(variant)), "ash_set_kernel_variant")
 
     def check(self, stream=None):
