@@ -366,6 +366,16 @@ ash_status ash_wgs_set_options(ash_hologram *h, float feedback, int fix_phase);
 int ash_wgs_launches(const ash_hologram *h, int iters);
 
 /*
+ * Kernel nodes of a graph the handle has captured and cached, counted when
+ * it was captured (kernels of embedded child graphs included): key = iters
+ * for the loop of ash_wgs_iterate(iters >= 2), key = -iters for that of
+ * ash_cg_refine(iters >= 1). Every kernel of those calls runs inside that
+ * graph. -1 if no graph is cached under key (none captured yet, or dropped
+ * by ash_set_kernel_variant / ash_wgs_set_options) or h is NULL.
+ */
+int ash_graph_kernels(const ash_hologram *h, int key);
+
+/*
  * Measurement helper: runs each kernel of one WGS iteration once on
  * `stream`, bracketed by CUDA events recorded on that stream, synchronises
  * it, and writes the durations in milliseconds to the host array ms_out[6]:
@@ -449,6 +459,11 @@ ash_status ash_batch_set_variant(ash_batch *b, int variant);
 
 /* Kernel launches one ash_batch_wgs call enqueues for `iters`; -1 if NULL. */
 int ash_batch_wgs_launches(const ash_batch *b, int iters);
+
+/* Kernel nodes of the graph ash_batch_wgs captured for `iters` (every
+ * kernel of the call; the graph is captured on its first call with that
+ * count); -1 if no such graph is cached or b is NULL. */
+int ash_batch_graph_kernels(const ash_batch *b, int iters);
 
 /*
  * Weighted GS on every hologram of the batch (same rule as

@@ -49,6 +49,7 @@ SIGNATURES = {
     "ash_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "ash_hologram_check": (c_int, [c_void_p, c_void_p]),
     "ash_wgs_launches": (c_int, [c_void_p, c_int]),
+    "ash_graph_kernels": (c_int, [c_void_p, c_int]),
     "ash_set_kernel_variant": (c_int, [c_void_p, c_int]),
     "ash_hologram_launch_info": (c_int, [c_void_p, c_int_p]),
     "ash_profile": (c_int, [c_void_p, c_void_p, c_void_p, c_float_p, c_void_p]),
@@ -59,6 +60,7 @@ SIGNATURES = {
     "ash_batch_info": (c_int, [c_void_p, c_int_p, c_int_p, c_int_p, ctypes.POINTER(ctypes.c_longlong)]),
     "ash_batch_set_grid": (c_int, [c_void_p, c_int]),
     "ash_batch_wgs_launches": (c_int, [c_void_p, c_int]),
+    "ash_batch_graph_kernels": (c_int, [c_void_p, c_int]),
     "ash_batch_wgs": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p]),
     "ash_batch_tune": (c_int, [c_void_p, c_void_p, ctypes.c_char_p, c_int_p, c_void_p]),
     "ash_forward_noalloc": (c_int, [c_int, c_int, c_void_p, c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p,

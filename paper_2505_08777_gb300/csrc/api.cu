@@ -95,8 +95,7 @@ ash_status ws(ash_hologram* h, T** out, size_t count) {
 }
 
 void release(ash_hologram* h) {
-  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
-  h->graphs.clear();
+  ash::clear_graphs(h);
   for (void* p : h->allocs) {
     if (g_free) g_free(g_alloc_ctx, p, h->home);
     else cudaFreeAsync(p, h->home);
@@ -338,6 +337,60 @@ bool bad_ptr(const void* p) { return p == nullptr; }
 }  // namespace
 
 namespace ash {
+
+int graph_kernel_nodes(cudaGraph_t g) {
+  size_t n = 0;
+  if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess) return -1;
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (n && cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return -1;
+  int k = 0;
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nd, &t) != cudaSuccess) return -1;
+    if (t == cudaGraphNodeTypeKernel) {
+      ++k;
+    } else if (t == cudaGraphNodeTypeGraph) {
+      cudaGraph_t child = nullptr;
+      if (cudaGraphChildGraphNodeGetGraph(nd, &child) != cudaSuccess) return -1;
+      const int m = graph_kernel_nodes(child);
+      if (m < 0) return -1;
+      k += m;
+    }
+  }
+  return k;
+}
+
+ash_status cached_graph(ash_hologram* h, int key, ash_status (*body)(ash_hologram*, int, cudaStream_t), int iters,
+                        cudaGraphExec_t* exec) {
+  auto it = h->graphs.find(key);
+  if (it != h->graphs.end()) {
+    *exec = it->second.exec;
+    return ASH_OK;
+  }
+  cudaGraph_t graph = nullptr;
+  ASH_CUDA(cudaStreamBeginCapture(h->capture, cudaStreamCaptureModeThreadLocal));
+  ash_status st = body(h, iters, h->capture);
+  cudaError_t ce = cudaStreamEndCapture(h->capture, &graph);
+  if (st != ASH_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+  ash_hologram::CachedGraph c;
+  c.kernels = graph_kernel_nodes(graph);
+  ce = cudaGraphInstantiate(&c.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
+  h->graphs[key] = c;
+  *exec = c.exec;
+  return ASH_OK;
+}
+
+void clear_graphs(ash_hologram* h) {
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second.exec);
+  h->graphs.clear();
+}
+
 ash_status wgs_body(ash_hologram* h, int iters, cudaStream_t s) { return enqueue_wgs_body(h, iters, s); }
 ash_status forward_enqueue(ash_hologram* h, int source, const float* phase, const float2* field, float2* E,
                            cudaStream_t s) {
@@ -818,25 +871,9 @@ ash_status ash_wgs_iterate(ash_hologram* h, float* phase, float* w, const float*
   ASH_CUDA(cudaMemcpyAsync(h->wgs_w, w, N * 4, cudaMemcpyDeviceToDevice, s));
   ASH_CUDA(cudaMemcpyAsync(h->wgs_T, target, N * 4, cudaMemcpyDeviceToDevice, s));
   if (iters >= 2) {
-    auto it = h->graphs.find(iters);
     cudaGraphExec_t exec = nullptr;
-    if (it != h->graphs.end()) {
-      exec = it->second;
-    } else {
-      cudaGraph_t graph = nullptr;
-      ASH_CUDA(cudaStreamBeginCapture(h->capture, cudaStreamCaptureModeThreadLocal));
-      ash_status st = enqueue_wgs_body(h, iters, h->capture);
-      cudaError_t ce = cudaStreamEndCapture(h->capture, &graph);
-      if (st != ASH_OK) {
-        if (graph) cudaGraphDestroy(graph);
-        return st;
-      }
-      if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
-      ce = cudaGraphInstantiate(&exec, graph, 0);
-      cudaGraphDestroy(graph);
-      if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
-      h->graphs[iters] = exec;
-    }
+    ash_status st = cached_graph(h, iters, enqueue_wgs_body, iters, &exec);
+    if (st != ASH_OK) return st;
     ASH_CUDA(cudaGraphLaunch(exec, s));
   } else {
     ash_status st = enqueue_wgs_body(h, iters, s);
@@ -896,8 +933,7 @@ ash_status ash_set_kernel_variant(ash_hologram* h, int variant) {
   if (variant == 2 && !h->tc_ok)
     return set_error(ASH_ERR_UNSUPPORTED, "tensor-core kernels need D <= %d (D = %d)", kTcMaxModes, h->g.D);
   h->variant = variant;
-  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
-  h->graphs.clear();
+  clear_graphs(h);
   return ASH_OK;
 }
 
@@ -907,9 +943,14 @@ ash_status ash_wgs_set_options(ash_hologram* h, float feedback, int fix_phase) {
   if (fix_phase != 0 && fix_phase != 1) return set_error(ASH_ERR_INVALID_ARG, "fix_phase must be 0 or 1");
   h->wgs_feedback = feedback;
   h->wgs_fix = fix_phase != 0;
-  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);   // the graphs hold the old options
-  h->graphs.clear();
+  clear_graphs(h);   // the graphs hold the old options
   return ASH_OK;
+}
+
+int ash_graph_kernels(const ash_hologram* h, int key) {
+  if (!h) return -1;
+  auto it = h->graphs.find(key);
+  return it == h->graphs.end() ? -1 : it->second.kernels;
 }
 
 int ash_wgs_launches(const ash_hologram* h, int iters) {

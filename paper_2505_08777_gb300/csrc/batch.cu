@@ -261,6 +261,7 @@ struct ash_batch {
   float2* split_buf = nullptr;
   cudaStream_t capture = nullptr;
   std::map<int, cudaGraphExec_t> graphs;
+  std::map<int, int> graph_kernels;   // kernel nodes of each cached graph
   std::string key;         // autotuner cache key
   // tensor-core path
   int variant = 0;         // 0 auto, 1 FMA-pipe kernels, 2 tensor-core kernels
@@ -424,6 +425,7 @@ ash_status set_grid(ash_batch* b, int G) {
   if (G != b->G) {
     for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
     b->graphs.clear();
+    b->graph_kernels.clear();
   }
   b->G = G;
   Schedule s{b->U, G};
@@ -522,6 +524,7 @@ void destroy_batch(ash_batch* b) {
   cudaDeviceSynchronize();
   for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
   b->graphs.clear();
+  b->graph_kernels.clear();
   if (b->dev) cudaFree(b->dev);
   if (b->split_buf) cudaFree(b->split_buf);
   for (void* q : {(void*)b->d_adj, (void*)b->d_fwd, (void*)b->d_hu0, (void*)b->d_g0, (void*)b->d_begin,
@@ -740,11 +743,18 @@ ash_status ash_batch_set_variant(ash_batch* b, int variant) {
   b->variant = variant;
   for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
   b->graphs.clear();
+  b->graph_kernels.clear();
   b->G = 0;
   return set_grid(b, b->use_tc() ? b->tc_slots : b->slots);
 }
 
 int ash_batch_standalone(const ash_batch* b) { return b ? (int)b->solo.size() : -1; }
+
+int ash_batch_graph_kernels(const ash_batch* b, int iters) {
+  if (!b) return -1;
+  auto it = b->graph_kernels.find(iters);
+  return it == b->graph_kernels.end() ? -1 : it->second;
+}
 
 int ash_batch_wgs_launches(const ash_batch* b, int iters) {
   if (!b || iters < 0) return -1;
@@ -791,10 +801,12 @@ ash_status ash_batch_wgs(ash_batch* b, float* const* phases, float* const* weigh
       return st;
     }
     if (ce != cudaSuccess) return status_cuda(ce, "batch cudaStreamEndCapture");
+    const int kernels = graph_kernel_nodes(graph);
     ce = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (ce != cudaSuccess) return status_cuda(ce, "batch cudaGraphInstantiate");
     b->graphs[iters] = exec;
+    b->graph_kernels[iters] = kernels;
   }
   BCUDA(cudaGraphLaunch(exec, s));
   for (int i = 0; i < b->members; ++i) {

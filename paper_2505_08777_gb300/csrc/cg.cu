@@ -235,25 +235,9 @@ ash_status ash_cg_refine(ash_hologram* h, float* phase, const float* t, int iter
   ASH_CUDA(cudaMemcpyAsync(h->cg_t, t, (size_t)h->g.N * 4, cudaMemcpyDeviceToDevice, s));
   ASH_CUDA(cudaMemcpyAsync(h->cg_scal, init, sizeof init, cudaMemcpyHostToDevice, s));
   if (iters >= 1) {
-    auto it = h->graphs.find(-iters);
     cudaGraphExec_t exec = nullptr;
-    if (it != h->graphs.end()) {
-      exec = it->second;
-    } else {
-      cudaGraph_t graph = nullptr;
-      ASH_CUDA(cudaStreamBeginCapture(h->capture, cudaStreamCaptureModeThreadLocal));
-      ash_status st = enqueue_cg_body(h, iters, h->capture);
-      cudaError_t ce = cudaStreamEndCapture(h->capture, &graph);
-      if (st != ASH_OK) {
-        if (graph) cudaGraphDestroy(graph);
-        return st;
-      }
-      if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
-      ce = cudaGraphInstantiate(&exec, graph, 0);
-      cudaGraphDestroy(graph);
-      if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
-      h->graphs[-iters] = exec;
-    }
+    ash_status st = cached_graph(h, -iters, enqueue_cg_body, iters, &exec);
+    if (st != ASH_OK) return st;
     ASH_CUDA(cudaGraphLaunch(exec, s));
   } else {
     ash_status st = enqueue_cg_body(h, 0, s);

@@ -86,11 +86,27 @@ struct ash_hologram {
   std::vector<void*> allocs;
   size_t bytes = 0;
   cudaStream_t capture = nullptr;
-  std::map<int, cudaGraphExec_t> graphs;   // WGS loops by iteration count; CG loops under -iters
+  // WGS loops by iteration count; CG loops under -iters. `kernels`: the
+  // kernel nodes of the captured graph (those of child graphs included).
+  struct CachedGraph {
+    cudaGraphExec_t exec = nullptr;
+    int kernels = 0;
+  };
+  std::map<int, CachedGraph> graphs;
 };
 
 namespace ash {
 
+// The handle's executable graph for `key` (a WGS iteration count, or minus a
+// CG iteration count): on first use, body(h, iters, capture stream) is
+// captured, instantiated and cached with its kernel-node count.
+ash_status cached_graph(ash_hologram* h, int key, ash_status (*body)(ash_hologram*, int, cudaStream_t), int iters,
+                        cudaGraphExec_t* exec);
+// Drop every cached graph (options or shapes they captured have changed).
+void clear_graphs(ash_hologram* h);
+// Kernel nodes of a graph, those of embedded child graphs included (-1 if
+// the graph cannot be inspected).
+int graph_kernel_nodes(cudaGraph_t g);
 // Record a message for ash_last_error() (any translation unit).
 void record_error(const char* msg);
 // Map a CUDA error to ASH_ERR_CUDA with a message.

@@ -216,6 +216,15 @@ class Hologram:
                 "adjoint_variant", "pixels_per_thread"]
         return dict(zip(keys, list(out)))
 
+    def wgs_launches(self, iters: int) -> int:
+        """Kernel launches of one wgs() call with `iters` iterations."""
+        return int(self._lib.ash_wgs_launches(self._h, int(iters)))
+
+    def graph_kernels(self, key: int) -> int:
+        """Kernel nodes of the cached loop graph: key = iters of a wgs() call
+        (iters >= 2), -iters of a cg_refine() call; -1 if none is cached."""
+        return int(self._lib.ash_graph_kernels(self._h, int(key)))
+
     def set_variant(self, variant: int):
         """0 = automatic, 1 = FMA-pipe kernels, 2 = tensor-core phase contraction (D <= 21)."""
         _lib.check(self._lib.ash_set_kernel_variant(self._h, int(variant)), "ash_set_kernel_variant")
@@ -288,6 +297,10 @@ class Batch:
 
     def launches(self, iters: int) -> int:
         return int(self._lib.ash_batch_wgs_launches(self._b, int(iters)))
+
+    def graph_kernels(self, iters: int) -> int:
+        """Kernel nodes of the graph captured for `iters` (-1 if none is cached)."""
+        return int(self._lib.ash_batch_graph_kernels(self._b, int(iters)))
 
     def _ptrs(self, tensors, dtype, shapes, name):
         if len(tensors) != self.count:
