@@ -348,8 +348,8 @@ def main():
     dom = "forward" if kms["forward"] >= kms["adjoint"] else "adjoint"
     P = 8 if p.D <= 12 else 4
     linfo = h.launch_info()
-    fwd_tc = bool(linfo["adjoint_variant"] & 4)
-    adj_tc = bool(linfo["adjoint_variant"] & 2)
+    fwd_tc = bool(linfo["kernels"] & 4)
+    adj_tc = bool(linfo["kernels"] & 2)
     # K-atoms per tensor-core operand row: one for D <= 10, and for D = 11
     # when the basis holds both tilts (their two-slot exact form)
     NA = 1 if 3 * p.D <= 32 or (3 * (p.D - 2) + 4 <= 32 and 2 in p.noll and 3 in p.noll) else 2

@@ -322,8 +322,8 @@ ash_status ash_grad(ash_hologram *h, const float *phase, const float *grad_E, fl
 /*
  * Launch shapes chosen for the handle, written to the host array out[8]:
  *   {CTAs of the FMA-pipe transform launches, their resident CTAs per SM
- *    (forward), (adjoint), CTAs of the tensor-core adjoint (0 if not
- *    available), its resident CTAs per SM, split flags (bit 0: FMA schedule
+ *    (forward), (adjoint), CTAs of the tensor-core adjoint and of the
+ *    tensor-core forward (0 if not available), split flags (bit 0: FMA schedule
  *    splits tiles, bit 1: tensor-core schedule splits sub-tiles, bit 2:
  *    the tensor-core forward splits spot blocks), kernels in use (adjoint:
  *    1 FMA or 2 tensor core, plus 4 if the forward and 8 if the

@@ -212,8 +212,8 @@ class Hologram:
     def launch_info(self) -> dict:
         out = (ctypes.c_int * 8)()
         _lib.check(self._lib.ash_hologram_launch_info(self._h, out), "ash_hologram_launch_info")
-        keys = ["grid", "fwd_ctas_per_sm", "adj_ctas_per_sm", "tc_grid", "tc_ctas_per_sm", "split_flags",
-                "adjoint_variant", "pixels_per_thread"]
+        keys = ["grid", "fwd_ctas_per_sm", "adj_ctas_per_sm", "tc_adj_grid", "tc_fwd_grid", "split_flags",
+                "kernels", "pixels_per_thread"]
         return dict(zip(keys, list(out)))
 
     def wgs_launches(self, iters: int) -> int:

@@ -130,4 +130,4 @@ def _check_grad(nx, ny, N, noll, variant=0):
     r1 = np.linalg.norm(dph - dph_ref) / np.linalg.norm(dph_ref)
     r2 = np.linalg.norm(dC - dC_ref) / np.linalg.norm(dC_ref)
     assert r1 <= GRAD_TOL and r2 <= GRAD_TOL, (r1, r2)
-    return bool(h.launch_info()["adjoint_variant"] & 8)
+    return bool(h.launch_info()["kernels"] & 8)
