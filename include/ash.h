@@ -288,14 +288,15 @@ ash_status ash_adjoint(ash_hologram *h, const float *y, float *g, float *phase_o
  *   phase        device float[ny*nx], in/out (the loop state).
  *   w            device float[N], in/out (the loop state).
  *   target       device float[N], target amplitudes T (> 0).
- *   iters        >= 0.
+ *   iters        0 <= iters <= 1000000.
  *   E_out        device float[2*N] or NULL: field of the final phase.
  *   metrics_out  device float[4] or NULL: {uniformity, efficiency,
  *                sum |E|^2, min |E|^2/T^2}; uniformity
  *                U = 1 - (max I^ - min I^)/(max I^ + min I^), I^_n = |E_n|^2/T_n^2;
  *                efficiency = sum |E|^2 / (M sum A^2).
- * The state is exactly (phase, w): running k iterations twice equals running
- * 2k iterations once, bit for bit. The loop is enqueued as a CUDA graph when
+ * The state is exactly (phase, w), plus the held spot phases when phase
+ * fixing is on (ash_wgs_set_options): running k iterations twice equals
+ * running 2k iterations once, bit for bit. The loop is enqueued as a CUDA graph when
  * iters > 1 (captured on first use per handle and iteration count).
  */
 ash_status ash_wgs_iterate(ash_hologram *h, float *phase, float *w, const float *target, int iters,
@@ -336,9 +337,10 @@ ash_status ash_hologram_launch_info(const ash_hologram *h, int *out);
  * coefficient-gradient moments: 0 = automatic (the faster measured family
  * per pass: tensor cores when the operand row fits one K-atom, for the
  * forward and the moments from N = 64 spots, for the adjoint from N = 256),
- * 1 = FMA-pipe kernels, 2 = tensor-core kernels (ASH_ERR_UNSUPPORTED if
- * D > 21; the moments stay on the FMA pipe where their tensor-core pass is
- * not available). Both
+ * 1 = FMA-pipe kernels, 2 = tensor-core kernels (available for every D a
+ * handle accepts: one K-atom per operand row for D <= 10 and for D = 11
+ * with both tilts, two otherwise; the moments stay on the FMA pipe where
+ * their tensor-core pass is not available). Both
  * compute the same sums; the tensor-core variant forms the phases
  * C_n . dZ_m with split-tf32 tcgen05 MMAs into tensor memory. Drops the
  * handle's captured graphs.
@@ -396,12 +398,14 @@ ash_status ash_hologram_check(ash_hologram *h, void *stream);
 
 /* ------------------------------------------------------------------------
  * Batched uneven form: many holograms (different grids, spot counts and
- * mode counts) solved together. Each phase of a WGS iteration (forward,
- * reduction, spot update, adjoint, fix-up) is ONE launch over the work units
- * (hologram, tile, spot) of all holograms, cut into equal contiguous ranges
- * per CTA; the whole loop is one CUDA graph. Not in the paper (which solves
- * one hologram at a time); results equal the per-hologram path's up to fp32
- * summation order.
+ * mode counts) solved together, the whole loop one CUDA graph. Members
+ * below a size threshold form the persistent group: each phase of a WGS
+ * iteration (forward, reduction, spot update, adjoint, fix-up) is ONE launch
+ * over the work units (hologram, tile, spot) of all of them, cut into equal
+ * contiguous ranges per CTA. Larger members run their own single-hologram
+ * loop inside the same graph (ash_batch_create_ex). Not in the paper (which
+ * solves one hologram at a time); results equal the per-hologram path's up
+ * to fp32 summation order, and bit for bit for standalone members.
  */
 typedef struct ash_batch ash_batch;
 

@@ -226,7 +226,7 @@ class Hologram:
         return int(self._lib.ash_graph_kernels(self._h, int(key)))
 
     def set_variant(self, variant: int):
-        """0 = automatic, 1 = FMA-pipe kernels, 2 = tensor-core phase contraction (D <= 21)."""
+        """0 = automatic, 1 = FMA-pipe kernels, 2 = tensor-core phase contraction (any D)."""
         _lib.check(self._lib.ash_set_kernel_variant(self._h, int(variant)), "ash_set_kernel_variant")
 
     def check(self, stream=None):
