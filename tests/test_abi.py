@@ -72,6 +72,42 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert lib.ash_debug_fail_after(-1) == 1
 
 
+def test_later_entry_points_reject_bad_arguments_without_gpu(lib):
+    # CG, calibration, batch, launch counts, no-alloc forward, mixed bases,
+    # sin/cos check: each returns ASH_ERR_INVALID_ARG (or -1 for the counts)
+    # from its host-side checks, before any CUDA call
+    vp, INV = ctypes.c_void_p, 1
+    one = vp(1)
+    d3 = (ctypes.c_float * 3)(-1.0, 0.0, 1.0)
+    same = (ctypes.c_float * 3)(0.5, 0.5, 0.5)
+    assert lib.ash_cg_refine(None, one, one, 5, 0.05, None, None) == INV
+    assert lib.ash_zsub_sweep(None, one, 0, d3, 3, one, None) == INV
+    assert lib.ash_zsub_estimate(one, d3, 2, 4, one, None, 0, 0, None) == INV      # K < 3
+    assert lib.ash_zsub_estimate(one, d3, 33, 4, one, None, 0, 0, None) == INV     # K > 32
+    assert lib.ash_zsub_estimate(one, same, 3, 4, one, None, 0, 0, None) == INV    # one distinct offset
+    assert b"distinct" in lib.ash_last_error()
+    assert lib.ash_zsub_estimate(None, d3, 3, 4, one, None, 0, 0, None) == INV
+    for fn in ("ash_wgs_launches", "ash_graph_kernels", "ash_batch_wgs_launches", "ash_batch_graph_kernels"):
+        assert getattr(lib, fn)(None, 4) == -1, fn
+    assert lib.ash_batch_standalone(None) == -1
+    b = ctypes.c_void_p(0)
+    assert lib.ash_batch_create(ctypes.byref(b), 0, None, None) == INV
+    assert lib.ash_batch_create_ex(ctypes.byref(b), 1, one, -1, None) == INV
+    assert lib.ash_set_kernel_variant(None, 1) == INV
+    assert lib.ash_wgs_set_options(None, 1.0, 0) == INV
+    assert lib.ash_debug_sincos(one, -1, one, one, 0, None) == INV
+    assert lib.ash_debug_sincos(one, 4, one, one, 2, None) == INV
+    E = one
+    assert lib.ash_forward_noalloc(0, 8, one, one, 2, one, 4, one, E, None) == INV
+    assert lib.ash_forward_noalloc(8, 8, one, one, 2, one, 131073, one, E, None) == INV
+    assert lib.ash_forward_noalloc(8, 8, None, one, 2, one, 4, one, E, None) == INV
+    noll = (ctypes.c_int * 2)(2, 3)
+    mix = (ctypes.c_double * 4)(1, 0, 0, 1)
+    h = ctypes.c_void_p(0)
+    assert lib.ash_hologram_create_mixed(ctypes.byref(h), 8, 8, one, 0, noll, 2, mix, 4, one, None) == INV
+    assert lib.ash_hologram_create_mixed(ctypes.byref(h), 8, 8, one, 65, noll, 2, mix, 4, one, None) == INV
+
+
 def test_fault_injection_counts_calls(lib):
     # the n-th launching call fails with ASH_ERR_INJECTED; argument errors are not counted
     assert lib.ash_debug_fail_after(1) == 0
