@@ -188,6 +188,49 @@ def oracle_sample(p, Z, workers):
     return 2 * p.N * p.M, dt
 
 
+# Pixel-sampled oracle timings: the transforms' sums run over pixels, so the
+# oracle on every stride-th pixel does the same work per term; the stride
+# bounds the sample (the forward and the WGS adjoint use a thread pool, the
+# gradient's adjoint and moments run single-threaded).
+ORACLE_SAMPLE_TERMS = {"wgs": 1.5e9, "grad": 2e8}
+
+
+def oracle_sampled(kind, ps, workers):
+    """kind "wgs": one WGS iteration (forward, spot update, adjoint, arg) per
+    problem; "grad": the forward, then dL/dphi and dL/dC (adjoint and
+    moments). Returns (terms, seconds, stride)."""
+    from oracle import grad, transform, wgs, zernike
+    per_term = 2 if kind == "wgs" else 3
+    total = sum(per_term * p.N * p.M for p in ps)
+    stride = max(1, int(math.ceil(total / ORACLE_SAMPLE_TERMS[kind])))
+    terms, secs = 0, 0.0
+    for p in ps:
+        idx = np.arange(0, p.M, stride)
+        Z = zernike.basis(p.nx, p.ny, p.noll)[:, idx]
+        A = p.amp.astype(np.float64).ravel()[idx]
+        ph = p.phase0.astype(np.float64).ravel()[idx]
+        C = p.coeff.astype(np.float64)
+        T = p.target.astype(np.float64)
+        t0 = time.perf_counter()
+        E = transform.forward(transform.field(A, ph), C, Z, workers=workers)
+        if kind == "wgs":
+            _, y = wgs.weight_update(E, T, T)
+            transform.phase_of(transform.adjoint(y, C, Z, workers=workers))
+        else:
+            grad.backward(A, ph, C, Z, grad.grad_E(E, T))
+        secs += time.perf_counter() - t0
+        terms += per_term * p.N * idx.size
+    return terms, secs, stride
+
+
+def _sampled_baseline(kind, ps, what):
+    cores = _cpu_cores()
+    terms, secs, stride = oracle_sampled(kind, ps, cores)
+    return {"value": terms / secs / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{what} over every {stride}-th pixel ({terms:.3g} terms), numpy complex128",
+            "seconds": secs}
+
+
 def run_reference(args):
     rank, world, _ = _dist()
     if rank != 0:
@@ -395,6 +438,8 @@ def main():
                                 "sample": "one WGS iteration (forward + update + adjoint) over the full 1024x1024 "
                                           "grid and all 400 spots, numpy complex128 thread pool",
                                 "seconds": secs}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.config == "c3":
+        line["cpu_baseline"] = _sampled_baseline("wgs", [p], "one WGS iteration (forward + update + adjoint)")
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -469,6 +514,8 @@ def bench_autograd(args):
             "graph_captured_step": graphed,
             "gpu_launches": None if step_kernels is None else step_kernels * args.steps,
             "clocks": clocks.summary()}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = _sampled_baseline("grad", ps[:1], "one hologram's forward + dL/dphi + dL/dC")
     print(json.dumps(line))
     return 0
 
@@ -895,6 +942,8 @@ def bench_batch(args):
             "uniformity_min": float(met[:, 0].min()), "uniformity_median": float(np.median(met[:, 0])),
             "frac_of_peak": terms / (ms_b * 1e-3) / 1e9 / _peak_gterm(torch, dev),
             "clocks": clocks.summary()}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = _sampled_baseline("wgs", ps[:8], "one WGS iteration of the first 8 holograms")
     print(json.dumps(line))
     return 0
 
