@@ -18,8 +18,10 @@
 // tracked by mbarriers. Two TMEM buffers of 64 fp32 columns alternate: each
 // warp copies a chunk's phases out of TMEM, arrives on a shared counter and
 // goes on to the sincos and the complex multiply-accumulate; the warp that
-// arrives last refills the rings and issues the MMA two chunks ahead into
-// the buffer just freed. No CTA-wide barrier is taken in the main loop. The
+// arrives last refills the rings and issues the next MMAs: in the forward
+// two chunks ahead, into the buffer just freed; in the adjoint one chunk
+// ahead (its shared memory holds two spot-row slots, so that four CTAs fit
+// on an SM). No CTA-wide barrier is taken in the main loop. The
 // producer steps of consecutive chunks cannot overlap: the last arrival for
 // chunk c comes after every warp's arrival for c, and the warp that ran the
 // producer step of c - 1 arrives for c only after finishing it (its release
