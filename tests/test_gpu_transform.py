@@ -12,8 +12,8 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
-from gpu_helpers import REL_TOL, assert_close, basis_at, oracle_forward, oracle_inputs  # noqa: E402
-from oracle import transform, zernike  # noqa: E402
+from gpu_helpers import GRAD_TOL, REL_TOL, assert_close, basis_at, oracle_forward, oracle_inputs  # noqa: E402
+from oracle import grad as ograd, transform, zernike  # noqa: E402
 from workloads import config_c1, config_c2, config_c3, random_problem  # noqa: E402
 
 pytestmark = pytest.mark.gpu
@@ -102,6 +102,29 @@ def test_user_basis_matches_zernike_path():
                             p.coeff.astype(np.float64), Z.astype(np.float32).astype(np.float64))
     assert_close(E_b, ref, what="user basis")
     assert_close(E_n, E_b, what="noll vs user basis")
+
+
+@pytest.mark.parametrize("variant", [0, 2])
+def test_user_basis_adjoint_and_gradients(variant):
+    # a caller basis has no polynomial form, so dL/dC runs on the FMA moment
+    # kernel; the adjoint and dL/dphi on the family the variant picks
+    p = random_problem(19, 112, 80, 300, list(range(2, 12)), defocus_max=4.0)
+    Z32 = zernike.basis(p.nx, p.ny, p.noll).astype(np.float32)
+    h = _holo(p, basis=Z32.reshape(len(p.noll), p.ny, p.nx))
+    h.set_variant(variant)
+    Z, C = Z32.astype(np.float64), p.coeff.astype(np.float64)
+    A = p.amp.astype(np.float64).ravel()
+    rng = np.random.default_rng(4)
+    y = _rand_complex(rng, p.N)
+    g, _ = h.adjoint(torch.from_numpy(y).cuda())
+    assert_close(g.cpu().numpy(), transform.adjoint(y.astype(np.complex128), C, Z), what="user basis adjoint")
+    E = transform.forward(transform.field(A, p.phase0), C, Z)
+    gE = ograd.grad_E(E, p.target).astype(np.complex64)
+    dph, dC = h.grad(torch.from_numpy(p.phase0).cuda(), torch.from_numpy(gE).cuda())
+    dph_ref, dC_ref = ograd.backward(A, p.phase0, C, Z, gE.astype(np.complex128))
+    assert np.linalg.norm(dph.cpu().numpy().ravel() - dph_ref) <= GRAD_TOL * np.linalg.norm(dph_ref)
+    assert np.linalg.norm(dC.cpu().numpy() - dC_ref) <= GRAD_TOL * np.linalg.norm(dC_ref)
+    assert not (h.launch_info()["kernels"] & 8)   # no tensor-core moments for a caller basis
 
 
 def test_phase_conjugate_focus_and_flat_phase():
