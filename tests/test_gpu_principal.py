@@ -6,8 +6,8 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
-from gpu_helpers import assert_close  # noqa: E402
-from oracle import svd, transform, zernike  # noqa: E402
+from gpu_helpers import GRAD_TOL, assert_close  # noqa: E402
+from oracle import grad as ograd, svd, transform, zernike  # noqa: E402
 from workloads import random_problem  # noqa: E402
 
 pytestmark = pytest.mark.gpu
@@ -44,6 +44,15 @@ def test_principal_mode_hologram_matches_oracle(nx, ny, N, noll, K):
     g_ref = transform.adjoint(y.astype(np.complex128), C_lib, Zm)
     g, _ = h.adjoint(torch.from_numpy(y).cuda(), want_field=True, want_phase=False)
     assert_close(g.cpu().numpy(), g_ref, what="principal-mode adjoint")
+    # gradients: the rotated modes are still polynomials, so dL/dC takes the
+    # tensor-core moment pass with tile polynomials of the mixed monomials
+    gE = ograd.grad_E(E_ref, p.target).astype(np.complex64)
+    dph, dC = h.grad(torch.from_numpy(p.phase0).cuda(), torch.from_numpy(gE).cuda())
+    dph_ref, dC_ref = ograd.backward(A, p.phase0, C_lib, Zm, gE.astype(np.complex128))
+    assert np.linalg.norm(dph.cpu().numpy().ravel() - dph_ref) <= GRAD_TOL * np.linalg.norm(dph_ref)
+    assert np.linalg.norm(dC.cpu().numpy() - dC_ref) <= GRAD_TOL * np.linalg.norm(dC_ref)
+    if N >= 64:
+        assert h.launch_info()["kernels"] & 8
     if K == len(cols):
         # full rank: the same transform as the original Zernike problem
         E_orig = transform.forward(f, p.coeff.astype(np.float64), Z)
