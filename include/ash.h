@@ -398,9 +398,21 @@ ash_status ash_profile(ash_hologram *h, const float *phase, const float *y, floa
 
 /*
  * Synchronise `stream` and report device-side errors recorded by the
- * handle's kernels (ASH_ERR_DEVICE / ASH_ERR_TIMEOUT), clearing them.
+ * handle's kernels, clearing them: ASH_ERR_TIMEOUT if a bounded wait gave up
+ * (every spin-wait of the tensor-core kernels has an iteration limit; on
+ * reaching it the kernel records the timeout, stops waiting and returns, so
+ * the context stays usable), ASH_ERR_DEVICE for any other recorded error.
  */
 ash_status ash_hologram_check(ash_hologram *h, void *stream);
+
+/*
+ * For tests of that path: enqueue one kernel whose single bounded wait is
+ * never released (a fresh mbarrier nothing arrives on). It gives up after
+ * `polls` polls (1 <= polls <= 2^20) and records the timeout in the handle's
+ * error word, as a transform kernel would; the next ash_hologram_check
+ * returns ASH_ERR_TIMEOUT. No fault, no trap, nothing left running.
+ */
+ash_status ash_debug_wait_timeout(ash_hologram *h, unsigned polls, void *stream);
 
 /* ------------------------------------------------------------------------
  * Batched uneven form: many holograms (different grids, spot counts and

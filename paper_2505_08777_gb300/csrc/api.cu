@@ -13,6 +13,7 @@
 #include "basis_host.h"
 #include "handle.h"
 #include "launch.h"
+#include "tc_common.cuh"
 #include "tc_launch.h"
 
 using namespace ash;
@@ -402,6 +403,19 @@ ash_status adjoint_enqueue(ash_hologram* h, const float2* y, float2* g_out, floa
 }
 cudaError_t coeff_images_enqueue(ash_hologram* h, cudaStream_t s) { return enqueue_tc_coeff(h, s); }
 }  // namespace ash
+
+// A bounded wait that is never released: one thread waits on a fresh
+// mbarrier that nothing arrives on, for at most `polls` polls, and then
+// reports the timeout in the error word exactly as the transforms do.
+static __global__ void k_debug_wait(uint32_t polls, unsigned* __restrict__ err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (!mbar_wait(&bar, 0u, polls)) atomicOr(err, kErrTimeout);
+    mbar_inval(&bar);
+  }
+}
 
 // Two pixels per thread, as in the transforms' pair loops.
 static __global__ void k_debug_sincos(const float* __restrict__ x, int n, float* __restrict__ s, float* __restrict__ c,
@@ -1062,8 +1076,19 @@ ash_status ash_hologram_check(ash_hologram* h, void* stream) {
   ASH_CUDA(cudaStreamSynchronize(s));
   if (word) {
     ASH_CUDA(cudaMemsetAsync(h->err_word, 0, sizeof word, s));
+    ASH_CUDA(cudaStreamSynchronize(s));
+    if (word & kErrTimeout)
+      return set_error(ASH_ERR_TIMEOUT, "a bounded wait gave up (device error word 0x%x)", word);
     return set_error(ASH_ERR_DEVICE, "device error word 0x%x", word);
   }
+  return ASH_OK;
+}
+
+ash_status ash_debug_wait_timeout(ash_hologram* h, unsigned polls, void* stream) {
+  if (!h) return set_error(ASH_ERR_INVALID_ARG, "handle is NULL");
+  if (polls < 1 || polls > (1u << 20)) return set_error(ASH_ERR_INVALID_ARG, "polls outside [1, 2^20]");
+  k_debug_wait<<<1, 32, 0, as_stream(stream)>>>(polls, h->err_word);
+  ASH_CUDA(cudaGetLastError());
   return ASH_OK;
 }
 

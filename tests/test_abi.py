@@ -90,6 +90,7 @@ def test_later_entry_points_reject_bad_arguments_without_gpu(lib):
     for fn in ("ash_wgs_launches", "ash_graph_kernels", "ash_batch_wgs_launches", "ash_batch_graph_kernels"):
         assert getattr(lib, fn)(None, 4) == -1, fn
     assert lib.ash_batch_standalone(None) == -1
+    assert lib.ash_debug_wait_timeout(None, 16, None) == INV
     b = ctypes.c_void_p(0)
     assert lib.ash_batch_create(ctypes.byref(b), 0, None, None) == INV
     assert lib.ash_batch_create_ex(ctypes.byref(b), 1, one, -1, None) == INV

@@ -127,6 +127,20 @@ def test_user_basis_adjoint_and_gradients(variant):
     assert not (h.launch_info()["kernels"] & 8)   # no tensor-core moments for a caller basis
 
 
+def test_set_amplitude_changes_the_nearfield():
+    p = random_problem(23, 96, 72, 60, list(range(2, 12)))
+    h = _holo(p)
+    ph = torch.from_numpy(p.phase0).cuda()
+    rng = np.random.default_rng(8)
+    amp2 = rng.uniform(0.2, 1.0, size=p.amp.shape).astype(np.float32)
+    h.set_amplitude(torch.from_numpy(amp2).cuda())
+    Z, C, _ = oracle_inputs(p)
+    ref = transform.forward(transform.field(amp2.astype(np.float64).ravel(), p.phase0), C, Z)
+    assert_close(h.forward(ph).cpu().numpy(), ref, what="forward after set_amplitude")
+    h.set_amplitude(torch.from_numpy(p.amp).cuda())
+    assert_close(h.forward(ph).cpu().numpy(), oracle_forward(p, p.phase0), what="amplitude restored")
+
+
 def test_phase_conjugate_focus_and_flat_phase():
     # closed forms on the GPU path: C = 0, phase 0 -> E = sum A; conjugate hologram focuses spot n
     p = random_problem(5, 128, 96, 8, list(range(2, 12)), defocus_max=10.0)
