@@ -574,8 +574,9 @@ def _kernels_enqueued(fn, stream):
 
 def _autograd_step_kernels(hs, phases, coeffs):
     """The library kernels of one c4 step: per hologram the calls SpotField
-    makes (coefficients, forward; coefficients, ash_grad for both
-    gradients), with preallocated outputs so that nothing else is enqueued."""
+    makes (coefficients and forward; then ash_grad for both gradients, the
+    handle still holding those coefficients), with preallocated outputs so
+    that nothing else is enqueued."""
     import ctypes
 
     import torch
@@ -590,7 +591,6 @@ def _autograd_step_kernels(hs, phases, coeffs):
         for h, ph, c, (E, gE, dph, dC) in zip(hs, phases, coeffs, outs):
             h.set_coefficients(c.detach(), stream=side)
             h.forward(ph.detach(), out=E, stream=side)
-            h.set_coefficients(c.detach(), stream=side)
             rc = h._lib.ash_grad(h.handle, ctypes.c_void_p(ph.data_ptr()), ctypes.c_void_p(gE.data_ptr()),
                                  ctypes.c_void_p(dph.data_ptr()), ctypes.c_void_p(dC.data_ptr()),
                                  ctypes.c_void_p(side.cuda_stream))

@@ -27,6 +27,7 @@ class SpotField(torch.autograd.Function):
         E = holo.forward(phase)
         ctx.save_for_backward(phase, coeff)
         ctx.holo = holo
+        ctx.epoch = holo.coeff_epoch
         return E
 
     @staticmethod
@@ -36,7 +37,10 @@ class SpotField(torch.autograd.Function):
         want_phase, want_coeff = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
         if not (want_phase or want_coeff):
             return None, None, None
-        holo.set_coefficients(coeff)
+        if holo.coeff_epoch != ctx.epoch:
+            # the handle was given other coefficients since this forward
+            # (an in-place change of `coeff` itself fails autograd's check)
+            holo.set_coefficients(coeff)
         dphase, dcoeff = holo.grad(phase, grad_E.contiguous(), want_phase=want_phase, want_coeff=want_coeff)
         return dphase, dcoeff, None
 

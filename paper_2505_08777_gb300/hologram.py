@@ -53,6 +53,7 @@ class Hologram:
         `basis`: a caller basis (D, ny, nx) instead of Noll modes."""
         self._lib = _lib.load()
         self._h = ctypes.c_void_p(0)
+        self.coeff_epoch = 0   # counts set_coefficients calls
         if amp.dim() != 2:
             raise ValueError("amp must be (ny, nx)")
         self.ny, self.nx = int(amp.shape[0]), int(amp.shape[1])
@@ -115,8 +116,11 @@ class Hologram:
 
     # -- state ------------------------------------------------------------
     def set_coefficients(self, coeff: torch.Tensor, stream=None):
+        """Replace C; `coeff_epoch` counts these calls (made through this
+        object), so a caller can tell whether C changed since it set it."""
         _need(coeff, torch.float32, (self.N, self.D), "coeff")
         _lib.check(self._lib.ash_set_coefficients(self._h, _ptr(coeff), _stream_ptr(stream)), "ash_set_coefficients")
+        self.coeff_epoch += 1
         if coeff.data_ptr() != self._coeff.data_ptr():
             self._coeff.copy_(coeff.detach())
 

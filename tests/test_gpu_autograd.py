@@ -55,6 +55,30 @@ def test_autograd_matches_oracle_and_torch_reference():
     assert _rel(coeff.grad.double().cpu().numpy(), C64.grad.cpu().numpy()) <= GRAD_TOL
 
 
+def test_one_handle_two_coefficient_sets_in_one_graph():
+    # two forwards on one handle with different C, then one backward: the
+    # second backward to run finds the handle holding the other C and must
+    # set its own again (the handle counts set_coefficients calls)
+    from paper_2505_08777_gb300.autograd import spot_field, spot_intensity_loss
+    p, h = _setup(seed=6)
+    rng = np.random.default_rng(3)
+    C2np = (p.coeff + rng.normal(0.0, 0.3, p.coeff.shape)).astype(np.float32)
+    phase = torch.from_numpy(p.phase0).cuda().requires_grad_(True)
+    c1 = torch.from_numpy(p.coeff).cuda().requires_grad_(True)
+    c2 = torch.from_numpy(C2np).cuda().requires_grad_(True)
+    t = torch.from_numpy(p.target).cuda()
+    loss = spot_intensity_loss(spot_field(h, phase, c1), t) + spot_intensity_loss(spot_field(h, phase, c2), t)
+    loss.backward()
+    Z, C1, A = oracle_inputs(p)
+    ph = p.phase0.astype(np.float64).ravel()
+    L1, dphi1, dC1 = ograd.grad(A, ph, C1, Z, p.target)
+    L2, dphi2, dC2 = ograd.grad(A, ph, C2np.astype(np.float64), Z, p.target)
+    assert abs(loss.item() - (L1 + L2)) <= 1e-3 * abs(L1 + L2)
+    assert _rel(c1.grad.cpu().numpy().astype(np.float64), dC1) <= GRAD_TOL
+    assert _rel(c2.grad.cpu().numpy().astype(np.float64), dC2) <= GRAD_TOL
+    assert _rel(phase.grad.cpu().numpy().astype(np.float64).ravel(), dphi1 + dphi2) <= GRAD_TOL
+
+
 def test_adam_lowers_spot_loss():
     from paper_2505_08777_gb300.autograd import spot_field, spot_intensity_loss
     p, h = _setup(seed=9, nx=96, ny=96, N=64)
