@@ -9,7 +9,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
-from gpu_helpers import UNIF_TOL, assert_close, oracle_inputs  # noqa: E402
+from gpu_helpers import UNIF_TOL, oracle_inputs  # noqa: E402
 from oracle import transform, wgs  # noqa: E402
 from workloads import random_problem  # noqa: E402
 

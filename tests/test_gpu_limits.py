@@ -11,7 +11,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
-from gpu_helpers import REL_TOL, assert_close, basis_at  # noqa: E402
+from gpu_helpers import assert_close, basis_at  # noqa: E402
 from workloads import random_problem  # noqa: E402
 
 pytestmark = pytest.mark.gpu
