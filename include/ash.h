@@ -197,6 +197,10 @@ ash_status ash_hologram_info(const ash_hologram *h, int *nx, int *ny, int *N, in
 /* Replace the coefficient matrix C (device float[N*D]); same N and D. */
 ash_status ash_set_coefficients(ash_hologram *h, const float *coeff, void *stream);
 
+/* Copy the coefficient matrix the handle holds into coeff (device
+ * float[N*D], row-major), stream-ordered after the calls before it. */
+ash_status ash_get_coefficients(const ash_hologram *h, float *coeff, void *stream);
+
 /* Replace the illumination amplitude A (device float[ny*nx]). */
 ash_status ash_set_amplitude(ash_hologram *h, const float *amp, void *stream);
 

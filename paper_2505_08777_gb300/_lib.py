@@ -50,6 +50,7 @@ SIGNATURES = {
     "ash_hologram_check": (c_int, [c_void_p, c_void_p]),
     "ash_wgs_launches": (c_int, [c_void_p, c_int]),
     "ash_graph_kernels": (c_int, [c_void_p, c_int]),
+    "ash_get_coefficients": (c_int, [c_void_p, c_void_p, c_void_p]),
     "ash_debug_wait_timeout": (c_int, [c_void_p, ctypes.c_uint, c_void_p]),
     "ash_set_kernel_variant": (c_int, [c_void_p, c_int]),
     "ash_hologram_launch_info": (c_int, [c_void_p, c_int_p]),

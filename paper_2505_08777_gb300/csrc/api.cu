@@ -833,6 +833,13 @@ ash_status ash_set_coefficients(ash_hologram* h, const float* coeff, void* strea
   return ASH_OK;
 }
 
+ash_status ash_get_coefficients(const ash_hologram* h, float* coeff, void* stream) {
+  if (!h || !coeff) return set_error(ASH_ERR_INVALID_ARG, "NULL argument");
+  ASH_CUDA(cudaMemcpyAsync(coeff, h->coeff, (size_t)h->g.N * h->g.D * sizeof(float), cudaMemcpyDeviceToDevice,
+                           as_stream(stream)));
+  return ASH_OK;
+}
+
 ash_status ash_set_amplitude(ash_hologram* h, const float* amp, void* stream) {
   if (!h || !amp) return set_error(ASH_ERR_INVALID_ARG, "NULL argument");
   if (injected_failure()) return set_error(ASH_ERR_INJECTED, "injected failure");

@@ -71,7 +71,7 @@ class Hologram:
         if basis is not None:
             _need(basis, torch.float32, (self.D, self.ny, self.nx), "basis")
         self.noll = noll
-        self._coeff = coeff.detach().clone()
+        self.device = amp.device
         if mix is not None:
             if noll is None or basis is not None:
                 raise ValueError("mix needs noll (and no basis)")
@@ -121,12 +121,12 @@ class Hologram:
         _need(coeff, torch.float32, (self.N, self.D), "coeff")
         _lib.check(self._lib.ash_set_coefficients(self._h, _ptr(coeff), _stream_ptr(stream)), "ash_set_coefficients")
         self.coeff_epoch += 1
-        if coeff.data_ptr() != self._coeff.data_ptr():
-            self._coeff.copy_(coeff.detach())
 
-    def coefficients(self) -> torch.Tensor:
-        """The coefficient matrix the handle currently holds (N, D)."""
-        return self._coeff
+    def coefficients(self, stream=None) -> torch.Tensor:
+        """A copy of the coefficient matrix the handle currently holds (N, D)."""
+        out = torch.empty((self.N, self.D), dtype=torch.float32, device=self.device)
+        _lib.check(self._lib.ash_get_coefficients(self._h, _ptr(out), _stream_ptr(stream)), "ash_get_coefficients")
+        return out
 
     def set_amplitude(self, amp: torch.Tensor, stream=None):
         _need(amp, torch.float32, (self.ny, self.nx), "amp")

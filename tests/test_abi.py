@@ -91,6 +91,7 @@ def test_later_entry_points_reject_bad_arguments_without_gpu(lib):
         assert getattr(lib, fn)(None, 4) == -1, fn
     assert lib.ash_batch_standalone(None) == -1
     assert lib.ash_debug_wait_timeout(None, 16, None) == INV
+    assert lib.ash_get_coefficients(None, one, None) == INV
     b = ctypes.c_void_p(0)
     assert lib.ash_batch_create(ctypes.byref(b), 0, None, None) == INV
     assert lib.ash_batch_create_ex(ctypes.byref(b), 1, one, -1, None) == INV

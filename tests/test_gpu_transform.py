@@ -127,6 +127,16 @@ def test_user_basis_adjoint_and_gradients(variant):
     assert not (h.launch_info()["kernels"] & 8)   # no tensor-core moments for a caller basis
 
 
+def test_coefficients_round_trip():
+    p = random_problem(24, 64, 48, 30, [2, 3, 4, 5, 6])
+    h = _holo(p)
+    np.testing.assert_array_equal(h.coefficients().cpu().numpy(), p.coeff)
+    C2 = torch.from_numpy(p.coeff * 0.5).cuda()
+    h.set_coefficients(C2)
+    got = h.coefficients()
+    assert torch.equal(got, C2) and got.data_ptr() != C2.data_ptr()
+
+
 def test_set_amplitude_changes_the_nearfield():
     p = random_problem(23, 96, 72, 60, list(range(2, 12)))
     h = _holo(p)
