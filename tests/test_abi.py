@@ -130,3 +130,11 @@ def test_python_binding_rejects_cpu_tensors():
     from paper_2505_08777_gb300 import Hologram
     with pytest.raises(ValueError):
         Hologram(torch.ones(4, 4), torch.zeros(2, 3), noll=[2, 3, 4])
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    # no CPU fallback: without libash.so the binding raises instead of computing
+    from paper_2505_08777_gb300 import _lib
+    monkeypatch.setattr(_lib, "_lib", None)
+    with pytest.raises(ImportError, match="not built"):
+        _lib.load(str(tmp_path / "libash.so"))
