@@ -15,7 +15,7 @@ import torch
 
 from .hologram import Hologram
 
-__all__ = ["SpotField", "spot_field"]
+__all__ = ["SpotField", "spot_field", "spot_intensity_loss"]
 
 
 class SpotField(torch.autograd.Function):
