@@ -31,30 +31,124 @@ if ROOT not in sys.path:
 METRIC = "spot-kernel Gterm/s (N*M phase+sincos+cMAC) fwd+adj; WGS iter/s at 1024^2 x 400"
 UNIT = "Gterm/s"
 L2_FLUSH_BYTES = 256 << 20
-MUFU_PER_CLK_PER_SM = 16          # measured: sin.approx / cos.approx throughput per SM per clock
+# Nominal pipe rates per SM per clock; the bench lines use the rates the
+# library's probe (ash_probe_rates) measures on the GPU at hand instead.
+MUFU_PER_CLK_PER_SM = 16          # sin.approx / cos.approx results
 MUFU_PER_TERM = 2                 # one sin and one cos per term
-FP32_PER_CLK_PER_SM = 128         # FP32 lanes per SM (an FFMA2 occupies two lane-slots)
-# FP32 lane-operations per term: on the MUFU path the argument scaling (1)
-# and the complex multiply-accumulate (4); on the FP32 path the sin / cos
-# polynomial with its reduction (16) and the same multiply-accumulate (4)
+FP32_PER_CLK_PER_SM = 128         # FP32 lane results (an FFMA2 gives two)
+# FP32 lane-operations per term of this design: on the MUFU path the
+# argument scaling (1) and the complex multiply-accumulate (4); on the FP32
+# path the sin / cos polynomial with its reduction (16) and the same
+# multiply-accumulate (4)
 FP32_PER_TERM_MUFU_PATH = 5
 FP32_PER_TERM_POLY_PATH = 20
-MAX_SM_MHZ = 2070.0
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
-# ncu capture of the named kernel on this workload; see profiles/. Reported as
-# roofline.traffic only for the kernel build these counters were taken on.
-NCU_TRAFFIC_BYTES = {"k_tc_forward<1>": 146.443008e6 + 3.285504e6, "k_tc_adjoint<1>": 151.223040e6 + 7.863296e6}
+MAX_SM_MHZ = 2070.0               # nominal maximum SM clock (MEASURED_PEAKS.json's sm_max_mhz when present)
+# ncu DRAM traffic of the transforms: a summary under profiles/ whose rows
+# name the kernel, its dram bytes per launch and the hash of the kernel
+# sources the counters were taken on (reported only while they match)
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_k_tc_transforms_c2_1024x1024_N400_D10.md")
+TRAFFIC_SOURCES = ["common.cuh", "tc_common.cuh", "tc_kernels.cuh", "tc_launch.h", "tc.cu"]
 
 
-def alu_terms_per_clk_per_sm():
+def alu_terms_per_clk_per_sm(mufu=MUFU_PER_CLK_PER_SM, fp32=FP32_PER_CLK_PER_SM):
     """Two-pipe ceiling of a term (sin, cos, complex MAC): a share a of the
     terms takes its sin / cos on the FP32 pipe, the rest on the MUFU pipe;
     the best a equalises the two pipes' times,
     MUFU_PER_TERM (1 - a) / MUFU rate = (f_m (1 - a) + f_p a) / FP32 rate."""
-    m, F = MUFU_PER_TERM / MUFU_PER_CLK_PER_SM, 1.0 / FP32_PER_CLK_PER_SM
+    m, F = MUFU_PER_TERM / mufu, 1.0 / fp32
     fm, fp = FP32_PER_TERM_MUFU_PATH, FP32_PER_TERM_POLY_PATH
     a = (m - F * fm) / (m + F * (fp - fm))
     return 1.0 / (m * (1.0 - a))
+
+
+def planned_terms_per_clk_per_sm(D, mufu=MUFU_PER_CLK_PER_SM, fp32=FP32_PER_CLK_PER_SM):
+    """The FP32/SFU roofline of a term with the phase on the FP32 pipe: D
+    FMAs of the phase, about 3 FP32 operations of range reduction and 4 of
+    the complex multiply-accumulate (D + 7 lane operations), and one sin and
+    one cos on the MUFU: min(FP32 rate / (D + 7), MUFU rate / 2)."""
+    return min(fp32 / (D + 7.0), mufu / 2.0)
+
+
+def max_sm_mhz():
+    """The GPU's maximum SM clock: MEASURED_PEAKS.json (driver-written) when
+    present, else the nominal figure."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            v = float(json.load(f).get("sm_max_mhz") or 0.0)
+        if v > 0:
+            return v, "MEASURED_PEAKS.json sm_max_mhz"
+    except (OSError, ValueError):
+        pass
+    return MAX_SM_MHZ, "nominal maximum SM clock"
+
+
+def probe_rates(lib, stream_ptr):
+    """Per-SM unit rates measured by the library's probe on this GPU."""
+    import ctypes
+    from paper_2505_08777_gb300 import _lib
+    out = (ctypes.c_double * 6)()
+    _lib.check(lib.ash_probe_rates(out, stream_ptr), "ash_probe_rates")
+    v = list(out)
+    return {"mufu_sincos_per_clk_sm": v[0], "ffma_lanes_per_clk_sm": v[1], "ffma2_lanes_per_clk_sm": v[2],
+            "ex2_per_clk_sm": v[3], "probe_sm_mhz": v[4], "sms": int(v[5]),
+            "how": "ash_probe_rates: one 1024-thread CTA per SM, independent chains, SM cycle counter"}
+
+
+def source_hash(names=TRAFFIC_SOURCES):
+    import hashlib
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_2505_08777_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def ncu_traffic(kernel):
+    """dram bytes per launch of `kernel` from the committed ncu summary, if
+    it was taken on the current kernel sources; else None."""
+    try:
+        rows = open(TRAFFIC_FILE).read().splitlines()
+    except OSError:
+        return None
+    want = source_hash()
+    for r in rows:
+        cells = [c.strip() for c in r.strip().strip("|").split("|")]
+        if len(cells) >= 3 and cells[0] == kernel and cells[2] == want:
+            try:
+                return float(cells[1])
+            except ValueError:
+                return None
+    return None
+
+
+def roofline_alu(achieved, D, rates, kernel, algorithmic):
+    """roofline object of an ALU-bound transform: peak = the FP32/SFU
+    roofline R_terms = SMs x f_clk x min(FP32 / (D + 7), MUFU / 2) from the
+    probe's measured rates at the maximum SM clock; the design's two-pipe
+    ceiling (tensor-core phases, sin/cos shared by the MUFU and an FP32
+    polynomial) and the MUFU-only bound beside it."""
+    mhz, mhz_src = max_sm_mhz()
+    sms = rates["sms"]
+    mufu = rates["mufu_sincos_per_clk_sm"]
+    fp32 = max(rates["ffma_lanes_per_clk_sm"], rates["ffma2_lanes_per_clk_sm"])
+    per_sm = planned_terms_per_clk_per_sm(D, mufu, fp32)
+    peak = sms * per_sm * mhz * 1e6 / 1e9
+    two = sms * alu_terms_per_clk_per_sm(mufu, fp32) * mhz * 1e6 / 1e9
+    mufu_only = sms * (mufu / MUFU_PER_TERM) * mhz * 1e6 / 1e9
+    return {
+        "bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "Gterm/s",
+        "frac": achieved / peak, "traffic": ncu_traffic(kernel.split(" ")[0]),
+        "peak_basis": f"R_terms = SMs x f_clk x min(FP32/(D+7), MUFU/2) = {sms} x {mhz:.0f} MHz ({mhz_src}) x "
+                      f"min({fp32:.1f}/{D + 7}, {mufu:.2f}/2) = {per_sm:.2f} terms/clk/SM; rates measured by "
+                      f"ash_probe_rates on this GPU",
+        "two_pipe_peak": two, "frac_two_pipe": achieved / two,
+        "two_pipe_basis": f"tensor-core phases; a term costs 2 MUFU + {FP32_PER_TERM_MUFU_PATH} FP32 or "
+                          f"{FP32_PER_TERM_POLY_PATH} FP32 (polynomial sin/cos), best split "
+                          f"{alu_terms_per_clk_per_sm(mufu, fp32):.2f} terms/clk/SM",
+        "mufu_only_peak": mufu_only, "frac_mufu_only": achieved / mufu_only,
+        "algorithmic_per_launch": algorithmic, "rates": rates,
+    }
 
 
 WORKLOAD_TEXT = {
@@ -85,11 +179,12 @@ def _args():
     ap.add_argument("--batch-solo-terms", type=int, default=None,
                     help="c5: N*M threshold above which a batch member runs standalone in the batch's graph "
                          "(default: the library's)")
-    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5", "zsub", "cg"],
+    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5", "zsub", "cg", "peaks"],
                     help="c2 (default, the headline): anisoplanatic 2D WGS; c3: 3D volume WGS; "
                          "c4: autograd + Adam on 8 holograms; c5: 64 uneven holograms, batched vs looped; "
                          "zsub: simulated Zernike-subtraction calibration round on the c2 system; "
-                         "cg: conjugate-gradient top-hat refinement after WGS on c2")
+                         "cg: conjugate-gradient top-hat refinement after WGS on c2; "
+                         "peaks: the per-SM pipe rates the roofline is built from (ash_probe_rates)")
     return ap.parse_args()
 
 
@@ -273,6 +368,8 @@ def main():
         return bench_zsub(args)
     if args.config == "cg":
         return bench_cg(args)
+    if args.config == "peaks":
+        return bench_peaks(args)
     import torch
 
     from paper_2505_08777_gb300 import Hologram
@@ -385,9 +482,7 @@ def main():
     gterm = {k: NM / (kms[k] * 1e-3) / 1e9 for k in ("forward", "adjoint", "grad_coeff") if kms[k] > 0}
 
     clk = clocks.summary()
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = sms * alu_terms_per_clk_per_sm() * MAX_SM_MHZ * 1e6 / 1e9
-    mufu_peak = sms * (MUFU_PER_CLK_PER_SM / MUFU_PER_TERM) * MAX_SM_MHZ * 1e6 / 1e9
+    rates = probe_rates(L, ctypes.c_void_p(stream.cuda_stream))
     dom = "forward" if kms["forward"] >= kms["adjoint"] else "adjoint"
     P = 8 if p.D <= 12 else 4
     linfo = h.launch_info()
@@ -403,18 +498,10 @@ def main():
                                 f"spots into TMEM, sincos + packed complex MAC, arg epilogue)") if adj_tc else
                                f"k_adjoint<D={p.D},P={P}> (pixel-stationary adjoint, arg epilogue)"}
     achieved = gterm[dom]
-    roofline = {
-        "bound": "alu", "kernel": kernel_names[dom],
-        "achieved": achieved, "peak": peak, "unit": "Gterm/s", "frac": achieved / peak,
-        "peak_basis": f"two-pipe ALU ceiling: {MUFU_PER_CLK_PER_SM} sin/cos per clk per SM (MUFU, measured) and "
-                      f"{FP32_PER_CLK_PER_SM} FP32 lanes per SM; a term costs 2 MUFU + {FP32_PER_TERM_MUFU_PATH} FP32 "
-                      f"or {FP32_PER_TERM_POLY_PATH} FP32 (polynomial sin/cos), best split "
-                      f"{alu_terms_per_clk_per_sm():.2f} terms/clk/SM; {sms} SMs x {MAX_SM_MHZ:.0f} MHz max clock",
-        "mufu_only_peak": mufu_peak,
-        "algorithmic_per_launch": f"N*M = {NM} terms",
-        "traffic": NCU_TRAFFIC_BYTES.get(kernel_names[dom].split(" ")[0]) if args.config == "c2" else None,
-        "frac_at_sampled_clock": (achieved / (peak * clk["sm_mhz"] / MAX_SM_MHZ)) if clk.get("sm_mhz") else None,
-    }
+    roofline = roofline_alu(achieved, p.D, rates, kernel_names[dom], f"N*M = {NM} terms")
+    roofline["per_kernel_frac"] = {k: v / roofline["peak"] for k, v in gterm.items()}
+    if clk.get("sm_mhz"):
+        roofline["frac_at_sampled_clock"] = achieved / (roofline["peak"] * clk["sm_mhz"] / max_sm_mhz()[0])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -447,9 +534,14 @@ def main():
     return 0
 
 
-def _peak_gterm(torch, dev):
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    return sms * alu_terms_per_clk_per_sm() * MAX_SM_MHZ * 1e6 / 1e9
+def _peak_gterm(torch, dev, D=10):
+    """R_terms (the FP32/SFU roofline, see roofline_alu) for D modes from
+    the probe's measured rates on this GPU, at the maximum SM clock."""
+    from paper_2505_08777_gb300 import _lib
+    rates = probe_rates(_lib.load(), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    mufu = rates["mufu_sincos_per_clk_sm"]
+    fp32 = max(rates["ffma_lanes_per_clk_sm"], rates["ffma2_lanes_per_clk_sm"])
+    return rates["sms"] * planned_terms_per_clk_per_sm(D, mufu, fp32) * max_sm_mhz()[0] * 1e6 / 1e9
 
 
 def bench_autograd(args):
@@ -748,8 +840,7 @@ def bench_cg(args):
         e2e_ms += a.elapsed_time(b)
     terms = iters * 3 * p.N * p.nx * p.ny + 2 * p.N * p.nx * p.ny    # 3 transforms per iteration + the start
     value = terms * args.steps / (ms * 1e-3) / 1e9
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = sms * alu_terms_per_clk_per_sm() * MAX_SM_MHZ * 1e6 / 1e9
+    peak = _peak_gterm(torch, dev, p.D)
     line = {"metric": "conjugate-gradient refinement Gterm/s (2 forwards + 1 gradient adjoint per iteration), "
                       "CG iterations/s, workload cg",
             "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -841,8 +932,7 @@ def bench_zsub(args):
     per_order = 1 + len(ZSUB_DELTAS)               # one adjoint + K forwards
     terms = len(modes) * per_order * p.N * p.nx * p.ny
     value = terms * args.steps / (ms * 1e-3) / 1e9
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = sms * alu_terms_per_clk_per_sm() * MAX_SM_MHZ * 1e6 / 1e9
+    peak = _peak_gterm(torch, dev, p.D)
     line = {"metric": "Zernike-subtraction calibration Gterm/s (baseline adjoint + 7-offset sweep per order), "
                       "rounds/s, workload zsub",
             "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -944,6 +1034,41 @@ def bench_batch(args):
             "clocks": clocks.summary()}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = _sampled_baseline("wgs", ps[:8], "one WGS iteration of the first 8 holograms")
+    print(json.dumps(line))
+    return 0
+
+
+def bench_peaks(args):
+    """The per-SM unit rates behind the roofline, measured by the library's
+    probe (`--steps` repetitions, median), with the SM clocks sampled while
+    it runs; prints one JSON line."""
+    import torch
+
+    from paper_2505_08777_gb300 import _lib
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    L = _lib.load()
+    sp = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for _ in range(max(args.warmup, 1)):
+        probe_rates(L, sp)
+    runs = []
+    with ClockSampler(0) as clocks:
+        for _ in range(max(args.steps, 1)):
+            runs.append(probe_rates(L, sp))
+    keys = ["mufu_sincos_per_clk_sm", "ffma_lanes_per_clk_sm", "ffma2_lanes_per_clk_sm", "ex2_per_clk_sm",
+            "probe_sm_mhz"]
+    med = {k: float(np.median([r[k] for r in runs])) for k in keys}
+    mhz, mhz_src = max_sm_mhz()
+    sms = runs[0]["sms"]
+    fp32 = max(med["ffma_lanes_per_clk_sm"], med["ffma2_lanes_per_clk_sm"])
+    line = {"metric": "per-SM pipe rates (results per clock per SM)", "value": med["mufu_sincos_per_clk_sm"],
+            "unit": "sin/cos per clk per SM", "n_gpus": 1, "steps": len(runs), "warmup": args.warmup,
+            "rates": med | {"sms": sms}, "runs": runs,
+            "r_terms_gterm_s": {str(D): sms * planned_terms_per_clk_per_sm(D, med["mufu_sincos_per_clk_sm"], fp32)
+                                * mhz * 1e6 / 1e9 for D in (5, 10, 11)},
+            "two_pipe_gterm_s": sms * alu_terms_per_clk_per_sm(med["mufu_sincos_per_clk_sm"], fp32) * mhz * 1e6 / 1e9,
+            "clock_for_peaks_mhz": mhz, "clock_source": mhz_src, "clocks": clocks.summary(),
+            "higher_is_better": True, "data": "synthetic", "dtype": "f32"}
     print(json.dumps(line))
     return 0
 

@@ -121,6 +121,26 @@ ash_status ash_debug_fail_after(int n_calls);
 ash_status ash_debug_sincos(const float *x, int n, float *s, float *c, int path, void *stream);
 
 /*
+ * Per-SM unit rates that bound the transforms (Methods, "Computational
+ * Scaling": every term needs a phase, a sine, a cosine and a complex
+ * multiply-accumulate, so the chip's sin/cos and FP32 rates set the
+ * roofline). Measured on the current device: one CTA of 1024 threads per SM,
+ * independent chains of one operation, timed by the SM cycle counter.
+ *   out  host double[ASH_PROBE_COUNT]:
+ *        [0] sin.approx / cos.approx results per clock per SM (MUFU)
+ *        [1] fma.rn.f32 lane results per clock per SM
+ *        [2] fma.rn.f32x2 lane results per clock per SM (two per instruction)
+ *        [3] ex2.approx results per clock per SM (MUFU)
+ *        [4] SM clock during the probe, MHz (cycles / CUDA-event time)
+ *        [5] SMs that ran the probe
+ * Allocates two small device arrays on `stream` (stream-ordered) and
+ * synchronises it; takes about 10 ms. ASH_ERR_INVALID_ARG for a NULL out,
+ * ASH_ERR_CUDA if a launch fails.
+ */
+#define ASH_PROBE_COUNT 6
+ash_status ash_probe_rates(double *out, void *stream);
+
+/*
  * Create a hologram (paper Sec. II: kernels K_n built from the N x D matrix
  * w_d^(n) and the per-pixel basis, Methods "Computational Scaling").
  *   out     host: receives the handle.

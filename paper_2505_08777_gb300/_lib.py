@@ -26,6 +26,7 @@ SIGNATURES = {
     "ash_set_allocator": (c_int, [ALLOC_FN, FREE_FN, c_void_p]),
     "ash_debug_fail_after": (c_int, [c_int]),
     "ash_debug_sincos": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int, c_void_p]),
+    "ash_probe_rates": (c_int, [ctypes.POINTER(ctypes.c_double), c_void_p]),
     "ash_zsub_sweep": (c_int, [c_void_p, c_void_p, c_int, c_float_p, c_int, c_void_p, c_void_p]),
     "ash_cg_refine": (c_int, [c_void_p, c_void_p, c_void_p, c_int, ctypes.c_float, c_void_p, c_void_p]),
     "ash_zsub_estimate": (c_int, [c_void_p, c_float_p, c_int, c_int, c_void_p, c_void_p, c_int, c_int, c_void_p]),

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libash.so")
 
-SOURCES = ["api.cu", "basis_host.cu", "principal.cu", "inst_r0.cu", "inst_r1.cu", "inst_r2.cu", "inst_r3.cu", "tc.cu", "tc_grad.cu", "noalloc.cu", "batch.cu", "cg.cu", "zsub.cu"]
+SOURCES = ["api.cu", "basis_host.cu", "principal.cu", "inst_r0.cu", "inst_r1.cu", "inst_r2.cu", "inst_r3.cu", "tc.cu", "tc_grad.cu", "noalloc.cu", "batch.cu", "cg.cu", "zsub.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

@@ -138,3 +138,7 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(_lib, "_lib", None)
     with pytest.raises(ImportError, match="not built"):
         _lib.load(str(tmp_path / "libash.so"))
+
+
+def test_probe_rejects_null_output(lib):
+    assert lib.ash_probe_rates(None, None) == 1
