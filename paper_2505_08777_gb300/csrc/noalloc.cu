@@ -192,20 +192,39 @@ struct DeviceSetup {
   bool ready = false;
   float* scratch = nullptr;   // device address of g_noalloc_scratch
   int sms = 0;
+  int per_sm[ASH_MAX_MODES + 1] = {};   // resident CTAs per SM of the kernel for D modes
 };
 
 std::mutex g_setup_mu;
 DeviceSetup g_setup[kMaxDevices];
+
+// Resident CTAs per SM of the kernel for D modes (part of the one-time
+// set-up per device, so that a call does no occupancy query).
+template <int D>
+cudaError_t occupancy_of(int* out) {
+  constexpr int P = pixels_per_thread(D);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_forward_noalloc<D, P>, kTilePix / P,
+                                                       fwd_smem_bytes(D));
+}
+
+template <int LO, int HI>
+cudaError_t fill_occupancy(int* per_sm) {
+  if constexpr (LO > HI) {
+    return cudaSuccess;
+  } else {
+    cudaError_t e = occupancy_of<LO>(&per_sm[LO]);
+    if (e != cudaSuccess) return e;
+    return fill_occupancy<LO + 1, HI>(per_sm);
+  }
+}
 
 template <int D>
 cudaError_t launch_direct(const DirectParams& base, const DeviceSetup& ds, float* E, cudaStream_t s) {
   constexpr int P = pixels_per_thread(D);
   constexpr int NT = kTilePix / P;
   constexpr int NW = NT / 32;
-  int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_forward_noalloc<D, P>, NT,
-                                                                fwd_smem_bytes(D));
-  if (e != cudaSuccess) return e;
+  const int per_sm = ds.per_sm[D];
+  cudaError_t e = cudaSuccess;
   const long long cap_rows = (long long)(kNoallocScratchFloats / (2 * (size_t)base.N));
   long long grid = (long long)ds.sms * (per_sm > 0 ? per_sm : 1);
   if (grid > base.T) grid = base.T;
@@ -269,6 +288,11 @@ extern "C" ash_status ash_forward_noalloc(int nx, int ny, const float* amp, cons
       if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(ASH_ERR_CUDA, "noalloc: cudaDeviceGetAttribute failed");
+      }
+      e = fill_occupancy<1, ASH_MAX_MODES>(slot.per_sm);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ASH_ERR_CUDA, "noalloc: occupancy query failed");
       }
       slot.scratch = static_cast<float*>(ptr);
       slot.ready = true;
