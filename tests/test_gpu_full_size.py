@@ -1,0 +1,112 @@
+"""Full-size parity of the benchmark workloads.
+
+* Weighted GS at the benchmark sizes, the whole loop (Sec. II / Sec. III):
+  the anisoplanatic 2D array (1024^2, N = 400, D = 10, 50 iterations) and
+  the 3D volume (1920 x 1152, N = 2000, D = 11, 100 iterations, on a seeded
+  random 1/16 of the pixels: the amplitude is 0 on the others, and the
+  oracle sums over the kept pixels only). The final spot uniformity must be
+  within 1e-3 absolute of the oracle's, whose values
+  tests/golden/make_wgs_golden.py wrote from `oracle/` alone.
+* The gradient at the differentiable workload's size (1024^2, N = 1024,
+  D = 10; Methods, gradients through the transform): dL/dC on 16 sampled
+  spots over all pixels and dL/dphase on 4096 sampled pixels, against the
+  oracle's closed form on the oracle's own dL/dE from a full forward, at
+  1e-3 normwise.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from gpu_helpers import GRAD_TOL, UNIF_TOL, basis_at  # noqa: E402
+from oracle import grad as ograd  # noqa: E402
+from oracle import transform, zernike  # noqa: E402
+from workloads import config_c2, config_c3, config_c4, masked_amplitude, pixel_sample  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "wgs_full_loops.json")
+WORKERS = os.cpu_count() or 4
+
+
+def _golden(key):
+    with open(GOLDEN) as f:
+        return json.load(f)[key]
+
+
+def _wgs(p):
+    from paper_2505_08777_gb300 import Hologram
+    h = Hologram(torch.from_numpy(p.amp).cuda(), torch.from_numpy(p.coeff).cuda(), noll=p.noll)
+    ph = torch.from_numpy(p.phase0).cuda().clone()
+    w = torch.from_numpy(p.target).cuda().clone()
+    T = torch.from_numpy(p.target).cuda()
+    _, met = h.wgs(ph, w, T, p.iters)
+    torch.cuda.synchronize()
+    h.check()
+    kernels = h.launch_info()["kernels"]
+    h.close()
+    return met.cpu().numpy().astype(np.float64), kernels
+
+
+def test_wgs_full_loop_2d_array_matches_oracle():
+    g = _golden("c2")
+    p = config_c2(1)
+    assert (p.nx, p.ny, p.N, p.D, p.iters) == (g["nx"], g["ny"], g["N"], g["D"], g["iters"])
+    met, kernels = _wgs(p)
+    assert kernels & 6 == 6   # the benchmark's tensor-core forward and adjoint
+    assert abs(met[0] - g["uniformity"]) <= UNIF_TOL, (met[0], g["uniformity"])
+    assert abs(met[1] - g["efficiency"]) <= 1e-3 * g["efficiency"], (met[1], g["efficiency"])
+
+
+def test_wgs_full_loop_3d_volume_matches_oracle():
+    g = _golden("c3_sampled")
+    p = config_c3(1)
+    idx = pixel_sample(p.nx, p.ny, g["sample_frac"], g["sample_seed"])
+    assert idx.size == g["pixels_summed"]
+    p = masked_amplitude(p, idx)
+    assert (p.nx, p.ny, p.N, p.D, p.iters) == (g["nx"], g["ny"], g["N"], g["D"], g["iters"])
+    met, kernels = _wgs(p)
+    assert kernels & 6 == 6
+    assert abs(met[0] - g["uniformity"]) <= UNIF_TOL, (met[0], g["uniformity"])
+    # the library's efficiency divides by nx * ny pixels, the oracle's by the pixels it summed
+    eff = met[1] * p.nx * p.ny / idx.size
+    assert abs(eff - g["efficiency"]) <= 1e-3 * g["efficiency"], (eff, g["efficiency"])
+
+
+def test_gradient_at_the_differentiable_workload_size():
+    from paper_2505_08777_gb300 import Hologram
+    p = config_c4(1)
+    assert (p.nx, p.ny, p.N, p.D) == (1024, 1024, 1024, 10)
+    Z = zernike.basis(p.nx, p.ny, p.noll)
+    C = p.coeff.astype(np.float64)
+    A = p.amp.astype(np.float64).ravel()
+    phase = p.phase0.astype(np.float64).ravel()
+    f = transform.field(A, phase)
+    E = transform.forward(f, C, Z, workers=WORKERS)
+    gE = ograd.grad_E(E, p.target).astype(np.complex64)
+    gE64 = gE.astype(np.complex128)
+
+    h = Hologram(torch.from_numpy(p.amp).cuda(), torch.from_numpy(p.coeff).cuda(), noll=p.noll)
+    assert h.launch_info()["kernels"] & 8   # tensor-core moment pass
+    dph, dC = h.grad(torch.from_numpy(p.phase0).cuda(), torch.from_numpy(gE).cuda())
+    torch.cuda.synchronize()
+    h.check()
+    dph = dph.cpu().numpy().astype(np.float64).ravel()
+    dC = dC.cpu().numpy().astype(np.float64)
+    h.close()
+
+    rng = np.random.default_rng(4)
+    spots = np.sort(rng.choice(p.N, 16, replace=False))
+    S = ograd.moments(f, C[spots], Z)
+    dC_ref = np.imag(np.conj(gE64[spots])[:, None] * S)
+    r2 = np.linalg.norm(dC[spots] - dC_ref) / np.linalg.norm(dC_ref)
+
+    pix = np.sort(rng.choice(p.nx * p.ny, 4096, replace=False))
+    Zp = basis_at(p, pix)
+    hp = transform.adjoint(gE64, C, Zp)
+    dph_ref = -np.imag(f[pix] * np.conj(hp))
+    r1 = np.linalg.norm(dph[pix] - dph_ref) / np.linalg.norm(dph_ref)
+    assert r1 <= GRAD_TOL and r2 <= GRAD_TOL, (r1, r2)

@@ -31,7 +31,7 @@ import numpy as np
 __all__ = [
     "Problem", "gaussian_amplitude", "flat_amplitude", "random_phase",
     "config_c1", "config_c2", "config_c3", "config_c4", "config_c5",
-    "make_config", "random_problem", "CONFIG_NAMES",
+    "make_config", "random_problem", "CONFIG_NAMES", "pixel_sample", "masked_amplitude",
 ]
 
 
@@ -303,3 +303,20 @@ def random_problem(seed: int, nx: int, ny: int, N: int, noll, tilt_span: float =
     target = rng.uniform(target_range[0], target_range[1], size=N)
     return Problem(f"rand_{nx}x{ny}_N{N}_D{D}_s{seed}", nx, ny, amp, random_phase(rng, nx, ny),
                    noll, C.astype(np.float32), target.astype(np.float32), 10)
+
+
+def pixel_sample(nx: int, ny: int, frac: float, seed: int) -> np.ndarray:
+    """Seeded random subset of the flat pixel indices (each pixel kept with
+    probability `frac`), sorted. A problem restricted to these pixels is the
+    same problem with the illumination amplitude set to 0 everywhere else."""
+    rng = np.random.default_rng(seed)
+    keep = rng.random(nx * ny) < frac
+    return np.flatnonzero(keep)
+
+
+def masked_amplitude(p: Problem, idx: np.ndarray) -> Problem:
+    """Copy of `p` whose amplitude is kept on the flat pixels `idx` and is 0
+    elsewhere (no renormalisation: the weighted-GS loop is scale-invariant)."""
+    amp = np.zeros(p.M, np.float32)
+    amp[idx] = p.amp.ravel()[idx]
+    return dataclasses.replace(p, amp=amp.reshape(p.ny, p.nx), name=p.name + f"_sampled{idx.size}")
