@@ -176,6 +176,10 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--shard", action="store_true",
+                    help="c2 as ONE hologram sharded by pixel rows over the ranks: band handles, one NCCL "
+                         "all-reduce of the N spot fields per forward, replicated spot update, local adjoint "
+                         "(strong scaling); default: one independent hologram per rank (weak scaling)")
     ap.add_argument("--batch-solo-terms", type=int, default=None,
                     help="c5: N*M threshold above which a batch member runs standalone in the batch's graph "
                          "(default: the library's)")
@@ -370,6 +374,8 @@ def main():
         return bench_cg(args)
     if args.config == "peaks":
         return bench_peaks(args)
+    if args.shard:
+        return bench_shard(args)
     import torch
 
     from paper_2505_08777_gb300 import Hologram
@@ -1070,6 +1076,88 @@ def bench_peaks(args):
             "clock_for_peaks_mhz": mhz, "clock_source": mhz_src, "clocks": clocks.summary(),
             "higher_is_better": True, "data": "synthetic", "dtype": "f32"}
     print(json.dumps(line))
+    return 0
+
+
+def bench_shard(args):
+    """c2 as one hologram sharded over the ranks by whole 32-row tile bands
+    (Methods, per-pixel independence): each rank holds a band handle; per
+    WGS iteration its forward partial fields, one all-reduce of N complex64
+    (NCCL), the replicated spot update and the band's adjoint. One step =
+    one full solve (50 iterations + the final forward) of the one hologram;
+    value = its terms / the max over ranks of the step time."""
+    import torch
+
+    from paper_2505_08777_gb300.shard import band_holograms, row_block, sharded_wgs
+    from workloads import config_c2
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    p = config_c2(1)
+    iters = p.iters
+    r0, r1 = row_block(p.ny, rank, world)
+    amp = torch.from_numpy(p.amp).to(dev)
+    coeff = torch.from_numpy(p.coeff).to(dev)
+    bands = band_holograms(amp, coeff, p.noll, p.ny, [(r0, r1)])
+    sa = torch.tensor([bands[0].band_info()[2]], dtype=torch.float64, device=dev)
+    allreduce = None
+    if world > 1:
+        torch.distributed.all_reduce(sa)
+        allreduce = lambda E: torch.distributed.all_reduce(E)   # noqa: E731
+    sum_a2 = float(sa.item())
+    ph0 = torch.from_numpy(p.phase0[r0:r1]).to(dev)
+    T = torch.from_numpy(p.target).to(dev)
+    ph = ph0.clone()
+    w = T.clone()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ph.copy_(ph0)
+        w.copy_(T)
+        return sharded_wgs(bands, [ph], w, T, iters, allreduce=allreduce, sum_a2=sum_a2)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    total = 0.0
+    with ClockSampler(local) as clocks:
+        for _ in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            _, met = step()
+            b.record(stream)
+            b.synchronize()
+            total += a.elapsed_time(b)
+    if world > 1:
+        torch.distributed.barrier()
+    t = torch.tensor([total], device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    total_max = float(t.item())
+    terms = (2 * iters + 1) * p.N * p.M
+    value = terms * args.steps / (total_max * 1e-3) / 1e9
+    line = {"metric": METRIC + " (one hologram sharded by pixel rows)", "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_max / args.steps,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": _workload_config(p, iters) | {"parallelism": f"pixel rows over {world} rank(s), "
+                                                                   "one all-reduce of N complex64 per forward",
+                                                    "band_rows": [r0, r1]},
+            "wgs_iter_per_s": iters * args.steps / (total_max * 1e-3),
+            "final_uniformity": float(met[0].item()), "clocks": clocks.summary()}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
     return 0
 
 

@@ -185,6 +185,63 @@ ash_status ash_hologram_create_mixed(ash_hologram **out, int nx, int ny, const f
                                      const float *coeff, void *stream);
 
 /*
+ * Create a band hologram: rows [row0, row1) of an SLM grid of nx x ny_full
+ * pixels, for pixel-sharded transforms over several GPUs (Methods,
+ * "Computational Scaling": each pixel's kernel values depend only on that
+ * pixel and the global N x D matrix, so the forward is a sum over pixel
+ * blocks and the adjoint is independent per pixel). The band uses the full
+ * grid's coordinates (unit disk of radius min(nx, ny_full)/2 about the full
+ * grid's centre), tiles and tile anchors, so that
+ *   sum over bands of ash_forward(band)  ==  ash_forward(full grid)
+ *   ash_adjoint(band)                    ==  the band's rows of ash_adjoint(full grid)
+ * up to the summation order of fp32 partial sums.
+ *   row0, row1  0 <= row0 < row1 <= ny_full; row0 a multiple of 32 and row1
+ *               a multiple of 32 or ny_full (whole 32-row tile rows).
+ *   amp     device float[(row1-row0)*nx]: the band's rows of the amplitude.
+ *   basis   device float[D*(row1-row0)*nx] (the band's rows of each mode) or
+ *           NULL with `noll`.
+ * Phases, fields and outputs of the band's calls are (row1-row0) x nx.
+ * Other arguments and behaviour as ash_hologram_create.
+ */
+ash_status ash_hologram_create_band(ash_hologram **out, int nx, int ny_full, int row0, int row1,
+                                    const float *amp, int D, const int *noll, const float *basis, int N,
+                                    const float *coeff, void *stream);
+
+/*
+ * Band of a handle: first row and rows of the full grid (0 and ny for a
+ * handle that is not a band), and the handle's sum of A^2 over its own
+ * pixels (host double). Any pointer may be NULL. Reading sum_a2
+ * synchronises the device.
+ */
+ash_status ash_hologram_band(const ash_hologram *h, int *row0, int *ny_full, double *sum_a2);
+
+/*
+ * The weighted-GS spot update alone (Sec. II / Sec. III; rule and options as
+ * in ash_wgs_iterate and ash_wgs_set_options): from the spot fields E,
+ *   w <- w (T^ / E^)^p, renormalised;  y = w exp(i psi)  (psi = arg E, or the
+ *   held phases when phase fixing is on).
+ *   E       device float[2N] complex64 (e.g. the all-reduced partial fields
+ *           of all bands of a sharded grid).
+ *   w       device float[N], updated in place; target device float[N].
+ *   y       device float[2N] complex64, written: the adjoint's spot weights.
+ * Uses and updates the handle's held spot phases like ash_wgs_iterate. A
+ * sharded loop runs it on every rank with the same E, so every rank holds
+ * the same w and y.
+ */
+ash_status ash_spot_update(ash_hologram *h, const float *E, float *w, const float *target, float *y,
+                           void *stream);
+
+/*
+ * Spot metrics of E (as ash_wgs_iterate's metrics_out): uniformity,
+ * efficiency sum|E|^2 / (nx * ny_full * sum A^2), sum |E|^2, min |E|^2/T^2.
+ *   sum_a2  the sum of A^2 over the whole grid (host double; for a sharded
+ *           grid the sum over all bands), or 0 for the handle's own.
+ *   metrics_out  device float[4].
+ */
+ash_status ash_spot_metrics(ash_hologram *h, const float *E, const float *target, double sum_a2,
+                            float *metrics_out, void *stream);
+
+/*
  * Principal isoplanatic modes (paper, Methods "Anisoplanatic Singular Value
  * Decomposition"; Sec. III "principal isoplanatic modes"): the SVD
  * W = U Sigma V^T of the N x ncols block W of the coefficient matrix formed

@@ -34,6 +34,11 @@ SIGNATURES = {
                                     c_int, c_void_p, c_void_p]),
     "ash_hologram_create_mixed": (c_int, [ctypes.POINTER(c_void_p), c_int, c_int, c_void_p, c_int, c_int_p, c_int,
                                           ctypes.POINTER(ctypes.c_double), c_int, c_void_p, c_void_p]),
+    "ash_hologram_create_band": (c_int, [ctypes.POINTER(c_void_p), c_int, c_int, c_int, c_int, c_void_p, c_int,
+                                         c_int_p, c_void_p, c_int, c_void_p, c_void_p]),
+    "ash_hologram_band": (c_int, [c_void_p, c_int_p, c_int_p, ctypes.POINTER(ctypes.c_double)]),
+    "ash_spot_update": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ash_spot_metrics": (c_int, [c_void_p, c_void_p, c_void_p, ctypes.c_double, c_void_p, c_void_p]),
     "ash_principal_modes": (c_int, [c_int, c_int, ctypes.POINTER(ctypes.c_float), c_int, c_int_p, c_int,
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float),
                                     ctypes.POINTER(ctypes.c_double)]),

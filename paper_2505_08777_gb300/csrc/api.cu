@@ -528,8 +528,8 @@ ash_status build_spec(int D_in, const int* noll, int D, const double* mix, Basis
   return ASH_OK;
 }
 
-ash_status create_impl(ash_hologram** out, int nx, int ny, const float* amp, int D, const BasisSpec* spec,
-                       const float* basis, int N, const float* coeff, void* stream) {
+ash_status create_impl(ash_hologram** out, int nx, int ny, int row0, int ny_full, const float* amp, int D,
+                       const BasisSpec* spec, const float* basis, int N, const float* coeff, void* stream) {
   const int* noll = spec ? spec->noll_eff.data() : nullptr;
   const int max_order = spec ? spec->max_order : 0;
   if (injected_failure()) return set_error(ASH_ERR_INJECTED, "injected failure (ash_debug_fail_after)");
@@ -548,6 +548,8 @@ ash_status create_impl(ash_hologram** out, int nx, int ny, const float* amp, int
   g.N = N;
   g.P = pixels_per_thread(D);
   g.NT = kTilePix / g.P;
+  g.row0 = row0;
+  g.ny_full = ny_full;
 
   auto fail = [&](ash_status st) {
     release(h);
@@ -580,7 +582,7 @@ ash_status create_impl(ash_hologram** out, int nx, int ny, const float* amp, int
   if (D <= kTcMaxModes) {
     // tensor-core path: one range of units per resident CTA, at least two
     // MMA chunks per CTA
-    h->tc_layout = tc_layout(D, noll, nx, ny);
+    h->tc_layout = tc_layout(D, noll, g);
     h->tc_na = h->tc_layout.NA;
     ce = tc_prepare(h->tc_na, &h->li.tc_adj_ctas_per_sm, &h->li.tc_fwd_ctas_per_sm);
     if (ce != cudaSuccess) return fail(cuda_fail(ce, "tensor-core kernel preparation"));
@@ -698,6 +700,7 @@ ash_status create_impl(ash_hologram** out, int nx, int ny, const float* amp, int
   if ((st = ws(h, &h->cg_part, kCgRedBlocks)) != ASH_OK) return fail(st);
   if ((st = ws(h, &h->cg_loss, kCgMaxIters + 1)) != ASH_OK) return fail(st);
   if ((st = ws(h, &h->sum_a2, 1)) != ASH_OK) return fail(st);
+  if ((st = ws(h, &h->sum_a2_arg, 1)) != ASH_OK) return fail(st);
   if ((st = ws(h, &h->err_word, 1)) != ASH_OK) return fail(st);
   if (spec) {
     if ((st = ws(h, &h->terms, spec->terms.size() + 1)) != ASH_OK) return fail(st);
@@ -782,11 +785,11 @@ ash_status ash_hologram_create(ash_hologram** out, int nx, int ny, const float* 
   if (bad_ptr(amp) || bad_ptr(coeff)) return set_error(ASH_ERR_INVALID_ARG, "amp and coeff must be device pointers");
   if ((noll == nullptr) == (basis == nullptr))
     return set_error(ASH_ERR_INVALID_ARG, "exactly one of noll / basis must be given");
-  if (!noll) return create_impl(out, nx, ny, amp, D, nullptr, basis, N, coeff, stream);
+  if (!noll) return create_impl(out, nx, ny, 0, ny, amp, D, nullptr, basis, N, coeff, stream);
   BasisSpec spec;
   ash_status st = build_spec(D, noll, D, nullptr, &spec);
   if (st != ASH_OK) return st;
-  return create_impl(out, nx, ny, amp, D, &spec, nullptr, N, coeff, stream);
+  return create_impl(out, nx, ny, 0, ny, amp, D, &spec, nullptr, N, coeff, stream);
 }
 
 ash_status ash_hologram_create_mixed(ash_hologram** out, int nx, int ny, const float* amp, int D_in, const int* noll,
@@ -803,7 +806,73 @@ ash_status ash_hologram_create_mixed(ash_hologram** out, int nx, int ny, const f
   BasisSpec spec;
   ash_status st = build_spec(D_in, noll, D, mix, &spec);
   if (st != ASH_OK) return st;
-  return create_impl(out, nx, ny, amp, D, &spec, nullptr, N, coeff, stream);
+  return create_impl(out, nx, ny, 0, ny, amp, D, &spec, nullptr, N, coeff, stream);
+}
+
+ash_status ash_hologram_create_band(ash_hologram** out, int nx, int ny_full, int row0, int row1, const float* amp,
+                                    int D, const int* noll, const float* basis, int N, const float* coeff,
+                                    void* stream) {
+  if (!out) return set_error(ASH_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (nx < 1 || ny_full < 1 || nx > 16384 || ny_full > 16384)
+    return set_error(ASH_ERR_INVALID_ARG, "grid %dx%d outside [1, 16384]", nx, ny_full);
+  if (row0 < 0 || row1 <= row0 || row1 > ny_full)
+    return set_error(ASH_ERR_INVALID_ARG, "band rows [%d, %d) outside [0, %d) or empty", row0, row1, ny_full);
+  if (row0 % kTileY != 0 || (row1 % kTileY != 0 && row1 != ny_full))
+    return set_error(ASH_ERR_INVALID_ARG, "band rows [%d, %d) must start and end on whole %d-row tile rows", row0,
+                     row1, kTileY);
+  if (D < 1 || D > ASH_MAX_MODES) return set_error(ASH_ERR_INVALID_ARG, "D=%d outside [1, %d]", D, ASH_MAX_MODES);
+  if (N < 1 || N > (1 << 20)) return set_error(ASH_ERR_INVALID_ARG, "N=%d outside [1, 2^20]", N);
+  if (bad_ptr(amp) || bad_ptr(coeff)) return set_error(ASH_ERR_INVALID_ARG, "amp and coeff must be device pointers");
+  if ((noll == nullptr) == (basis == nullptr))
+    return set_error(ASH_ERR_INVALID_ARG, "exactly one of noll / basis must be given");
+  const int ny = row1 - row0;
+  if (!noll) return create_impl(out, nx, ny, row0, ny_full, amp, D, nullptr, basis, N, coeff, stream);
+  BasisSpec spec;
+  ash_status st = build_spec(D, noll, D, nullptr, &spec);
+  if (st != ASH_OK) return st;
+  return create_impl(out, nx, ny, row0, ny_full, amp, D, &spec, nullptr, N, coeff, stream);
+}
+
+ash_status ash_hologram_band(const ash_hologram* h, int* row0, int* ny_full, double* sum_a2) {
+  if (!h) return set_error(ASH_ERR_INVALID_ARG, "handle is NULL");
+  if (row0) *row0 = h->g.row0;
+  if (ny_full) *ny_full = h->g.ny_full;
+  if (sum_a2) {
+    ASH_CUDA(cudaMemcpy(sum_a2, h->sum_a2, sizeof(double), cudaMemcpyDeviceToHost));
+  }
+  return ASH_OK;
+}
+
+ash_status ash_spot_update(ash_hologram* h, const float* E, float* w, const float* target, float* y, void* stream) {
+  if (!h || !E || !w || !target || !y) return set_error(ASH_ERR_INVALID_ARG, "NULL argument");
+  if ((reinterpret_cast<uintptr_t>(E) & 7) || (reinterpret_cast<uintptr_t>(y) & 7))
+    return set_error(ASH_ERR_INVALID_ARG, "complex buffers must be 8-byte aligned");
+  if (injected_failure()) return set_error(ASH_ERR_INJECTED, "injected failure");
+  k_wgs_update<<<1, 1024, 0, as_stream(stream)>>>(reinterpret_cast<const float2*>(E), w, target,
+                                                  reinterpret_cast<float2*>(y), h->g.N, h->wgs_feedback,
+                                                  h->wgs_fix ? h->wgs_u : nullptr, h->wgs_fix ? nullptr : h->wgs_u);
+  ASH_CUDA(cudaGetLastError());
+  return ASH_OK;
+}
+
+ash_status ash_spot_metrics(ash_hologram* h, const float* E, const float* target, double sum_a2, float* metrics_out,
+                            void* stream) {
+  if (!h || !E || !target || !metrics_out) return set_error(ASH_ERR_INVALID_ARG, "NULL argument");
+  if (reinterpret_cast<uintptr_t>(E) & 7) return set_error(ASH_ERR_INVALID_ARG, "E must be 8-byte aligned");
+  if (!(sum_a2 >= 0.0)) return set_error(ASH_ERR_INVALID_ARG, "sum_a2 must be >= 0 (0: the handle's own)");
+  if (injected_failure()) return set_error(ASH_ERR_INJECTED, "injected failure");
+  cudaStream_t s = as_stream(stream);
+  const double* sa = h->sum_a2;
+  if (sum_a2 > 0.0) {
+    // the caller's total sum A^2 (e.g. over every band of a sharded grid)
+    ASH_CUDA(cudaMemcpyAsync(h->sum_a2_arg, &sum_a2, sizeof(double), cudaMemcpyHostToDevice, s));
+    sa = h->sum_a2_arg;
+  }
+  k_metrics<<<1, 1024, 0, s>>>(reinterpret_cast<const float2*>(E), target, h->g.N, sa,
+                               (double)h->g.nx * h->g.ny_full, metrics_out);
+  ASH_CUDA(cudaGetLastError());
+  return ASH_OK;
 }
 
 void ash_hologram_destroy(ash_hologram* h) {

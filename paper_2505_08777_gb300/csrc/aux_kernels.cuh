@@ -38,12 +38,10 @@ static __global__ void k_basis(const BasisParams p) {
   const int lane = t & 31, w = t >> 5;
   int ia, ja;
   tile_anchor(G, tile, ia, ja);
-  const double R = 0.5 * (double)min(G.nx, G.ny);
-  const double cx = 0.5 * (double)(G.nx - 1), cy = 0.5 * (double)(G.ny - 1);
   double axp[kMaxOrder + 1], ayp[kMaxOrder + 1];
   double xp[kMaxOrder + 1], yp[kMaxOrder + 1];
   if (!p.user_basis) {
-    const double xa = ((double)ia - cx) / R, ya = ((double)ja - cy) / R;
+    const double xa = grid_x(G, (double)ia), ya = grid_y(G, (double)ja);
     axp[0] = ayp[0] = 1.0;
     for (int o = 1; o <= p.max_order; ++o) {
       axp[o] = axp[o - 1] * xa;
@@ -56,7 +54,7 @@ static __global__ void k_basis(const BasisParams p) {
     const int j = ty * kTileY + w + (NT / 32) * k;
     const bool valid = (i < G.nx) && (j < G.ny);
     if (!p.user_basis && valid) {
-      const double x = ((double)i - cx) / R, y = ((double)j - cy) / R;
+      const double x = grid_x(G, (double)i), y = grid_y(G, (double)j);
       xp[0] = yp[0] = 1.0;
       for (int o = 1; o <= p.max_order; ++o) {
         xp[o] = xp[o - 1] * x;

@@ -29,14 +29,28 @@ constexpr int kTilePix = kTileX * kTileY;
 constexpr int kMaxModes = 16;
 
 struct Geometry {
-  int nx, ny;          // grid
+  int nx, ny;          // grid (for a band: the band's rows)
   int tiles_x, tiles_y;
   int T;               // number of tiles
   int D;               // modes
   int N;               // spots
   int P;               // pixels per thread
   int NT;              // threads per tile CTA (1024 / P)
+  int row0;            // first row of this grid within the full SLM grid (0 unless a band)
+  int ny_full;         // rows of the full SLM grid (ny unless a band)
 };
+
+// Unit-disk coordinates of the full SLM grid (nx x ny_full): pixel (i, j) of
+// this grid sits at x = (i - (nx - 1)/2) / R, y = (row0 + j - (ny_full - 1)/2) / R,
+// R = min(nx, ny_full) / 2. A band (a block of whole 32-row tile rows of the
+// full grid) therefore has the full grid's basis values and tile anchors.
+__host__ __device__ inline double grid_radius(const Geometry& g) {
+  return 0.5 * (double)(g.nx < g.ny_full ? g.nx : g.ny_full);
+}
+__host__ __device__ inline double grid_x(const Geometry& g, double i) { return (i - 0.5 * (double)(g.nx - 1)) / grid_radius(g); }
+__host__ __device__ inline double grid_y(const Geometry& g, double j) {
+  return ((double)g.row0 + j - 0.5 * (double)(g.ny_full - 1)) / grid_radius(g);
+}
 
 // Pixels per thread for a given mode count (register budget of the
 // pixel-stationary kernels: P * D basis values live in registers).

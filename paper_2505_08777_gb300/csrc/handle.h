@@ -80,6 +80,7 @@ struct ash_hologram {
   double* cg_part = nullptr;
   float* cg_loss = nullptr;     // [kCgMaxIters + 1]
   double* sum_a2 = nullptr;
+  double* sum_a2_arg = nullptr;   // a caller's total sum A^2 (ash_spot_metrics)
   ash::MonoTerm* terms = nullptr;
   int* term_off = nullptr;
   unsigned* err_word = nullptr;

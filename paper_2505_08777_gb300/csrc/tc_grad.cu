@@ -31,11 +31,9 @@ __global__ void k_tc_tile_poly(const Geometry G, const MonoTerm* __restrict__ te
     l -= ord - k + 1;
     ++k;
   }
-  const double R = 0.5 * (double)min(G.nx, G.ny);
-  const double cx = 0.5 * (double)(G.nx - 1), cy = 0.5 * (double)(G.ny - 1);
-  const double xc = ((double)((tile % G.tiles_x) * kTileX) + 15.5 - cx) / R;
-  const double yc = ((double)((tile / G.tiles_x) * kTileY) + 15.5 - cy) / R;
-  const double sc = 16.0 / R;
+  const double xc = grid_x(G, (double)((tile % G.tiles_x) * kTileX) + 15.5);
+  const double yc = grid_y(G, (double)((tile / G.tiles_x) * kTileY) + 15.5);
+  const double sc = 16.0 / grid_radius(G);
   double acc = 0.0;
   if (d < G.D) {
     for (int t = term_off[d]; t < term_off[d + 1]; ++t) {

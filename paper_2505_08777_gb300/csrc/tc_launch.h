@@ -32,11 +32,11 @@ struct TcLayout {
   int D;
   int NA;        // K-atoms of 32 tf32 per row
   int tx, ty;    // positions of the x / y tilt among the D modes (tilt-exact), else -1
-  float R;       // min(nx, ny) / 2
+  float R;       // min(nx, ny_full) / 2 (grid_radius)
 };
 __host__ __device__ constexpr int tc_na(int D) { return 3 * D <= 32 ? 1 : 2; }
-inline TcLayout tc_layout(int D, const int* noll, int nx, int ny) {
-  TcLayout L{D, tc_na(D), -1, -1, 0.5f * (float)(nx < ny ? nx : ny)};
+inline TcLayout tc_layout(int D, const int* noll, const Geometry& g) {
+  TcLayout L{D, tc_na(D), -1, -1, (float)grid_radius(g)};
   if (noll && L.NA > 1 && 3 * (D - 2) + 4 <= 32) {
     for (int d = 0; d < D; ++d) {
       if (noll[d] == 2) L.tx = d;

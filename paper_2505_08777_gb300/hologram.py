@@ -46,11 +46,14 @@ class Hologram:
     N x D coefficient matrix (paper Sec. II / Methods). Owns a libash handle."""
 
     def __init__(self, amp: torch.Tensor, coeff: torch.Tensor, noll=None, basis: torch.Tensor | None = None,
-                 mix=None, stream=None):
+                 mix=None, stream=None, row0: int | None = None, ny_full: int | None = None):
         """`noll`: Noll indices of the modes (one per column of coeff), or of
         the input Zernikes when `mix` is given; `mix` (D x len(noll), float64):
         output mode k = sum_d mix[k, d] Z_noll[d] (e.g. from principal_modes);
-        `basis`: a caller basis (D, ny, nx) instead of Noll modes."""
+        `basis`: a caller basis (D, ny, nx) instead of Noll modes.
+        `row0`, `ny_full`: a band of a larger grid -- this hologram holds rows
+        [row0, row0 + ny) of an nx x ny_full grid (amp, basis and every phase
+        or field are the band's rows), in the full grid's coordinates."""
         self._lib = _lib.load()
         self._h = ctypes.c_void_p(0)
         self.coeff_epoch = 0   # counts set_coefficients calls
@@ -72,6 +75,7 @@ class Hologram:
             _need(basis, torch.float32, (self.D, self.ny, self.nx), "basis")
         self.noll = noll
         self.device = amp.device
+        self.row0, self.ny_full = 0, self.ny
         if mix is not None:
             if noll is None or basis is not None:
                 raise ValueError("mix needs noll (and no basis)")
@@ -83,6 +87,15 @@ class Hologram:
                 ctypes.byref(self._h), self.nx, self.ny, _ptr(amp), len(noll), noll_arr, self.D,
                 mix.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self.N, _ptr(coeff), _stream_ptr(stream))
             _lib.check(st, "ash_hologram_create_mixed")
+            return
+        if row0 is not None or ny_full is not None:
+            if row0 is None or ny_full is None:
+                raise ValueError("a band needs both row0 and ny_full")
+            self.row0, self.ny_full = int(row0), int(ny_full)
+            st = self._lib.ash_hologram_create_band(ctypes.byref(self._h), self.nx, self.ny_full, self.row0,
+                                                    self.row0 + self.ny, _ptr(amp), self.D, noll_arr, _ptr(basis),
+                                                    self.N, _ptr(coeff), _stream_ptr(stream))
+            _lib.check(st, "ash_hologram_create_band")
             return
         st = self._lib.ash_hologram_create(ctypes.byref(self._h), self.nx, self.ny, _ptr(amp), self.D,
                                            noll_arr, _ptr(basis), self.N, _ptr(coeff), _stream_ptr(stream))
@@ -149,12 +162,16 @@ class Hologram:
         _lib.check(self._lib.ash_forward_field(self._h, _ptr(field), _ptr(E), _stream_ptr(stream)), "ash_forward_field")
         return E
 
-    def adjoint(self, y: torch.Tensor, want_field: bool = True, want_phase: bool = False, stream=None):
+    def adjoint(self, y: torch.Tensor, want_field: bool = True, want_phase: bool = False, stream=None,
+                phase_out: torch.Tensor | None = None):
         """g_m = sum_n y_n exp(+i C_n . Z_m); returns (g complex64 (ny, nx) or None,
-        phase float32 (ny, nx) or None)."""
+        phase float32 (ny, nx) or None); `phase_out`: write arg g there."""
         _need(y, torch.complex64, (self.N,), "y")
         g = torch.empty((self.ny, self.nx), dtype=torch.complex64, device=y.device) if want_field else None
-        ph = torch.empty((self.ny, self.nx), dtype=torch.float32, device=y.device) if want_phase else None
+        if phase_out is not None:
+            ph = _need(phase_out, torch.float32, (self.ny, self.nx), "phase_out")
+        else:
+            ph = torch.empty((self.ny, self.nx), dtype=torch.float32, device=y.device) if want_phase else None
         _lib.check(self._lib.ash_adjoint(self._h, _ptr(y), _ptr(g), _ptr(ph), _stream_ptr(stream)), "ash_adjoint")
         return g, ph
 
@@ -170,6 +187,38 @@ class Hologram:
         _lib.check(self._lib.ash_wgs_iterate(self._h, _ptr(phase), _ptr(weights), _ptr(target), int(iters), _ptr(E),
                                              _ptr(met), _stream_ptr(stream)), "ash_wgs_iterate")
         return E, met
+
+    def spot_update(self, E: torch.Tensor, weights: torch.Tensor, target: torch.Tensor,
+                    out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """The weighted-GS spot update alone: weights updated in place from E,
+        returns y = w exp(i arg E) (complex64 (N,)), the adjoint's input."""
+        _need(E, torch.complex64, (self.N,), "E")
+        _need(weights, torch.float32, (self.N,), "weights")
+        _need(target, torch.float32, (self.N,), "target")
+        y = out if out is not None else torch.empty(self.N, dtype=torch.complex64, device=E.device)
+        _need(y, torch.complex64, (self.N,), "out")
+        _lib.check(self._lib.ash_spot_update(self._h, _ptr(E), _ptr(weights), _ptr(target), _ptr(y),
+                                             _stream_ptr(stream)), "ash_spot_update")
+        return y
+
+    def spot_metrics(self, E: torch.Tensor, target: torch.Tensor, sum_a2: float = 0.0,
+                     out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """[uniformity, efficiency, sum |E|^2, min |E|^2/T^2] of E; `sum_a2`:
+        the whole grid's sum of A^2 (0: this handle's own)."""
+        _need(E, torch.complex64, (self.N,), "E")
+        _need(target, torch.float32, (self.N,), "target")
+        met = out if out is not None else torch.empty(4, dtype=torch.float32, device=E.device)
+        _need(met, torch.float32, (4,), "out")
+        _lib.check(self._lib.ash_spot_metrics(self._h, _ptr(E), _ptr(target), float(sum_a2), _ptr(met),
+                                              _stream_ptr(stream)), "ash_spot_metrics")
+        return met
+
+    def band_info(self) -> tuple[int, int, float]:
+        """(first row, rows of the full grid, sum of A^2 over this handle's pixels)."""
+        r0, nyf, sa = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
+        _lib.check(self._lib.ash_hologram_band(self._h, ctypes.byref(r0), ctypes.byref(nyf), ctypes.byref(sa)),
+                   "ash_hologram_band")
+        return int(r0.value), int(nyf.value), float(sa.value)
 
     def grad(self, phase: torch.Tensor, grad_E: torch.Tensor, want_phase: bool = True, want_coeff: bool = True,
              stream=None):

@@ -142,3 +142,20 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
 
 def test_probe_rejects_null_output(lib):
     assert lib.ash_probe_rates(None, None) == 1
+
+
+def test_band_arguments_rejected_without_gpu(lib):
+    h = ctypes.c_void_p(0)
+    arr = (ctypes.c_int * 2)(2, 3)
+
+    def band(nx, nyf, r0, r1):
+        return lib.ash_hologram_create_band(ctypes.byref(h), nx, nyf, r0, r1, ctypes.c_void_p(1), 2, arr, None, 4,
+                                            ctypes.c_void_p(1), None)
+    assert band(64, 100, 16, 64) == 1       # not on a 32-row tile boundary
+    assert band(64, 100, 0, 40) == 1        # ends inside a tile row that is not the last
+    assert band(64, 100, 64, 64) == 1       # empty
+    assert band(64, 100, 64, 101) == 1      # past the grid
+    assert band(0, 100, 0, 32) == 1
+    assert b"tile" in lib.ash_last_error() or b"grid" in lib.ash_last_error()
+    assert lib.ash_spot_update(None, None, None, None, None, None) == 1
+    assert lib.ash_spot_metrics(None, None, None, 0.0, None, None) == 1
