@@ -299,6 +299,26 @@ ash_status ash_forward(ash_hologram *h, const float *phase, float *E, void *stre
 ash_status ash_forward_field(ash_hologram *h, const float *field, float *E, void *stream);
 
 /*
+ * Set the coefficients and run the forward in one call (ash_set_coefficients
+ * then ash_forward, enqueued on `stream`): the forward pass of a gradient
+ * step on C (Methods, gradients through the transform) with one call.
+ *   coeff   device float[N*D]; phase device float[M]; E device float[2N].
+ */
+ash_status ash_forward_coeff(ash_hologram *h, const float *coeff, const float *phase, float *E, void *stream);
+
+/*
+ * Spot-intensity loss and its gradient (the objective of the gradient-descent
+ * refinement; the paper gives none, so this is the reading used throughout):
+ *   I_n = |E_n|^2, mu = mean I, r_n = I_n / mu - t_n, L = sum_n r_n^2,
+ *   grad_E_n = dL/dRe E_n + i dL/dIm E_n = 2 G_n E_n,
+ *   G_k = (2 / mu) (r_k - (1/N) sum_n r_n I_n / mu).
+ *   E       device float[2N] complex64; t device float[N]; 1 <= N <= 2^20.
+ *   loss    device float[1] or NULL; grad_E device float[2N] or NULL (not both NULL).
+ * One CTA, sums in fp64 in a fixed order (deterministic).
+ */
+ash_status ash_spot_loss(const float *E, const float *t, int N, float *loss, float *grad_E, void *stream);
+
+/*
  * Conjugate-gradient refinement of the SLM phase (paper Methods: precision
  * targets such as uniform top hats are refined by conjugate-gradient
  * descent through the transform's gradients). Loss: the spot-intensity

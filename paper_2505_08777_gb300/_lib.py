@@ -50,6 +50,8 @@ SIGNATURES = {
     "ash_set_amplitude": (c_int, [c_void_p, c_void_p, c_void_p]),
     "ash_forward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "ash_forward_field": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ash_forward_coeff": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ash_spot_loss": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "ash_adjoint": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "ash_wgs_iterate": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "ash_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),

@@ -13,9 +13,9 @@ from __future__ import annotations
 
 import torch
 
-from .hologram import Hologram
+from .hologram import Hologram, spot_loss
 
-__all__ = ["SpotField", "spot_field", "spot_intensity_loss"]
+__all__ = ["SpotField", "SpotIntensityLoss", "spot_field", "spot_intensity_loss"]
 
 
 class SpotField(torch.autograd.Function):
@@ -23,8 +23,7 @@ class SpotField(torch.autograd.Function):
     def forward(ctx, phase: torch.Tensor, coeff: torch.Tensor, holo: Hologram) -> torch.Tensor:
         phase = phase.detach().contiguous()
         coeff = coeff.detach().contiguous()
-        holo.set_coefficients(coeff)
-        E = holo.forward(phase)
+        E = holo.forward_coeff(coeff, phase)   # sets C and runs the forward in one call
         ctx.save_for_backward(phase, coeff)
         ctx.holo = holo
         ctx.epoch = holo.coeff_epoch
@@ -54,8 +53,25 @@ def spot_field(holo: Hologram, phase: torch.Tensor, coeff: torch.Tensor | None =
     return SpotField.apply(phase, coeff, holo)
 
 
+class SpotIntensityLoss(torch.autograd.Function):
+    """L = sum_n (|E_n|^2 / mean|E|^2 - t_n)^2 with its gradient dL/dE from
+    the same library kernel (ash_spot_loss); backward scales it."""
+
+    @staticmethod
+    def forward(ctx, E: torch.Tensor, t: torch.Tensor) -> torch.Tensor:
+        loss, g = spot_loss(E.detach().contiguous(), t.detach().contiguous(), want_grad=ctx.needs_input_grad[0])
+        ctx.save_for_backward(g if g is not None else loss)
+        return loss
+
+    @staticmethod
+    def backward(ctx, grad_L: torch.Tensor):
+        if not ctx.needs_input_grad[0]:
+            return None, None
+        (g,) = ctx.saved_tensors
+        return g * grad_L, None
+
+
 def spot_intensity_loss(E: torch.Tensor, t: torch.Tensor) -> torch.Tensor:
-    """L = sum_n (|E_n|^2 / mean|E|^2 - t_n)^2 (plain torch on N-vectors)."""
-    I = E.real * E.real + E.imag * E.imag
-    r = I / I.mean() - t
-    return (r * r).sum()
+    """L = sum_n (|E_n|^2 / mean|E|^2 - t_n)^2, differentiable in E (the loss
+    and its gradient in one library kernel)."""
+    return SpotIntensityLoss.apply(E, t)

@@ -95,6 +95,25 @@ ash_status ws(ash_hologram* h, T** out, size_t count) {
   return ws_alloc(h, reinterpret_cast<void**>(out), count * sizeof(T));
 }
 
+void free_one(ash_hologram* h, void* p, size_t bytes) {
+  for (size_t i = 0; i < h->allocs.size(); ++i)
+    if (h->allocs[i] == p) {
+      h->allocs.erase(h->allocs.begin() + (long)i);
+      break;
+    }
+  if (g_free) g_free(g_alloc_ctx, p, h->home);
+  else cudaFreeAsync(p, h->home);
+  h->bytes -= (bytes + 255) & ~(size_t)255;
+}
+
+size_t fma_image_bytes(const ash_hologram* h) { return (size_t)h->g.T * kTilePix * h->g.D * sizeof(float); }
+
+void drop_fma_image(ash_hologram* h) {
+  if (!h->dz) return;
+  free_one(h, h->dz, fma_image_bytes(h));
+  h->dz = nullptr;
+}
+
 void release(ash_hologram* h) {
   ash::clear_graphs(h);
   for (void* p : h->allocs) {
@@ -158,6 +177,10 @@ bool use_tc_grad(const ash_hologram* h) {
   if (!h->tgrad_ok || h->variant == 1) return false;
   return h->variant == 2 || h->g.N >= kTcFwdMinSpots;
 }
+
+// Whether the handle's current kernel choice runs any FMA-pipe kernel (they
+// read the register-image basis dz; the tensor-core kernels do not).
+bool needs_fma_image(const ash_hologram* h) { return !(use_tc_fwd(h) && use_tc_adj(h) && use_tc_grad(h)); }
 
 TcGradParams tc_grad_params(const ash_hologram* h, const float2* gE, float* dC) {
   TcGradParams p{};
@@ -258,6 +281,7 @@ ash_status enqueue_forward(ash_hologram* h, int source, const float* phase, cons
     }
     return ASH_OK;
   }
+  if (!h->dz) return set_error(ASH_ERR_DEVICE, "FMA-pipe forward without its basis image");
   FwdParams p{};
   p.v = view_of(h);
   p.phase = phase;
@@ -294,6 +318,7 @@ ash_status enqueue_adjoint(ash_hologram* h, const float2* y, float2* g_out, floa
     }
     return ASH_OK;
   }
+  if (!h->dz) return set_error(ASH_ERR_DEVICE, "FMA-pipe adjoint without its basis image");
   p.sched = h->sched;
   p.split = h->split;
   cudaError_t e = launch_adjoint(h->g.D, p, h->sched.G, s);
@@ -338,6 +363,25 @@ bool bad_ptr(const void* p) { return p == nullptr; }
 }  // namespace
 
 namespace ash {
+
+ash_status ensure_fma_image(ash_hologram* h) {
+  if (h->dz) return ASH_OK;
+  // work in flight may use the handle; the image is rebuilt with the device idle
+  ASH_CUDA(cudaDeviceSynchronize());
+  ash_status st = ws(h, &h->dz, (size_t)h->g.T * kTilePix * h->g.D);
+  if (st != ASH_OK) return st;
+  BasisParams bp{};
+  bp.g = h->g;
+  bp.terms = h->terms;
+  bp.term_off = h->term_off;
+  bp.max_order = h->basis_max_order;
+  bp.dz = h->dz;
+  bp.anchors = nullptr;   // the anchors are kept; only the image is rebuilt
+  k_basis<<<h->g.T, h->g.NT, 0, h->home>>>(bp);
+  ASH_CUDA(cudaGetLastError());
+  ASH_CUDA(cudaStreamSynchronize(h->home));
+  return ASH_OK;
+}
 
 int graph_kernel_nodes(cudaGraph_t g) {
   size_t n = 0;
@@ -736,6 +780,8 @@ ash_status create_impl(ash_hologram** out, int nx, int ny, int row0, int ny_full
   bp.anchors = h->anchors;
   k_basis<<<g.T, g.NT, 0, s>>>(bp);
   CREATE_CUDA(cudaGetLastError());
+  h->basis_max_order = max_order;
+  h->user_basis = basis != nullptr;
   if (h->tc_ok) {
     CREATE_CUDA(cudaMemcpyAsync(h->tfwd_begin, tfwd_begin.data(), tfwd_begin.size() * sizeof(long long),
                                 cudaMemcpyHostToDevice, s));
@@ -766,6 +812,11 @@ ash_status create_impl(ash_hologram** out, int nx, int ny, int row0, int ny_full
   // is used from another stream (the graph capture stream, or the caller's)
   CREATE_CUDA(cudaStreamSynchronize(s));
 #undef CREATE_CUDA
+  // the register-image basis serves only the FMA-pipe kernels: when every
+  // transform of this handle runs on the tensor cores, it is released (and
+  // rebuilt from the monomial tables if a later kernel choice needs it; a
+  // caller's basis is not kept, so its image stays)
+  if (!h->user_basis && !needs_fma_image(h)) drop_fma_image(h);
   *out = h;
   return ASH_OK;
 }
@@ -926,6 +977,26 @@ ash_status ash_forward(ash_hologram* h, const float* phase, float* E, void* stre
   return enqueue_forward(h, kSrcPhase, phase, nullptr, reinterpret_cast<float2*>(E), as_stream(stream));
 }
 
+ash_status ash_forward_coeff(ash_hologram* h, const float* coeff, const float* phase, float* E, void* stream) {
+  if (!h || !coeff || !phase || !E) return set_error(ASH_ERR_INVALID_ARG, "NULL argument");
+  if (injected_failure()) return set_error(ASH_ERR_INJECTED, "injected failure");
+  cudaStream_t s = as_stream(stream);
+  ASH_CUDA(cudaMemcpyAsync(h->coeff, coeff, (size_t)h->g.N * h->g.D * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  ASH_CUDA(enqueue_tc_coeff(h, s));
+  return enqueue_forward(h, kSrcPhase, phase, nullptr, reinterpret_cast<float2*>(E), s);
+}
+
+ash_status ash_spot_loss(const float* E, const float* t, int N, float* loss, float* grad_E, void* stream) {
+  if (!E || !t || (!loss && !grad_E)) return set_error(ASH_ERR_INVALID_ARG, "NULL argument");
+  if (N < 1 || N > (1 << 20)) return set_error(ASH_ERR_INVALID_ARG, "N=%d outside [1, 2^20]", N);
+  if ((reinterpret_cast<uintptr_t>(E) & 7) || (reinterpret_cast<uintptr_t>(grad_E) & 7))
+    return set_error(ASH_ERR_INVALID_ARG, "complex buffers must be 8-byte aligned");
+  k_spot_loss<<<1, 1024, 0, as_stream(stream)>>>(reinterpret_cast<const float2*>(E), t, N, loss,
+                                                 reinterpret_cast<float2*>(grad_E));
+  ASH_CUDA(cudaGetLastError());
+  return ASH_OK;
+}
+
 ash_status ash_forward_field(ash_hologram* h, const float* field, float* E, void* stream) {
   if (!h || !field || !E) return set_error(ASH_ERR_INVALID_ARG, "NULL argument");
   if ((reinterpret_cast<uintptr_t>(field) & 7) || (reinterpret_cast<uintptr_t>(E) & 7))
@@ -991,6 +1062,7 @@ ash_status ash_grad(ash_hologram* h, const float* phase, const float* grad_E, fl
   if (dcoeff && use_tc_grad(h)) {
     ASH_CUDA(enqueue_tc_gradc(h, phase, gE, dcoeff, s));
   } else if (dcoeff) {
+    if (!h->dz) return set_error(ASH_ERR_DEVICE, "FMA-pipe moments without their basis image");
     GradCParams p{};
     p.v = view_of(h);
     p.phase = phase;
@@ -1024,6 +1096,7 @@ ash_status ash_set_kernel_variant(ash_hologram* h, int variant) {
     return set_error(ASH_ERR_UNSUPPORTED, "tensor-core kernels need D <= %d (D = %d)", kTcMaxModes, h->g.D);
   h->variant = variant;
   clear_graphs(h);
+  if (needs_fma_image(h)) return ensure_fma_image(h);
   return ASH_OK;
 }
 
@@ -1059,6 +1132,7 @@ ash_status ash_profile(ash_hologram* h, const float* phase, const float* y, floa
   if (reinterpret_cast<uintptr_t>(y) & 7) return set_error(ASH_ERR_INVALID_ARG, "y must be 8-byte aligned");
   if (injected_failure()) return set_error(ASH_ERR_INJECTED, "injected failure");
   cudaStream_t s = as_stream(stream);
+  if (needs_fma_image(h) && !h->dz) return set_error(ASH_ERR_DEVICE, "FMA-pipe kernels without their basis image");
   cudaEvent_t ev[12];
   for (int q = 0; q < 12; ++q) ASH_CUDA(cudaEventCreate(&ev[q]));
   const float2* y2 = reinterpret_cast<const float2*>(y);

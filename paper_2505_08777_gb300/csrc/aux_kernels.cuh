@@ -17,7 +17,7 @@ struct BasisParams {
   int max_order;           // max px or py over all terms
   const float* user_basis; // [D][ny][nx] or null (then terms are used)
   float* dz;               // register image [T][NT][D][P]
-  float2* anchors;         // [T][D]
+  float2* anchors;         // [T][D], or NULL to rebuild dz only
 };
 
 __device__ inline double eval_mono(const MonoTerm* __restrict__ terms, int b, int e, const double* xp,
@@ -75,7 +75,7 @@ static __global__ void k_basis(const BasisParams p) {
       p.dz[(((size_t)tile * NT + t) * D + d) * P + k] = (float)v;
     }
   }
-  if (t < D) {
+  if (t < D && p.anchors) {
     const int d = t;
     double za;
     if (p.user_basis) {
@@ -276,6 +276,41 @@ __device__ __forceinline__ void metrics_body(const float2* __restrict__ E, const
   }
 }
 
+// Spot-intensity loss (one block, fp64 sums in a fixed order):
+//   I = |E|^2, mu = mean I, r = I / mu - t, L = sum r^2,
+//   dL/dRe E + i dL/dIm E = 2 G E, G_k = (2 / mu) (r_k - (1/N) sum_n r_n I_n / mu).
+__device__ __forceinline__ void spot_loss_body(const float2* __restrict__ E, const float* __restrict__ t, int N,
+                                               float* __restrict__ loss, float2* __restrict__ gE) {
+  __shared__ double red[32];
+  double sI = 0.0;
+  for (int n = threadIdx.x; n < N; n += 1024) {
+    const float2 e = E[n];
+    sI += (double)e.x * e.x + (double)e.y * e.y;
+  }
+  sI = block_sum<1024>(sI, red);
+  const double mu = sI / N;
+  double sL = 0.0, sR = 0.0;
+  for (int n = threadIdx.x; n < N; n += 1024) {
+    const float2 e = E[n];
+    const double I = (double)e.x * e.x + (double)e.y * e.y;
+    const double r = (mu > 0.0 ? I / mu : 0.0) - (double)t[n];
+    sL += r * r;
+    sR += mu > 0.0 ? r * I / mu : 0.0;
+  }
+  sL = block_sum<1024>(sL, red);
+  sR = block_sum<1024>(sR, red);
+  if (threadIdx.x == 0 && loss) *loss = (float)sL;
+  if (!gE) return;
+  const double c = sR / N;
+  for (int n = threadIdx.x; n < N; n += 1024) {
+    const float2 e = E[n];
+    const double I = (double)e.x * e.x + (double)e.y * e.y;
+    const double r = (mu > 0.0 ? I / mu : 0.0) - (double)t[n];
+    const double G = mu > 0.0 ? (2.0 / mu) * (r - c) : 0.0;
+    gE[n] = make_float2((float)(2.0 * G * e.x), (float)(2.0 * G * e.y));
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Single-hologram wrappers.
 
@@ -293,6 +328,11 @@ static __global__ void __launch_bounds__(1024) k_wgs_update(const float2* __rest
                                                             int N, float feedback, const float2* __restrict__ u_fixed,
                                                             float2* __restrict__ u_store) {
   wgs_update_body(E, w, T, y, N, feedback, u_fixed, u_store);
+}
+
+static __global__ void __launch_bounds__(1024) k_spot_loss(const float2* __restrict__ E, const float* __restrict__ t,
+                                                           int N, float* __restrict__ loss, float2* __restrict__ gE) {
+  spot_loss_body(E, t, N, loss, gE);
 }
 
 static __global__ void __launch_bounds__(1024) k_metrics(const float2* __restrict__ E, const float* __restrict__ T,

@@ -604,6 +604,9 @@ ash_status ash_batch_create_ex(ash_batch** out, int count, const ash_hologram_de
       continue;
     }
     b->holos.push_back(h);
+    // the persistent FMA-pipe kernels read the register-image basis
+    st = ensure_fma_image(h);
+    if (st != ASH_OK) return bail(st);
     BatchHolo bh{};
     bh.v = view_of(h);
     bh.unit0 = b->U;

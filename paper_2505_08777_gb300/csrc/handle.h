@@ -23,7 +23,9 @@ struct ash_hologram {
   int fwd_rows = 0;
   int gradc_gx = 0, gradc_gy = 0;
   // workspace
-  float* dz = nullptr;
+  float* dz = nullptr;           // register-image basis of the FMA-pipe kernels (NULL while unused)
+  int basis_max_order = 0;      // of the monomial tables (rebuilding dz)
+  bool user_basis = false;      // created from a caller's basis (dz is never dropped)
   float* amp_img = nullptr;
   float2* anchors = nullptr;
   float* coeff = nullptr;
@@ -108,6 +110,9 @@ void clear_graphs(ash_hologram* h);
 // Kernel nodes of a graph, those of embedded child graphs included (-1 if
 // the graph cannot be inspected).
 int graph_kernel_nodes(cudaGraph_t g);
+// The FMA-pipe kernels' register-image basis: rebuilt from the monomial
+// tables if it was released (synchronises the device).
+ash_status ensure_fma_image(ash_hologram* h);
 // Record a message for ash_last_error() (any translation unit).
 void record_error(const char* msg);
 // Map a CUDA error to ASH_ERR_CUDA with a message.

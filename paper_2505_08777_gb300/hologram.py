@@ -15,7 +15,7 @@ import torch
 
 from . import _lib
 
-__all__ = ["Hologram", "Batch", "zsub_estimate", "zernike_subtraction"]
+__all__ = ["Hologram", "Batch", "spot_loss", "zsub_estimate", "zernike_subtraction"]
 
 
 def _stream_ptr(stream=None) -> ctypes.c_void_p:
@@ -39,6 +39,20 @@ def _need(t: torch.Tensor, dtype, shape, name: str) -> torch.Tensor:
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
     return t
+
+
+def spot_loss(E: torch.Tensor, t: torch.Tensor, want_grad: bool = True, stream=None):
+    """Spot-intensity loss L = sum_n (|E_n|^2 / mean |E|^2 - t_n)^2 (0-dim float32
+    tensor) and, if asked, dL/dRe E + i dL/dIm E (complex64 (N,)), in one
+    library kernel."""
+    lib = _lib.load()
+    N = int(E.shape[0]) if E.dim() == 1 else -1
+    _need(E, torch.complex64, (N,), "E")
+    _need(t, torch.float32, (N,), "t")
+    loss = torch.empty((), dtype=torch.float32, device=E.device)
+    g = torch.empty_like(E) if want_grad else None
+    _lib.check(lib.ash_spot_loss(_ptr(E), _ptr(t), N, _ptr(loss), _ptr(g), _stream_ptr(stream)), "ash_spot_loss")
+    return loss, g
 
 
 class Hologram:
@@ -152,6 +166,19 @@ class Hologram:
         E = out if out is not None else torch.empty(self.N, dtype=torch.complex64, device=phase.device)
         _need(E, torch.complex64, (self.N,), "out")
         _lib.check(self._lib.ash_forward(self._h, _ptr(phase), _ptr(E), _stream_ptr(stream)), "ash_forward")
+        return E
+
+    def forward_coeff(self, coeff: torch.Tensor, phase: torch.Tensor, out: torch.Tensor | None = None,
+                      stream=None) -> torch.Tensor:
+        """Set the coefficients to `coeff` and run the forward, in one library
+        call (counts as a set_coefficients call for coeff_epoch)."""
+        _need(coeff, torch.float32, (self.N, self.D), "coeff")
+        _need(phase, torch.float32, (self.ny, self.nx), "phase")
+        E = out if out is not None else torch.empty(self.N, dtype=torch.complex64, device=phase.device)
+        _need(E, torch.complex64, (self.N,), "out")
+        _lib.check(self._lib.ash_forward_coeff(self._h, _ptr(coeff), _ptr(phase), _ptr(E), _stream_ptr(stream)),
+                   "ash_forward_coeff")
+        self.coeff_epoch += 1
         return E
 
     def forward_field(self, field: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:

@@ -159,3 +159,9 @@ def test_band_arguments_rejected_without_gpu(lib):
     assert b"tile" in lib.ash_last_error() or b"grid" in lib.ash_last_error()
     assert lib.ash_spot_update(None, None, None, None, None, None) == 1
     assert lib.ash_spot_metrics(None, None, None, 0.0, None, None) == 1
+
+
+def test_loss_and_fused_forward_reject_bad_arguments(lib):
+    assert lib.ash_spot_loss(None, None, 4, None, None, None) == 1
+    assert lib.ash_spot_loss(ctypes.c_void_p(8), ctypes.c_void_p(8), 0, ctypes.c_void_p(8), None, None) == 1
+    assert lib.ash_forward_coeff(None, None, None, None, None) == 1

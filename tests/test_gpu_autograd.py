@@ -137,3 +137,23 @@ def test_step_is_graph_capturable_and_bitwise_eager():
     torch.cuda.synchronize()
     assert torch.equal(L_static, L_eager)
     assert torch.equal(ph.grad, g_ph) and torch.equal(C.grad, g_C)
+
+
+def test_spot_loss_kernel_matches_float64_autograd():
+    # the library's loss and dL/dE against float64 torch autograd of the
+    # written-out loss, on random fields (sizes past one CTA's 1024 threads)
+    from paper_2505_08777_gb300.hologram import spot_loss
+    rng = np.random.default_rng(12)
+    for N in (7, 1024, 5000):
+        E = (rng.normal(size=N) + 1j * rng.normal(size=N)).astype(np.complex64)
+        t = rng.uniform(0.5, 1.5, size=N).astype(np.float32)
+        L, g = spot_loss(torch.from_numpy(E).cuda(), torch.from_numpy(t).cuda())
+        E64 = torch.from_numpy(E.astype(np.complex128)).requires_grad_(True)
+        I = E64.abs() ** 2
+        r = I / I.mean() - torch.from_numpy(t.astype(np.float64))
+        L64 = (r * r).sum()
+        L64.backward()
+        assert abs(L.item() - L64.item()) <= 1e-5 * abs(L64.item())
+        assert _rel(g.cpu().numpy().astype(np.complex128), E64.grad.numpy()) <= 1e-5
+        # and the oracle's closed form of the same gradient
+        assert _rel(g.cpu().numpy().astype(np.complex128), ograd.grad_E(E.astype(np.complex128), t)) <= 1e-5
