@@ -15,6 +15,7 @@ no collective on the data path); rank 0 prints one JSON line.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import math
 import os
@@ -183,9 +184,10 @@ def _args():
     ap.add_argument("--batch-solo-terms", type=int, default=None,
                     help="c5: N*M threshold above which a batch member runs standalone in the batch's graph "
                          "(default: the library's)")
-    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5", "zsub", "cg", "peaks"],
+    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5", "c5s", "zsub", "cg", "peaks"],
                     help="c2 (default, the headline): anisoplanatic 2D WGS; c3: 3D volume WGS; "
                          "c4: autograd + Adam on 8 holograms; c5: 64 uneven holograms, batched vs looped; "
+                         "c5s: 64 small uneven holograms (256^2-512^2, N 10-300), batched vs looped; "
                          "zsub: simulated Zernike-subtraction calibration round on the c2 system; "
                          "cg: conjugate-gradient top-hat refinement after WGS on c2; "
                          "peaks: the per-SM pipe rates the roofline is built from (ash_probe_rates)")
@@ -366,7 +368,7 @@ def main():
         return run_reference(args)
     if args.config == "c4":
         return bench_autograd(args)
-    if args.config == "c5":
+    if args.config in ("c5", "c5s"):
         return bench_batch(args)
     if args.config == "zsub":
         return bench_zsub(args)
@@ -969,11 +971,12 @@ def bench_batch(args):
     import torch
 
     from paper_2505_08777_gb300 import Batch, Hologram
-    from workloads import config_c5
+    from workloads import config_c5, config_c5_small
 
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    ps = config_c5(1, count=64)
+    small = args.config == "c5s"
+    ps = config_c5_small(1, count=64) if small else config_c5(1, count=64)
     iters = ps[0].iters
     amps = [torch.from_numpy(p.amp).to(dev) for p in ps]
     coeffs = [torch.from_numpy(p.coeff).to(dev) for p in ps]
@@ -1022,12 +1025,14 @@ def bench_batch(args):
     met = b.wgs([x.clone() for x in ph0], [t.clone() for t in T], T, iters).cpu().numpy()
     terms = sum((2 * iters + 1) * p.N * p.M for p in ps)
     info = b.info()
-    line = {"metric": "spot-kernel Gterm/s fwd+adj, batched uneven WGS (64 holograms x 50 iterations), workload c5",
+    wl = ("64 holograms, sizes {256^2, 384^2, 512^2}, N log-uniform [10, 300]" if small else
+          "64 holograms, sizes {512^2, 1024^2, 1920x1152}, N log-uniform [10, 5000]")
+    line = {"metric": "spot-kernel Gterm/s fwd+adj, batched uneven WGS (64 holograms x 50 iterations), "
+                      f"workload {args.config}",
             "value": terms / (ms_b * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "64 holograms, sizes {512^2, 1024^2, 1920x1152}, N log-uniform [10, 5000], "
-                                   "D in {5, 10, 11}, 50 WGS iterations each; one step = the whole batch",
+            "config": {"workload": wl + ", D in {5, 10, 11}, 50 WGS iterations each; one step = the whole batch",
                        "terms_per_step": terms, "l2": "flushed between steps (256 MiB write)",
                        "tuned_grid": tuned, "resident_ctas": info["resident_ctas"],
                        "standalone_members": info["standalone"]},

@@ -30,7 +30,7 @@ import numpy as np
 
 __all__ = [
     "Problem", "gaussian_amplitude", "flat_amplitude", "random_phase",
-    "config_c1", "config_c2", "config_c3", "config_c4", "config_c5",
+    "config_c1", "config_c2", "config_c3", "config_c4", "config_c5", "config_c5_small",
     "make_config", "random_problem", "CONFIG_NAMES", "pixel_sample", "masked_amplitude",
 ]
 
@@ -271,6 +271,16 @@ def config_c5(seed: int = 1, count: int = 64, sizes=None, max_spots: int = 5000)
         out.append(Problem(f"c5_h{h:02d}_{nx}x{ny}_N{N}_D{D}", nx, ny, amp, phase0, noll,
                            C.astype(np.float32), target.astype(np.float32), 50))
     return out
+
+
+C5_SMALL_SIZES = [(256, 256), (384, 384), (512, 512)]
+
+
+def config_c5_small(seed: int = 1, count: int = 64) -> list:
+    """Many small holograms: the c5 recipe with grids of 256^2 to 512^2 and
+    N log-uniform in [10, 300], where no single member fills the GPU (one
+    launch per phase for the whole batch against one graph per hologram)."""
+    return config_c5(seed, count=count, sizes=C5_SMALL_SIZES, max_spots=300)
 
 
 CONFIG_NAMES = ("c1", "c2", "c3", "c4")
