@@ -601,12 +601,24 @@ ash_status ash_batch_wgs(ash_batch *b, float *const *phases, float *const *weigh
                          int iters, float *metrics_out, void *stream);
 
 /*
- * Autotuner of the launch shape: times one batched forward + adjoint for
- * CTA counts of 0.5x .. 4x the resident CTAs on the given phases, keeps the
- * fastest, and appends "key grid" to the text file cache_path (NULL: no
- * cache). A cache line with this batch's key (device SM count and the
- * hologram shapes) is used without timing. grid_out (host, may be NULL)
- * receives the chosen CTA count. Synchronises `stream`.
+ * Autotuner (the batched form's "tile shapes picked by an autotuner"): for
+ * each distinct grouping of the members (every member standalone; the
+ * persistent group for members below 2^20, 2^22, 2^24, 2^26 terms; every
+ * member the persistent kernels can take in the group) and each kernel
+ * family of the persistent group (tensor-core and FMA-pipe, or only the one
+ * forced with ash_batch_set_variant), it picks the group's CTA count among
+ * 0.5x .. 4x the resident CTAs by timing one batched forward + adjoint, then
+ * times two WGS iterations of the whole batch as the CUDA graph
+ * ash_batch_wgs runs; the fastest (grouping, family, CTA count) is applied.
+ * Phases: the caller's (host array of device pointers); weights and targets
+ * are set to 1 for the timing, so the batch's WGS state is overwritten.
+ * The choice is appended as "key solo_terms family grid" to the text file
+ * cache_path (NULL: no cache); the key is the device's SM count and each
+ * member's log2 pixel count, log2 spot count and mode count (rounded up),
+ * plus the forced family. A cache line with this batch's key is applied
+ * without timing. grid_out (host, may be NULL) receives the persistent
+ * group's CTA count (0 if the choice makes every member standalone).
+ * Synchronises the device.
  */
 ash_status ash_batch_tune(ash_batch *b, const float *const *phases, const char *cache_path, int *grid_out,
                           void *stream);

@@ -242,6 +242,7 @@ struct ash_batch {
   // kernels, in the batch's graph); the others share the persistent batched
   // launches below, whose fields all refer to that group only
   int members = 0;
+  int device = 0, sms = 0;
   std::vector<ash_hologram*> all;    // every member, in the caller's order
   std::vector<ash_hologram*> solo;   // the standalone members
   std::vector<int> group_idx;        // member index of each persistent-group hologram
@@ -262,7 +263,6 @@ struct ash_batch {
   cudaStream_t capture = nullptr;
   std::map<int, cudaGraphExec_t> graphs;
   std::map<int, int> graph_kernels;   // kernel nodes of each cached graph
-  std::string key;         // autotuner cache key
   // tensor-core path
   int variant = 0;         // 0 auto, 1 FMA-pipe kernels, 2 tensor-core kernels
   bool tc_ok = false;      // every hologram has tensor-core images with the same K-atom count
@@ -520,8 +520,8 @@ ash_status enqueue_batch_body(ash_batch* b, int iters, cudaStream_t s) {
   return ASH_OK;
 }
 
-void destroy_batch(ash_batch* b) {
-  cudaDeviceSynchronize();
+// Persistent-group resources (everything but the member handles).
+void release_group(ash_batch* b) {
   for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
   b->graphs.clear();
   b->graph_kernels.clear();
@@ -530,32 +530,241 @@ void destroy_batch(ash_batch* b) {
   for (void* q : {(void*)b->d_adj, (void*)b->d_fwd, (void*)b->d_hu0, (void*)b->d_g0, (void*)b->d_begin,
                   (void*)b->d_tsplit, (void*)b->d_lists, (void*)b->d_field, (void*)b->d_tiles0})
     if (q) cudaFree(q);
+  b->dev = nullptr;
+  b->split_buf = nullptr;
+  b->d_adj = nullptr;
+  b->d_fwd = nullptr;
+  b->d_hu0 = nullptr;
+  b->d_g0 = nullptr;
+  b->d_begin = nullptr;
+  b->d_tsplit = nullptr;
+  b->d_lists = nullptr;
+  b->d_field = nullptr;
+  b->d_tiles0 = nullptr;
+  b->solo.clear();
+  b->group_idx.clear();
+  b->holos.clear();
+  b->host.clear();
+  b->count = 0;
+  b->U = 0;
+  b->total_tiles = 0;
+  b->max_cols = 0;
+  b->G = 0;
+  b->tc_ok = false;
+}
+
+void destroy_batch(ash_batch* b) {
+  cudaDeviceSynchronize();
+  release_group(b);
   if (b->capture) cudaStreamDestroy(b->capture);
   for (ash_hologram* h : b->all) ash_hologram_destroy(h);
   delete b;
 }
 
-std::string cache_lookup(const char* path, const std::string& key) {
-  if (!path) return "";
+// Split the members into standalone ones (N * M >= solo_terms, or D beyond
+// the persistent kernels) and the persistent group, and build the group's
+// descriptor table, split scratch and tensor-core tables.
+ash_status build_group(ash_batch* b, long long solo_terms, cudaStream_t s) {
+  cudaDeviceSynchronize();   // the previous grouping's graphs and tables may still be in use
+  release_group(b);
+  b->solo_terms = solo_terms;
+  for (int i = 0; i < b->members; ++i) {
+    ash_hologram* h = b->all[i];
+    const long long terms = (long long)h->g.N * h->g.nx * h->g.ny;
+    if (terms >= solo_terms || h->g.D > kBatchMaxD) {
+      b->solo.push_back(h);
+      // a standalone member runs the batch's kernel family
+      const ash_status st = ash_set_kernel_variant(h, b->variant == 2 && !h->tc_ok ? 0 : b->variant);
+      if (st != ASH_OK) return st;
+      continue;
+    }
+    b->group_idx.push_back(i);
+    b->holos.push_back(h);
+    // the persistent FMA-pipe kernels read the register-image basis
+    ash_status st = ensure_fma_image(h);
+    if (st != ASH_OK) return st;
+    BatchHolo bh{};
+    bh.v = view_of(h);
+    bh.unit0 = b->U;
+    bh.tile0 = b->total_tiles;
+    bh.partial = h->partial;
+    bh.E = h->wgs_E;
+    bh.y = h->y;
+    bh.w = h->wgs_w;
+    bh.T = h->wgs_T;
+    bh.phase = h->wgs_phase;
+    bh.metrics = h->wgs_metrics;
+    bh.sum_a2 = h->sum_a2;
+    b->host.push_back(bh);
+    b->U += (long long)h->g.T * h->g.N;
+    b->total_tiles += h->g.T;
+    if (2 * h->g.N > b->max_cols) b->max_cols = 2 * h->g.N;
+  }
+  b->count = (int)b->group_idx.size();
+  if (b->count == 0) return ASH_OK;   // every member standalone: no persistent group
+  const int count = b->count;
+  const int sms = b->sms;
+  int dmax = 1;
+  for (const ash_hologram* h : b->holos) dmax = h->g.D > dmax ? h->g.D : dmax;
+  for (int c : kDClasses)
+    if (c >= dmax) {
+      b->dclass = c;
+      break;
+    }
+  b->fwd = fwd_kernel(b->dclass);
+  b->adj = adj_kernel(b->dclass);
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(b->fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_fwd_smem())) !=
+      cudaSuccess)
+    return status_cuda(e, "batch forward attribute");
+  if ((e = cudaFuncSetAttribute(b->adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_adj_smem())) !=
+      cudaSuccess)
+    return status_cuda(e, "batch adjoint attribute");
+  int occ_f = 0, occ_a = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, b->fwd, kBatchNT, batch_fwd_smem());
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, b->adj, kBatchNT, batch_adj_smem());
+  int occ = occ_f < occ_a ? occ_f : occ_a;
+  if (occ < 1) occ = 1;
+  b->slots = sms * occ;
+  if ((e = cudaMalloc(&b->dev, sizeof(BatchHolo) * count)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ASH_ERR_OOM, "batch descriptor allocation");
+  }
+  if ((e = cudaMalloc(&b->split_buf, sizeof(float2) * (size_t)kGridFactorMax * b->slots * 2 * kTilePix)) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return fail(ASH_ERR_OOM, "batch split scratch allocation");
+  }
+  if ((e = cudaMemcpyAsync(b->dev, b->host.data(), sizeof(BatchHolo) * count, cudaMemcpyHostToDevice, s)) !=
+      cudaSuccess)
+    return status_cuda(e, "batch descriptor upload");
+  // tensor-core path: every hologram has the operand images, one K-atom count
+  b->tc_ok = true;
+  for (const ash_hologram* h : b->holos)
+    if (!h->tc_ok || h->tc_na != b->holos[0]->tc_na) b->tc_ok = false;
+  if (b->tc_ok) {
+    b->tc_na = b->holos[0]->tc_na;
+    // the batch kernels' smem limits are set with the single-hologram kernels' (tc_prepare)
+    if ((e = tc_batch_ctas_per_sm(b->tc_na, &b->tc_adj_per_sm, &b->tc_fwd_per_sm)) != cudaSuccess)
+      return status_cuda(e, "batch tensor-core occupancy");
+    b->tc_slots = sms * b->tc_adj_per_sm;
+    const size_t gmax = (size_t)kGridFactorMax * b->tc_slots;
+    size_t blocks = 0;
+    std::vector<TcFieldDesc> fd(count);
+    std::vector<int> tiles0(count);
+    int t0 = 0;
+    for (int i = 0; i < count; ++i) {
+      const ash_hologram* h = b->holos[i];
+      blocks += (h->g.N + kTcRows - 1) / kTcRows;
+      fd[i] = TcFieldDesc{h->g, h->amp_img, h->wgs_phase, h->fimg};
+      tiles0[i] = t0;
+      t0 += h->g.T;
+    }
+    b->cap_begin = 2 * gmax + 4 * (size_t)count + 4;
+    b->cap_split = (2 * gmax + 2 * (size_t)count) * 2 * kTcRows;
+    b->cap_fix = gmax + blocks + (size_t)count;
+    if (cudaMalloc(&b->d_adj, sizeof(TcAdjParams) * count) || cudaMalloc(&b->d_fwd, sizeof(TcFwdParams) * count) ||
+        cudaMalloc(&b->d_hu0, sizeof(long long) * 2 * (count + 1)) || cudaMalloc(&b->d_g0, sizeof(int) * 2 * count) ||
+        cudaMalloc(&b->d_begin, sizeof(long long) * b->cap_begin) ||
+        cudaMalloc(&b->d_tsplit, sizeof(float2) * b->cap_split) || cudaMalloc(&b->d_lists, sizeof(int4) * b->cap_fix) ||
+        cudaMalloc(&b->d_field, sizeof(TcFieldDesc) * count) || cudaMalloc(&b->d_tiles0, sizeof(int) * count)) {
+      cudaGetLastError();
+      return fail(ASH_ERR_OOM, "batch tensor-core table allocation");
+    }
+    if ((e = cudaMemcpy(b->d_field, fd.data(), sizeof(TcFieldDesc) * count, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(b->d_tiles0, tiles0.data(), sizeof(int) * count, cudaMemcpyHostToDevice)))
+      return status_cuda(e, "batch tensor-core descriptors");
+  }
+  return set_grid(b, b->use_tc() ? b->tc_slots : b->slots);
+}
+
+// Autotuner cache key: the device's SM count and, per member in order, its
+// bucketed shape (log2 of the pixel count and of the spot count, rounded
+// up) and its mode count.
+std::string tune_key(const ash_batch* b) {
+  auto lg = [](long long v) {
+    int k = 0;
+    while ((1LL << k) < v) ++k;
+    return k;
+  };
+  std::string key = "sm" + std::to_string(b->sms);
+  for (const ash_hologram* h : b->all)
+    key += "_m" + std::to_string(lg((long long)h->g.nx * h->g.ny)) + "n" + std::to_string(lg(h->g.N)) + "d" +
+           std::to_string(h->g.D);
+  return key;
+}
+
+// The batch's WGS loop for `iters` iterations (standalone members' loops
+// and the persistent group's launches) captured and instantiated.
+ash_status capture_loop(ash_batch* b, int iters, cudaGraphExec_t* exec, int* kernels) {
+  cudaGraph_t graph = nullptr;
+  BCUDA(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal));
+  ash_status st = ASH_OK;
+  for (ash_hologram* h : b->solo)
+    if (st == ASH_OK) st = wgs_body(h, iters, b->capture);
+  if (st == ASH_OK && b->count > 0) st = enqueue_batch_body(b, iters, b->capture);
+  cudaError_t ce = cudaStreamEndCapture(b->capture, &graph);
+  if (st != ASH_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (ce != cudaSuccess) return status_cuda(ce, "batch cudaStreamEndCapture");
+  if (kernels) *kernels = graph_kernel_nodes(graph);
+  ce = cudaGraphInstantiate(exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ce != cudaSuccess) return status_cuda(ce, "batch cudaGraphInstantiate");
+  return ASH_OK;
+}
+
+// Autotuner cache: text lines "key solo_terms family grid"; the last line
+// with the batch's key wins.
+struct TuneChoice {
+  long long solo_terms = -1;
+  int family = 0;   // the batch's kernel variant: 0 automatic (tensor core where possible), 1 FMA pipe
+  int grid = 0;
+};
+
+bool cache_lookup(const char* path, const std::string& key, TuneChoice* out) {
+  if (!path) return false;
   FILE* f = fopen(path, "r");
-  if (!f) return "";
-  char line[512];
-  std::string found;
-  while (fgets(line, sizeof line, f)) {
-    char k[400];
-    int g = 0;
-    if (sscanf(line, "%399s %d", k, &g) == 2 && key == k) found = std::to_string(g);
+  if (!f) return false;
+  std::vector<char> line(1 << 16);
+  bool found = false;
+  while (fgets(line.data(), (int)line.size(), f)) {
+    const std::string l(line.data());
+    const size_t sp = l.find(' ');
+    if (sp != key.size() || l.compare(0, sp, key) != 0) continue;
+    TuneChoice c;
+    if (sscanf(l.c_str() + sp, " %lld %d %d", &c.solo_terms, &c.family, &c.grid) == 3 && c.solo_terms >= 0 &&
+        (c.family == 0 || c.family == 1) && c.grid >= 0) {
+      *out = c;
+      found = true;
+    }
   }
   fclose(f);
   return found;
 }
 
-void cache_store(const char* path, const std::string& key, int G) {
+void cache_store(const char* path, const std::string& key, const TuneChoice& c) {
   if (!path) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s %d\n", key.c_str(), G);
+  fprintf(f, "%s %lld %d %d\n", key.c_str(), c.solo_terms, c.family, c.grid);
   fclose(f);
+}
+
+// Apply a tuned choice: grouping, kernel family, persistent grid.
+ash_status apply_choice(ash_batch* b, const TuneChoice& c, cudaStream_t s) {
+  b->variant = c.family;
+  ash_status st = build_group(b, c.solo_terms, s);
+  if (st != ASH_OK) return st;
+  if (b->count > 0 && c.grid > 0) st = set_grid(b, c.grid);
+  return st;
+}
+
+__global__ void k_fill_f(float* __restrict__ x, int n, float v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = v;
 }
 
 }  // namespace
@@ -579,137 +788,24 @@ ash_status ash_batch_create_ex(ash_batch** out, int count, const ash_hologram_de
   if (consume_injected_failure()) return fail(ASH_ERR_INJECTED, "injected failure");
   ash_batch* b = new ash_batch();
   b->members = count;
-  b->solo_terms = solo_terms;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   auto bail = [&](ash_status st) {
     destroy_batch(b);
     return st;
   };
-  int dev = 0, sms = 0;
-  cudaError_t e0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  std::vector<int> grouped;
-  for (int i = 0; i < count; ++i)
-    if (!is_solo(descs[i])) grouped.push_back(i);
-  std::string key = "sm" + std::to_string(sms) + "_n" + std::to_string(grouped.size());
+  cudaGetDevice(&b->device);
+  cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
   for (int i = 0; i < count; ++i) {
     const ash_hologram_desc& d = descs[i];
     ash_hologram* h = nullptr;
     ash_status st = ash_hologram_create(&h, d.nx, d.ny, d.amp, d.D, d.noll, d.basis, d.N, d.coeff, stream);
     if (st != ASH_OK) return bail(st);
     b->all.push_back(h);
-    if (is_solo(d)) {
-      b->solo.push_back(h);
-      continue;
-    }
-    b->holos.push_back(h);
-    // the persistent FMA-pipe kernels read the register-image basis
-    st = ensure_fma_image(h);
-    if (st != ASH_OK) return bail(st);
-    BatchHolo bh{};
-    bh.v = view_of(h);
-    bh.unit0 = b->U;
-    bh.tile0 = b->total_tiles;
-    bh.partial = h->partial;
-    bh.E = h->wgs_E;
-    bh.y = h->y;
-    bh.w = h->wgs_w;
-    bh.T = h->wgs_T;
-    bh.phase = h->wgs_phase;
-    bh.metrics = h->wgs_metrics;
-    bh.sum_a2 = h->sum_a2;
-    b->host.push_back(bh);
-    b->U += (long long)h->g.T * h->g.N;
-    b->total_tiles += h->g.T;
-    if (2 * h->g.N > b->max_cols) b->max_cols = 2 * h->g.N;
-    key += "_" + std::to_string(d.nx) + "x" + std::to_string(d.ny) + "n" + std::to_string(d.N) + "d" +
-           std::to_string(d.D);
-    if (key.size() > 300) key = key.substr(0, 300);
   }
-  b->key = key;
-  b->count = (int)grouped.size();
-  b->group_idx = grouped;
-  if ((e0 = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking)) != cudaSuccess)
-    return bail(status_cuda(e0, "batch capture stream"));
-  if (b->count == 0) {   // every member standalone: no persistent group
-    *out = b;
-    return ASH_OK;
-  }
-  count = b->count;
-  int dmax = 1;
-  for (int i : grouped) dmax = descs[i].D > dmax ? descs[i].D : dmax;
-  for (int c : kDClasses)
-    if (c >= dmax) {
-      b->dclass = c;
-      break;
-    }
-  b->fwd = fwd_kernel(b->dclass);
-  b->adj = adj_kernel(b->dclass);
-  cudaError_t e;
-  if ((e = cudaFuncSetAttribute(b->fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_fwd_smem())) !=
-      cudaSuccess)
-    return bail(status_cuda(e, "batch forward attribute"));
-  if ((e = cudaFuncSetAttribute(b->adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_adj_smem())) !=
-      cudaSuccess)
-    return bail(status_cuda(e, "batch adjoint attribute"));
-  int occ_f = 0, occ_a = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, b->fwd, kBatchNT, batch_fwd_smem());
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, b->adj, kBatchNT, batch_adj_smem());
-  int occ = occ_f < occ_a ? occ_f : occ_a;
-  if (occ < 1) occ = 1;
-  b->slots = sms * occ;
-  if ((e = cudaMalloc(&b->dev, sizeof(BatchHolo) * count)) != cudaSuccess) {
-    cudaGetLastError();
-    return bail(fail(ASH_ERR_OOM, "batch descriptor allocation"));
-  }
-  if ((e = cudaMalloc(&b->split_buf, sizeof(float2) * (size_t)kGridFactorMax * b->slots * 2 * kTilePix)) !=
-      cudaSuccess) {
-    cudaGetLastError();
-    return bail(fail(ASH_ERR_OOM, "batch split scratch allocation"));
-  }
-  if ((e = cudaMemcpyAsync(b->dev, b->host.data(), sizeof(BatchHolo) * count, cudaMemcpyHostToDevice, s)) !=
-      cudaSuccess)
-    return bail(status_cuda(e, "batch descriptor upload"));
-  // tensor-core path: every hologram has the operand images, one K-atom count
-  b->tc_ok = true;
-  for (const ash_hologram* h : b->holos)
-    if (!h->tc_ok || h->tc_na != b->holos[0]->tc_na) b->tc_ok = false;
-  if (b->tc_ok) {
-    b->tc_na = b->holos[0]->tc_na;
-    // the batch kernels' smem limits are set with the single-hologram kernels' (tc_prepare)
-    if ((e = tc_batch_ctas_per_sm(b->tc_na, &b->tc_adj_per_sm, &b->tc_fwd_per_sm)) != cudaSuccess)
-      return bail(status_cuda(e, "batch tensor-core occupancy"));
-    b->tc_slots = sms * b->tc_adj_per_sm;
-    const size_t gmax = (size_t)kGridFactorMax * b->tc_slots;
-    size_t blocks = 0;
-    std::vector<TcFieldDesc> fd(count);
-    std::vector<int> tiles0(count);
-    int t0 = 0;
-    for (int i = 0; i < count; ++i) {
-      const ash_hologram* h = b->holos[i];
-      blocks += (h->g.N + kTcRows - 1) / kTcRows;
-      fd[i] = TcFieldDesc{h->g, h->amp_img, h->wgs_phase, h->fimg};
-      tiles0[i] = t0;
-      t0 += h->g.T;
-    }
-    b->cap_begin = 2 * gmax + 4 * (size_t)count + 4;
-    b->cap_split = (2 * gmax + 2 * (size_t)count) * 2 * kTcRows;
-    b->cap_fix = gmax + blocks + (size_t)count;
-    if (cudaMalloc(&b->d_adj, sizeof(TcAdjParams) * count) || cudaMalloc(&b->d_fwd, sizeof(TcFwdParams) * count) ||
-        cudaMalloc(&b->d_hu0, sizeof(long long) * 2 * (count + 1)) || cudaMalloc(&b->d_g0, sizeof(int) * 2 * count) ||
-        cudaMalloc(&b->d_begin, sizeof(long long) * b->cap_begin) ||
-        cudaMalloc(&b->d_tsplit, sizeof(float2) * b->cap_split) || cudaMalloc(&b->d_lists, sizeof(int4) * b->cap_fix) ||
-        cudaMalloc(&b->d_field, sizeof(TcFieldDesc) * count) || cudaMalloc(&b->d_tiles0, sizeof(int) * count)) {
-      cudaGetLastError();
-      return bail(fail(ASH_ERR_OOM, "batch tensor-core table allocation"));
-    }
-    if ((e = cudaMemcpy(b->d_field, fd.data(), sizeof(TcFieldDesc) * count, cudaMemcpyHostToDevice)) ||
-        (e = cudaMemcpy(b->d_tiles0, tiles0.data(), sizeof(int) * count, cudaMemcpyHostToDevice)))
-      return bail(status_cuda(e, "batch tensor-core descriptors"));
-  }
-  ash_status gst = set_grid(b, b->use_tc() ? b->tc_slots : b->slots);
-  if (gst != ASH_OK) return bail(gst);
+  cudaError_t e0 = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
+  if (e0 != cudaSuccess) return bail(status_cuda(e0, "batch capture stream"));
+  ash_status st = build_group(b, solo_terms, s);
+  if (st != ASH_OK) return bail(st);
   *out = b;
   return ASH_OK;
 }
@@ -792,22 +888,9 @@ ash_status ash_batch_wgs(ash_batch* b, float* const* phases, float* const* weigh
   if (it != b->graphs.end()) {
     exec = it->second;
   } else {
-    cudaGraph_t graph = nullptr;
-    BCUDA(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal));
-    ash_status st = ASH_OK;
-    for (ash_hologram* h : b->solo)
-      if (st == ASH_OK) st = wgs_body(h, iters, b->capture);
-    if (st == ASH_OK && b->count > 0) st = enqueue_batch_body(b, iters, b->capture);
-    cudaError_t ce = cudaStreamEndCapture(b->capture, &graph);
-    if (st != ASH_OK) {
-      if (graph) cudaGraphDestroy(graph);
-      return st;
-    }
-    if (ce != cudaSuccess) return status_cuda(ce, "batch cudaStreamEndCapture");
-    const int kernels = graph_kernel_nodes(graph);
-    ce = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (ce != cudaSuccess) return status_cuda(ce, "batch cudaGraphInstantiate");
+    int kernels = 0;
+    ash_status st = capture_loop(b, iters, &exec, &kernels);
+    if (st != ASH_OK) return st;
     b->graphs[iters] = exec;
     b->graph_kernels[iters] = kernels;
   }
@@ -826,65 +909,130 @@ ash_status ash_batch_wgs(ash_batch* b, float* const* phases, float* const* weigh
 ash_status ash_batch_tune(ash_batch* b, const float* const* phases, const char* cache_path, int* grid_out,
                           void* stream) {
   if (!b || !phases) return fail(ASH_ERR_INVALID_ARG, "NULL argument");
-  const std::string key = b->key + (b->use_tc() ? "_tc" : "");
-  const std::string hit = cache_lookup(cache_path, key);
-  if (!hit.empty()) {
-    ash_status gst = set_grid(b, std::stoi(hit));
-    if (gst != ASH_OK) return gst;
+  for (int i = 0; i < b->members; ++i)
+    if (!phases[i]) return fail(ASH_ERR_INVALID_ARG, "NULL per-hologram phase");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // a kernel family forced with ash_batch_set_variant is kept; the automatic
+  // one is tuned between the tensor-core and the FMA-pipe kernels
+  const int forced = b->variant;
+  const std::string key = tune_key(b) + (forced ? "_v" + std::to_string(forced) : std::string());
+  TuneChoice hit;
+  if (cache_lookup(cache_path, key, &hit)) {
+    ash_status st = apply_choice(b, hit, s);
+    if (st != ASH_OK) return st;
     if (grid_out) *grid_out = b->G;
     return ASH_OK;
   }
   if (consume_injected_failure()) return fail(ASH_ERR_INJECTED, "injected failure");
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (b->count == 0) {   // nothing to tune: every member runs standalone
-    if (grid_out) *grid_out = 0;
-    return ASH_OK;
+  // the timed loops run on the caller's phases with unit weights and targets
+  for (int i = 0; i < b->members; ++i) {
+    ash_hologram* h = b->all[i];
+    const int N = h->g.N;
+    BCUDA(cudaMemcpyAsync(h->wgs_phase, phases[i], (size_t)h->g.nx * h->g.ny * 4, cudaMemcpyDeviceToDevice, s));
+    k_fill_f<<<(N + 255) / 256, 256, 0, s>>>(h->wgs_w, N, 1.0f);
+    k_fill_f<<<(N + 255) / 256, 256, 0, s>>>(h->wgs_T, N, 1.0f);
+    BCUDA(cudaGetLastError());
   }
-  for (int i = 0; i < b->count; ++i) {
-    const ash_hologram* h = b->holos[i];
-    BCUDA(cudaMemcpyAsync(h->wgs_phase, phases[b->group_idx[i]], (size_t)h->g.nx * h->g.ny * 4,
-                          cudaMemcpyDeviceToDevice, s));
-    BCUDA(cudaMemsetAsync(h->y, 0, (size_t)h->g.N * sizeof(float2), s));
-  }
-  if (b->use_tc()) BCUDA(tc_field_img_batch(b->d_field, b->d_tiles0, b->count, b->total_tiles, s));
-  auto fwd_adj = [&]() -> ash_status {
-    if (b->use_tc()) {
-      ash_status st = enqueue_tc_forward(b, s);
-      return st == ASH_OK ? enqueue_tc_adjoint(b, s) : st;
-    }
-    ash_status st = enqueue_batch_forward(b, s);
-    return st == ASH_OK ? enqueue_batch_adjoint(b, s) : st;
-  };
-  // candidate launch shapes: fractions and multiples of the resident CTAs
-  const int sl = b->use_tc() ? b->tc_slots : b->slots;
-  const int cands[] = {sl / 2, sl, (3 * sl) / 2, 2 * sl, 3 * sl, 4 * sl};
+  BCUDA(cudaStreamSynchronize(s));
   cudaEvent_t e0, e1;
   BCUDA(cudaEventCreate(&e0));
   BCUDA(cudaEventCreate(&e1));
-  float best = 1e30f;
-  int best_g = b->slots;
-  for (int c : cands) {
-    if (c < 1) continue;
-    ash_status st = set_grid(b, c);
-    if (st == ASH_OK) st = fwd_adj();   // warm-up
+  // one warm-up call, then `reps` timed calls
+  auto elapsed = [&](auto&& fn, int reps, float* ms) -> ash_status {
+    ash_status st = fn();
     if (st != ASH_OK) return st;
     BCUDA(cudaEventRecord(e0, s));
-    for (int r = 0; r < 2 && st == ASH_OK; ++r) st = fwd_adj();
+    for (int r = 0; r < reps && st == ASH_OK; ++r) st = fn();
     if (st != ASH_OK) return st;
     BCUDA(cudaEventRecord(e1, s));
     BCUDA(cudaEventSynchronize(e1));
-    float ms = 0.0f;
-    BCUDA(cudaEventElapsedTime(&ms, e0, e1));
-    if (ms < best) {
-      best = ms;
-      best_g = b->G;
+    BCUDA(cudaEventElapsedTime(ms, e0, e1));
+    return ASH_OK;
+  };
+  // candidate groupings: every member standalone, the persistent group for
+  // members below 2^20 .. 2^26 terms, every member in the group (those the
+  // persistent kernels cannot take stay standalone); distinct ones only
+  std::vector<long long> thresholds;
+  std::vector<std::vector<bool>> parts;
+  for (long long thr : {0LL, 1LL << 20, 1LL << 22, 1LL << 24, 1LL << 26, 1LL << 62}) {
+    std::vector<bool> p;
+    for (const ash_hologram* h : b->all)
+      p.push_back((long long)h->g.N * h->g.nx * h->g.ny >= thr || h->g.D > kBatchMaxD);
+    bool seen = false;
+    for (const auto& q : parts) seen = seen || q == p;
+    if (!seen) {
+      parts.push_back(p);
+      thresholds.push_back(thr);
     }
+  }
+  TuneChoice best;
+  best.solo_terms = b->solo_terms;
+  best.family = forced;
+  float best_ms = 1e30f;
+  const int kTimedIters = 2;
+  ash_status st = ASH_OK;
+  const std::vector<int> families = forced ? std::vector<int>{forced} : std::vector<int>{0, 1};
+  for (long long thr : thresholds) {
+    for (int fam : families) {
+      b->variant = fam;
+      if ((st = build_group(b, thr, s)) != ASH_OK) break;
+      // family 1 on a grouping without a persistent group, or 0 on a group
+      // the tensor-core kernels cannot take, repeats the other family's case
+      if (families.size() > 1 && fam == 1 && b->count == 0) continue;
+      if (families.size() > 1 && fam == 0 && b->count > 0 && !b->tc_ok) continue;
+      int grid = 0;
+      if (b->count > 0) {
+        // launch shape of the persistent group: one forward + adjoint per candidate CTA count
+        if (b->use_tc()) BCUDA(tc_field_img_batch(b->d_field, b->d_tiles0, b->count, b->total_tiles, s));
+        auto fwd_adj = [&]() -> ash_status {
+          if (b->use_tc()) {
+            ash_status r = enqueue_tc_forward(b, s);
+            return r == ASH_OK ? enqueue_tc_adjoint(b, s) : r;
+          }
+          ash_status r = enqueue_batch_forward(b, s);
+          return r == ASH_OK ? enqueue_batch_adjoint(b, s) : r;
+        };
+        const int sl = b->use_tc() ? b->tc_slots : b->slots;
+        float gbest = 1e30f;
+        for (int c : {sl / 2, sl, (3 * sl) / 2, 2 * sl, 3 * sl, 4 * sl}) {
+          if (c < 1) continue;
+          if ((st = set_grid(b, c)) != ASH_OK) break;
+          float ms = 0.0f;
+          if ((st = elapsed(fwd_adj, 2, &ms)) != ASH_OK) break;
+          if (ms < gbest) {
+            gbest = ms;
+            grid = b->G;
+          }
+        }
+        if (st == ASH_OK) st = set_grid(b, grid);
+        if (st != ASH_OK) break;
+      }
+      // the whole loop of this choice, as the graph ash_batch_wgs runs
+      cudaGraphExec_t exec = nullptr;
+      if ((st = capture_loop(b, kTimedIters, &exec, nullptr)) != ASH_OK) break;
+      float ms = 0.0f;
+      st = elapsed(
+          [&]() -> ash_status {
+            const cudaError_t ce = cudaGraphLaunch(exec, s);
+            return ce == cudaSuccess ? ASH_OK : status_cuda(ce, "tuner graph launch");
+          },
+          2, &ms);
+      cudaGraphExecDestroy(exec);
+      if (st != ASH_OK) break;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best.solo_terms = thr;
+        best.family = fam;
+        best.grid = grid;
+      }
+    }
+    if (st != ASH_OK) break;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  ash_status gst = set_grid(b, best_g);
-  if (gst != ASH_OK) return gst;
-  cache_store(cache_path, key, b->G);
+  if (st != ASH_OK) return st;
+  if ((st = apply_choice(b, best, s)) != ASH_OK) return st;
+  cache_store(cache_path, key, best);
   if (grid_out) *grid_out = b->G;
   return ASH_OK;
 }

@@ -113,12 +113,16 @@ def test_batch_autotuner_picks_and_caches(tmp_path, variant):
     ph, _, _ = _state(ps)
     cache = str(tmp_path / "tune.txt")
     g = b.tune(ph, cache)
-    assert g >= 1 and os.path.exists(cache)
-    lines = open(cache).read().split("\n")
-    assert any(line.endswith(f" {g}") for line in lines)
+    assert g >= 0 and os.path.exists(cache)
+    lines = [line.split() for line in open(cache).read().split("\n") if line]
+    assert len(lines) == 1 and int(lines[0][3]) == g and int(lines[0][2]) == variant
+    solo = int(lines[0][1])
+    assert b.info()["standalone"] == sum(p.N * p.nx * p.ny >= solo for p in ps)
     b2 = _batch(ps, variant)
     assert b2.tune(ph, cache) == g            # read from the cache
-    assert b2.info()["grid"] == g
+    assert b2.info()["grid"] == g and b2.info()["standalone"] == b.info()["standalone"]
+    if g == 0:
+        return
     if variant == 1:   # forward + reduction, update, adjoint (+ fix-up); final forward, metrics
         assert b.launches(5) in (5 * 4 + 3, 5 * 5 + 3)
     else:              # nearfield images and forward (+ reduction) once, then update, adjoint (+ fix-up), forward (+ reduction)
@@ -153,7 +157,11 @@ def test_batch_standalone_members(solo_terms):
     info = b.info()
     assert info["count"] == len(ps) and info["standalone"] == sum(solo)
     if all(solo):
-        assert info["grid"] == 0 and b.tune([torch.from_numpy(p.phase0).cuda() for p in ps]) == 0
+        assert info["grid"] == 0
+        # the tuner may regroup (it chooses the standalone threshold); its grid is the batch's
+        assert b.tune([torch.from_numpy(p.phase0).cuda() for p in ps]) == b.info()["grid"]
+        b = Batch([(torch.from_numpy(p.amp).cuda(), torch.from_numpy(p.coeff).cuda(), p.noll) for p in ps],
+                  solo_terms=solo_terms)
     ph, w, T = _state(ps)
     met = b.wgs(ph, w, T, 4)
     lib = _lib.load()
@@ -181,3 +189,23 @@ def test_batch_rejects_negative_threshold():
     p = _problems(95)[0]
     with pytest.raises(AshError):
         Batch([(torch.from_numpy(p.amp).cuda(), torch.from_numpy(p.coeff).cuda(), p.noll)], solo_terms=-1)
+
+
+def test_batch_autotuner_tunes_family_and_grouping(tmp_path):
+    # automatic family: the tuner chooses the grouping, the persistent
+    # group's kernel family and its CTA count; the tuned batch still solves
+    # every member as the oracle does
+    ps = _problems(95)
+    b = _batch(ps)
+    ph, w, T = _state(ps)
+    cache = str(tmp_path / "tune.txt")
+    g = b.tune(ph, cache)
+    key, solo, fam, grid = open(cache).read().split()
+    assert key.startswith("sm") and int(fam) in (0, 1) and int(grid) == g
+    assert b.info()["standalone"] == sum(p.N * p.nx * p.ny >= int(solo) for p in ps)
+    ph, w, T = _state(ps)
+    met = b.wgs(ph, w, T, 10).cpu().numpy()
+    for k, p in enumerate(ps):
+        Z, C, A = oracle_inputs(p)
+        res = wgs.run(A, p.phase0, C, Z, p.target, 10, workers=4)
+        assert abs(float(met[k, 0]) - res.uniformity) <= UNIF_TOL, (k, met[k, 0], res.uniformity)
