@@ -122,9 +122,14 @@ static __global__ void k_tc_build_czs(const float* __restrict__ coeff, int N, co
           const float hi = to_tf32(c);
           v = kind == 2 ? to_tf32(c - hi) : hi;   // [hi | hi | lo]
         } else {
-          const float cr = coeff[(size_t)n * D + (kind == 3 ? L.tx : L.ty)] / L.R;   // rad per pixel
-          const float hi = to_tf32(cr);
-          v = mode == 0 ? hi : to_tf32(cr - hi);
+          // rad per pixel, split into L.tp tf32 pieces (piece `mode`)
+          const double cr = (double)coeff[(size_t)n * D + (kind == 3 ? L.tx : L.ty)] / (double)L.R;
+          double rest = cr;
+          for (int q = 0; q <= mode; ++q) {
+            const float piece = to_tf32((float)rest);
+            v = piece;
+            rest -= (double)piece;
+          }
         }
       }
       dst[a * 2048 + swz128(r, kk)] = v;

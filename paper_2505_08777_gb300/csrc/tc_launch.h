@@ -20,35 +20,45 @@ constexpr int kTcMaxModes = 21;                        // 3 D <= 64
 
 // K layout of the operand rows. Regular: the pixel row [hi | lo | hi] and the
 // spot row [hi | hi | lo] of the D basis values / coefficients (3 D slots).
-// Tilt-exact (when the basis holds the x and y tilts, Noll 2 and 3, and the
-// regular layout would need a second K-atom): across a tile the tilts change
-// by exactly (i - i_anchor) / R and (j - j_anchor) / R, so the pixel row
-// carries the integer offsets di, dj (exact in tf32) and the spot row the
-// split c_x / R and c_y / R, two slots per tilt:
-//   pixel [hi | lo | hi (other D - 2 modes) | di  di  dj  dj ]
-//   spot  [hi | hi | lo (other D - 2 modes) | xh  xl  yh  yl ]
-// which fits D = 11 into one K-atom of 32.
+// Tilt-exact (when the basis holds the x and y tilts, Noll 2 and 3): across
+// a tile the tilts change by exactly (i - i_anchor) / R and (j - j_anchor) /
+// R, so the pixel row carries the integer offsets di, dj (exact in tf32) and
+// the spot row c_x / R and c_y / R split into tf32 pieces, TP slots per tilt:
+//   pixel [hi | lo | hi (other D - 2 modes) | di .. di  dj .. dj ]
+//   spot  [hi | hi | lo (other D - 2 modes) | x pieces  y pieces ]
+// Every product di * piece is exact, so the tilts' part of the local phase
+// carries only the error of splitting c / R: 2^-22 of it with two pieces,
+// about 2^-33 with three. Three pieces are used when they fit one K-atom
+// (D <= 10), two when only those fit (D = 11, which then needs one K-atom
+// instead of two); the regular layout keeps bases without both tilts.
 struct TcLayout {
   int D;
   int NA;        // K-atoms of 32 tf32 per row
   int tx, ty;    // positions of the x / y tilt among the D modes (tilt-exact), else -1
   float R;       // min(nx, ny_full) / 2 (grid_radius)
+  int tp;        // tf32 pieces of each tilt's c / R (tilt-exact: 2 or 3)
 };
 __host__ __device__ constexpr int tc_na(int D) { return 3 * D <= 32 ? 1 : 2; }
 inline TcLayout tc_layout(int D, const int* noll, const Geometry& g) {
-  TcLayout L{D, tc_na(D), -1, -1, (float)grid_radius(g)};
-  if (noll && L.NA > 1 && 3 * (D - 2) + 4 <= 32) {
+  TcLayout L{D, tc_na(D), -1, -1, (float)grid_radius(g), 0};
+  if (noll && D >= 2) {
+    int tx = -1, ty = -1;
     for (int d = 0; d < D; ++d) {
-      if (noll[d] == 2) L.tx = d;
-      if (noll[d] == 3) L.ty = d;
+      if (noll[d] == 2) tx = d;
+      if (noll[d] == 3) ty = d;
     }
-    if (L.tx >= 0 && L.ty >= 0) L.NA = 1;
-    else L.tx = L.ty = -1;
+    if (tx >= 0 && ty >= 0) {
+      if (3 * (D - 2) + 6 <= 32) {
+        L = TcLayout{D, 1, tx, ty, L.R, 3};
+      } else if (3 * (D - 2) + 4 <= 32) {
+        L = TcLayout{D, 1, tx, ty, L.R, 2};
+      }
+    }
   }
   return L;
 }
 // Slot `col` of a row: kind 0..2 = segment of mode `mode`, 3 = x tilt
-// (part `mode` = 0 hi / 1 lo), 4 = y tilt, -1 = padding.
+// (piece `mode`, 0 = hi), 4 = y tilt, -1 = padding.
 __host__ __device__ inline void tc_slot(const TcLayout& L, int col, int& kind, int& mode) {
   kind = -1;
   mode = 0;
@@ -70,9 +80,10 @@ __host__ __device__ inline void tc_slot(const TcLayout& L, int col, int& kind, i
         break;
       }
     }
-  } else if (col < 3 * Dp + 4) {
-    kind = col < 3 * Dp + 2 ? 3 : 4;
-    mode = (col - 3 * Dp) & 1;
+  } else if (col < 3 * Dp + 2 * L.tp) {
+    const int c = col - 3 * Dp;
+    kind = c < L.tp ? 3 : 4;
+    mode = c % L.tp;
   }
 }
 
