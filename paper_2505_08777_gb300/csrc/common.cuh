@@ -159,6 +159,45 @@ __device__ __forceinline__ void sincos2(float2 x, float2& s, float2& c) {
   c.y = __cosf(x.y);
 }
 
+// x - 2 pi rint(x / 2 pi) for two arguments (|x| < 2^22): the quotient's
+// rint on the FP32 pipe, then the product with 2 pi in two pieces whose high
+// part 6.28125 has 8 significant bits, so that k * 6.28125 is exact for
+// |k| < 2^16 and each fused step rounds once. The MUFU's sin.approx /
+// cos.approx error is about 3.4e-7 for |x| <= pi and grows about
+// 1.35e-7 |x| beyond, so reduced arguments keep the transforms' per-term
+// error near the fp32 rounding of the phase itself. 5 packed instructions.
+__device__ __forceinline__ float2 reduce_2pi2(float2 x) {
+  const float2 one = make_float2(1.0f, 1.0f);
+  const float2 magic = make_float2(12582912.0f, 12582912.0f), nmagic = make_float2(-12582912.0f, -12582912.0f);
+  const float2 t = mul2(x, make_float2(0.159154943091895336f, 0.159154943091895336f));
+  const float2 k = fma2(fma2(t, one, magic), one, nmagic);   // rint(t)
+  const float2 r = fma2(k, make_float2(-6.28125f, -6.28125f), x);
+  return fma2(k, make_float2(-1.9353071795864769e-3f, -1.9353071795864769e-3f), r);
+}
+
+// How the transforms feed the MUFU (ASH_MUFU_MODE): 0 the phase as it is;
+// 1 the phase reduced to [-pi, pi] first (reduce_2pi2); 2 the phase scaled
+// by 1 + kMufuBias. Measured on GB300 against float64 over |x| <= 33 rad:
+// sin.approx / cos.approx return the sine and cosine of a phase shrunk by
+// 6e-8 .. 9e-8 of itself (mean 7.5e-8, varying with the binade of
+// x / 2 pi), with a random part of about a third of that, so scaling the
+// argument by 1 + 7.5e-8 (one packed FMA per pair) removes most of the
+// systematic error that reduction removes with five.
+#ifndef ASH_MUFU_MODE
+#define ASH_MUFU_MODE 1
+#endif
+constexpr float kMufuBias = 7.5e-8f;
+__device__ __forceinline__ float2 mufu_arg2(float2 x) {
+  if constexpr (ASH_MUFU_MODE == 1) {
+    return reduce_2pi2(x);
+  } else if constexpr (ASH_MUFU_MODE == 2) {
+    return fma2(x, make_float2(kMufuBias, kMufuBias), x);
+  } else {
+    return x;
+  }
+}
+__device__ __forceinline__ void sincos2_reduced(float2 x, float2& s, float2& c) { sincos2(mufu_arg2(x), s, c); }
+
 // sin and cos of two arguments on the FP32 pipe (packed FFMA2), to share the
 // transforms' sincos load between the MUFU and the FP32 pipes. Reduction to
 // the half angle: t = x / (2 pi), r = t - rint(t) in [-1/2, 1/2] (rint by
@@ -172,7 +211,10 @@ __device__ __forceinline__ void sincos2(float2 x, float2& s, float2& c) {
 __device__ __forceinline__ void sincos2_poly(float2 x, float2& s, float2& c) {
   const float2 one = make_float2(1.0f, 1.0f), mone = make_float2(-1.0f, -1.0f);
   const float2 magic = make_float2(12582912.0f, 12582912.0f), nmagic = make_float2(-12582912.0f, -12582912.0f);
-  const float2 t = mul2(x, make_float2(0.159154943091895336f, 0.159154943091895336f));
+  // t = x / (2 pi); with ASH_MUFU_MODE 2 the fp32 constant's rounding
+  // (-4e-8 of it) is made up by a second term
+  float2 t = mul2(x, make_float2(0.159154943091895336f, 0.159154943091895336f));
+  if constexpr (ASH_MUFU_MODE == 2) t = fma2(x, make_float2(6.4206382e-09f, 6.4206382e-09f), t);
   const float2 k = fma2(fma2(t, one, magic), one, nmagic);   // rint(t)
   const float2 r = fma2(k, mone, t);
   const float2 u = mul2(r, r);
@@ -213,8 +255,9 @@ __device__ __forceinline__ void sin2_mixed(int k, float2 x, float2& s) {
     float2 c;
     sincos2_poly(x, s, c);   // the cosine's last step is dead code here
   } else {
-    s.x = __sinf(x.x);
-    s.y = __sinf(x.y);
+    const float2 r = mufu_arg2(x);
+    s.x = __sinf(r.x);
+    s.y = __sinf(r.y);
   }
 }
 
@@ -223,7 +266,7 @@ __device__ __forceinline__ void sincos2_mixed(int k, float2 x, float2& s, float2
   if (NUM > 0 && (k * NUM) % 9 < NUM) {
     sincos2_poly(x, s, c);
   } else {
-    sincos2(x, s, c);
+    sincos2_reduced(x, s, c);
   }
 }
 

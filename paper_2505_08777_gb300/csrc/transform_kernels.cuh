@@ -202,7 +202,7 @@ __device__ __forceinline__ void forward_tile(const HoloView& hv, int source, con
           for (int q = 0; q < P / 2; ++q) {
             const float2 x = local_phase<D>(cc, dz[q]);
             float2 sn, cs;
-            sincos2(x, sn, cs);
+            sincos2_reduced(x, sn, cs);
             re2 = fma2(fr2[q], cs, re2);
             re2 = fma2(fi2[q], sn, re2);
             im2 = fma2(fi2[q], cs, im2);
@@ -271,7 +271,7 @@ __device__ __forceinline__ void adjoint_tile(const HoloView& hv, const float2* _
       for (int q = 0; q < P / 2; ++q) {
         const float2 x = local_phase<D>(cc, dz[q]);
         float2 sn, cs;
-        sincos2(x, sn, cs);
+        sincos2_reduced(x, sn, cs);
         re2[q] = fma2(yr2, cs, re2[q]);
         re2[q] = fma2(nyi2, sn, re2[q]);
         im2[q] = fma2(yi2, cs, im2[q]);
