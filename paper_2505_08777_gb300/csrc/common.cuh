@@ -211,10 +211,10 @@ __device__ __forceinline__ void sincos2_reduced(float2 x, float2& s, float2& c) 
 __device__ __forceinline__ void sincos2_poly(float2 x, float2& s, float2& c) {
   const float2 one = make_float2(1.0f, 1.0f), mone = make_float2(-1.0f, -1.0f);
   const float2 magic = make_float2(12582912.0f, 12582912.0f), nmagic = make_float2(-12582912.0f, -12582912.0f);
-  // t = x / (2 pi); with ASH_MUFU_MODE 2 the fp32 constant's rounding
+  // t = x / (2 pi); unless ASH_MUFU_MODE is 0 the fp32 constant's rounding
   // (-4e-8 of it) is made up by a second term
   float2 t = mul2(x, make_float2(0.159154943091895336f, 0.159154943091895336f));
-  if constexpr (ASH_MUFU_MODE == 2) t = fma2(x, make_float2(6.4206382e-09f, 6.4206382e-09f), t);
+  if constexpr (ASH_MUFU_MODE != 0) t = fma2(x, make_float2(6.4206382e-09f, 6.4206382e-09f), t);
   const float2 k = fma2(fma2(t, one, magic), one, nmagic);   // rint(t)
   const float2 r = fma2(k, mone, t);
   const float2 u = mul2(r, r);
@@ -232,19 +232,23 @@ __device__ __forceinline__ void sincos2_poly(float2 x, float2& s, float2& c) {
 
 // Which pixel pairs of an unrolled loop take the FP32-pipe sincos: NUM of
 // every 9, spread evenly. Per pair the MUFU path costs 32 MUFU-pipe cycles
-// per warp (4 sin/cos at 16 per clk per SM) and ~10 FP32-pipe cycles, the
-// FP32 path ~40 FP32-pipe cycles; the measured best share is lower than the
-// pipe balance (the polynomial's dependent chains add latency) and depends
-// on the kernel's own FP32 work: ASH_POLY_FWD / _ADJ / _GRAD of 9. Measured
-// on GB300 (1024^2, D = 10): 2 / 9 in the tensor-core forward and adjoint
-// (5-9 % faster than 0 / 9; 3 / 9 and 4 / 9 gain less, 5 / 9 is slower),
-// 0 / 9 in the moment pass (it needs one sine per pixel, not a sine and a
-// cosine, and its FP32 pipe also carries the moments: 1 / 9 is 5 % slower).
+// per warp (4 sin/cos at 16 per clk per SM) and ~10 FP32-pipe cycles (~20
+// with the argument reduction), the FP32 path ~40 FP32-pipe cycles; the
+// measured best share is lower than the pipe balance (the polynomial's
+// dependent chains add latency) and depends on the kernel's own FP32 work:
+// ASH_POLY_FWD / _ADJ / _GRAD of 9. Measured on GB300 with the reduced MUFU
+// arguments (c2 1024^2 N = 400 / c4 N = 1024 / c3, forward and adjoint us):
+// 0/9 277.6, 290.7 / 620.2, 688.1 / 2615, 2845; 2/9 273.4, 292.8 / 609.6,
+// 694.3 / 2570, 2844; 3/9 267.3, 298.9 / 601.2, 706.5 / 2544, 2954; 4/9
+// 273.4, 307.1 / 621.6, 714.7 / 2634, 3086: 3/9 in the forward, 0/9 in the
+// adjoint. The moment pass needs one sine per pixel, not a sine and a
+// cosine, and its FP32 pipe also carries the moments: 0/9 (1/9 is 5 %
+// slower).
 #ifndef ASH_POLY_FWD
-#define ASH_POLY_FWD 2
+#define ASH_POLY_FWD 3
 #endif
 #ifndef ASH_POLY_ADJ
-#define ASH_POLY_ADJ 2
+#define ASH_POLY_ADJ 0
 #endif
 #ifndef ASH_POLY_GRAD
 #define ASH_POLY_GRAD 0
