@@ -182,6 +182,49 @@ bool use_tc_grad(const ash_hologram* h) {
 // read the register-image basis dz; the tensor-core kernels do not).
 bool needs_fma_image(const ash_hologram* h) { return !(use_tc_fwd(h) && use_tc_adj(h) && use_tc_grad(h)); }
 
+// CTA range starts that give every CTA the same estimated time rather than
+// the same number of units: prefix(u) is the summed cost of units [0, u)
+// (non-decreasing); begin[g] is the first unit at which it reaches g / G of
+// the total.
+template <typename F>
+std::vector<long long> balanced_begins(long long units, int G, F prefix) {
+  std::vector<long long> b((size_t)G + 1);
+  const double total = prefix(units);
+  b[0] = 0;
+  b[G] = units;
+  for (int g = 1; g < G; ++g) {
+    const double target = total * g / G;
+    long long lo = b[g - 1], hi = units;
+    while (lo < hi) {
+      const long long mid = lo + (hi - lo) / 2;
+      if (prefix(mid) >= target) hi = mid;
+      else lo = mid + 1;
+    }
+    b[g] = lo;
+  }
+  return b;
+}
+
+// Relative cost of the transforms' cheaper units. The adjoint's last spot
+// chunk of a group, with v of its 64 columns valid, costs about
+// 0.3 + 0.7 v / 64 of a full chunk (its MMA, barriers and TMEM loads are
+// paid whatever v is): weighting it so gave the c3 adjoint (N = 2000,
+// v = 16) 2800 us against 2841 with equal ranges (0.2: 2796, 0.45: 2818).
+// A chunk of the forward's replicated last spot block has a quarter or a
+// half of a full chunk's arithmetic per warp, but the CTAs that run them
+// are bound by the MMA pipeline: weighting them 0.4 / 0.55 / 0.7 made the
+// c2 forward 380 / 316 / 287 us against 267 with equal ranges, so they
+// count as full chunks.
+#ifndef ASH_FWD_REP4_COST
+#define ASH_FWD_REP4_COST 1.0
+#endif
+#ifndef ASH_FWD_REP2_COST
+#define ASH_FWD_REP2_COST 1.0
+#endif
+#ifndef ASH_ADJ_TAIL_FIXED
+#define ASH_ADJ_TAIL_FIXED 0.3
+#endif
+
 TcGradParams tc_grad_params(const ash_hologram* h, const float2* gE, float* dC) {
   TcGradParams p{};
   p.g = h->g;
@@ -638,9 +681,15 @@ ash_status create_impl(ash_hologram** out, int nx, int ny, int row0, int ny_full
     if (Ga < 1) Ga = 1;
     h->tadj.W = Wa;
     h->tadj.G = (int)Ga;
-    for (int b = 0; b <= h->tadj.G; ++b) tadj_begin.push_back(h->tadj.begin(b));
+    {
+      const int v = N - kTcChunk * (nch - 1);
+      const double tail = nch > 1 ? ASH_ADJ_TAIL_FIXED + (1.0 - ASH_ADJ_TAIL_FIXED) * v / kTcChunk : 1.0;
+      tadj_begin = balanced_begins(Wa, h->tadj.G, [&](long long u) {
+        return (double)(u / nch) * (nch - 1 + tail) + (double)(u % nch);
+      });
+    }
     for (int b = 1; b < h->tadj.G; ++b) {
-      const long long u = h->tadj.begin(b);
+      const long long u = tadj_begin[b];
       if (u % nch == 0) continue;
       const int grp = (int)(u / nch);
       if (tadj_groups.empty() || tadj_groups.back().x != grp) {
@@ -658,7 +707,14 @@ ash_status create_impl(ash_hologram** out, int nx, int ny, int row0, int ny_full
     if (Gf > f.units() / 2) Gf = f.units() / 2;
     if (Gf < 1) Gf = 1;
     f.G = (int)Gf;
-    for (int b = 0; b <= f.G; ++b) tfwd_begin.push_back(f.begin(b));
+    {
+      const int rep = tc_fwd_rep(N);
+      const double cheap = rep == 4 ? ASH_FWD_REP4_COST : rep == 2 ? ASH_FWD_REP2_COST : 1.0;
+      const long long u_rep = (long long)(f.nb - 1) * f.nq;
+      tfwd_begin = balanced_begins(f.units(), f.G, [&](long long u) {
+        return (double)(u < u_rep ? u : u_rep) + cheap * (double)(u > u_rep ? u - u_rep : 0);
+      });
+    }
     for (int b = 1; b < f.G; ++b)
       if (tfwd_begin[b] % f.nq != 0) h->tfwd_split = true;
     for (int b = 0; b < f.nb; ++b) {

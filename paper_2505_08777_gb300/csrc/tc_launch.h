@@ -129,9 +129,10 @@ __host__ __device__ inline TcPixel tc_pixel(const Geometry& G, long long qc, int
 }
 
 // Forward schedule: units (spot block b, pixel chunk q), u = b * nq + q, in
-// equal ranges per CTA. A chunk of a partial last block costs as much time
-// as a full one: its time is set by its busiest warp, and the warps share
-// their SM sub-partitions with the other resident CTAs.
+// ranges per CTA tabulated on the host (balanced_begins in api.cu). A chunk
+// of a partial last block costs as much time as a full one: its time is set
+// by the MMA pipeline and its busiest warp, and the warps share their SM
+// sub-partitions with the other resident CTAs.
 struct TcFwdSched {
   int nb, nq, G;
   __host__ __device__ long long units() const { return (long long)nb * nq; }
