@@ -208,13 +208,11 @@ __device__ __forceinline__ void sincos2_reduced(float2 x, float2& s, float2& c) 
 // least-squares fit on Chebyshev nodes, written by gen_sincos_poly.py;
 // absolute error below 5e-7 on both (that script's float32 bound; the GPU
 // test checks the device function against float64).
-__device__ __forceinline__ void sincos2_poly(float2 x, float2& s, float2& c) {
+// sin(2 pi t) and cos(2 pi t) on the FP32 pipe for two phases t in turns:
+// r = t - rint(t) is exact, u = r^2, and the polynomials below.
+__device__ __forceinline__ void sincos2_poly_turns(float2 t, float2& s, float2& c) {
   const float2 one = make_float2(1.0f, 1.0f), mone = make_float2(-1.0f, -1.0f);
   const float2 magic = make_float2(12582912.0f, 12582912.0f), nmagic = make_float2(-12582912.0f, -12582912.0f);
-  // t = x / (2 pi); unless ASH_MUFU_MODE is 0 the fp32 constant's rounding
-  // (-4e-8 of it) is made up by a second term
-  float2 t = mul2(x, make_float2(0.159154943091895336f, 0.159154943091895336f));
-  if constexpr (ASH_MUFU_MODE != 0) t = fma2(x, make_float2(6.4206382e-09f, 6.4206382e-09f), t);
   const float2 k = fma2(fma2(t, one, magic), one, nmagic);   // rint(t)
   const float2 r = fma2(k, mone, t);
   const float2 u = mul2(r, r);
@@ -228,6 +226,14 @@ __device__ __forceinline__ void sincos2_poly(float2 x, float2& s, float2& c) {
   C = fma2(C, u, make_float2(kCosPoly[0], kCosPoly[0]));
   s = mul2(mul2(r, S), C);
   c = fma2(C, C, mone);
+}
+
+__device__ __forceinline__ void sincos2_poly(float2 x, float2& s, float2& c) {
+  // t = x / (2 pi); unless ASH_MUFU_MODE is 0 the fp32 constant's rounding
+  // (-4e-8 of it) is made up by a second term
+  float2 t = mul2(x, make_float2(0.159154943091895336f, 0.159154943091895336f));
+  if constexpr (ASH_MUFU_MODE != 0) t = fma2(x, make_float2(6.4206382e-09f, 6.4206382e-09f), t);
+  sincos2_poly_turns(t, s, c);
 }
 
 // Which pixel pairs of an unrolled loop take the FP32-pipe sincos: NUM of
@@ -271,6 +277,45 @@ __device__ __forceinline__ void sincos2_mixed(int k, float2 x, float2& s, float2
     sincos2_poly(x, s, c);
   } else {
     sincos2_reduced(x, s, c);
+  }
+}
+
+// The same for phases in turns (the tensor-core transforms: their operand
+// rows carry C / 2 pi and their nearfield images phases / 2 pi, so the
+// reduction r = t - rint(t) is exact and costs two packed instructions plus
+// the subtraction; the MUFU then gets 2 pi r, |2 pi r| <= pi).
+__device__ __forceinline__ float2 mufu_arg2_turns(float2 t) {
+  const float2 tp = make_float2(6.283185307179586f, 6.283185307179586f);
+  if constexpr (ASH_MUFU_MODE == 1) {
+    const float2 one = make_float2(1.0f, 1.0f), mone = make_float2(-1.0f, -1.0f);
+    const float2 magic = make_float2(12582912.0f, 12582912.0f), nmagic = make_float2(-12582912.0f, -12582912.0f);
+    const float2 k = fma2(fma2(t, one, magic), one, nmagic);
+    return mul2(fma2(k, mone, t), tp);
+  } else if constexpr (ASH_MUFU_MODE == 2) {
+    return mufu_arg2(mul2(t, tp));
+  } else {
+    return mul2(t, tp);
+  }
+}
+
+template <int NUM>
+__device__ __forceinline__ void sin2_turns_mixed(int k, float2 t, float2& s) {
+  if (NUM > 0 && (k * NUM) % 9 < NUM) {
+    float2 c;
+    sincos2_poly_turns(t, s, c);   // the cosine's last step is dead code here
+  } else {
+    const float2 r = mufu_arg2_turns(t);
+    s.x = __sinf(r.x);
+    s.y = __sinf(r.y);
+  }
+}
+
+template <int NUM>
+__device__ __forceinline__ void sincos2_turns_mixed(int k, float2 t, float2& s, float2& c) {
+  if (NUM > 0 && (k * NUM) % 9 < NUM) {
+    sincos2_poly_turns(t, s, c);
+  } else {
+    sincos2(mufu_arg2_turns(t), s, c);
   }
 }
 

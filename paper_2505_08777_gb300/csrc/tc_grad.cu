@@ -65,8 +65,9 @@ struct TcGradShape {
 // + x (x the local phase from the tensor core) and w = conj(gE_n exp(+i 2 pi
 // base)) = |w| exp(i alpha), constant over a tile, each term adds q Z_dm
 // with q = Im(w f_m exp(-i x)) = |w| A_m sin(phi_m + alpha - x) (the
-// nearfield image holds f = A exp(i phi) as (A, phi)); |w| is applied once
-// per tile. Over a tile Z_dm = sum_{k + l <= ORD} b_dkl u^k v^l (u, v the
+// nearfield image holds f = A exp(i phi) as (A, phi / 2 pi), the tensor
+// core gives x / 2 pi, and the sine is taken of the sum in turns); |w| is
+// applied once per tile. Over a tile Z_dm = sum_{k + l <= ORD} b_dkl u^k v^l (u, v the
 // pixel's column and row offsets), so thread t (spot t of the block)
 // accumulates along each row the power moments P_k = sum q u^k (u^k
 // compile-time constants here), folds them into the tile moments
@@ -189,7 +190,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_tc_gradc(const TcGradParams p
       const float2 rt = n < N ? __ldg(p.rot + (size_t)(q / kTcChunksPerTile) * N + n) : make_float2(0.0f, 0.0f);
       // w = |w| exp(i alpha): q = Im(w f exp(-i x)) = |w| Im(f exp(-i (x - alpha)))
       const float wr = gh.x * rt.x - gh.y * rt.y, wi = -(gh.x * rt.y + gh.y * rt.x);
-      const float alpha = atan2f(wi, wr);
+      const float alpha = atan2f(wi, wr) * 0.15915494309189535f;   // turns, as phi and x
       alpha2 = make_float2(alpha, alpha);
       wmag = sqrtf(wr * wr + wi * wi);
     }
@@ -212,8 +213,8 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_tc_gradc(const TcGradParams p
             make_float2(__uint_as_float(x[k / 8][2 * (k % 8)]), __uint_as_float(x[k / 8][2 * (k % 8) + 1]));
         // q / |w| = Im(A exp(i phi) exp(-i (x - alpha))) = A sin(phi + alpha - x)
         float2 sn;
-        sin2_mixed<ASH_POLY_GRAD>(16 * hr + k, fma2(xv, make_float2(-1.0f, -1.0f), fma2(ph, make_float2(1.0f, 1.0f), alpha2)),
-                                  sn);
+        sin2_turns_mixed<ASH_POLY_GRAD>(
+            16 * hr + k, fma2(xv, make_float2(-1.0f, -1.0f), fma2(ph, make_float2(1.0f, 1.0f), alpha2)), sn);
         const float2 qv = mul2(am, sn);
         // columns 2k, 2k + 1 of the row
         const float u0 = (2.0f * k - 15.5f) * 0.0625f, u1 = (2.0f * k + 1.0f - 15.5f) * 0.0625f;

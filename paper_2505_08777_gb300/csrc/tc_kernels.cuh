@@ -100,9 +100,11 @@ static __global__ void k_tc_build_zs(const Geometry G, const TcLayout L, const f
     }
 }
 
-// czs from the coefficients: one thread per (spot chunk, row); rows >= N are
-// 0. The two chunks after the nc64 main ones hold the last 128-spot block
-// with its first 128 / rep spots repeated rep times.
+// czs from the coefficients, in turns (C / 2 pi, so that the MMA gives the
+// local phase in turns): one thread per (spot chunk, row); rows >= N are 0.
+// The two chunks after the nc64 main ones hold the last 128-spot block with
+// its first 128 / rep spots repeated rep times.
+constexpr double kInv2PiD = 0.15915494309189533576888376337251;
 static __global__ void k_tc_build_czs(const float* __restrict__ coeff, int N, const TcLayout L, int nc64, int rep,
                                       float* __restrict__ czs) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -118,12 +120,13 @@ static __global__ void k_tc_build_czs(const float* __restrict__ coeff, int N, co
       float v = 0.0f;
       if (kind >= 0 && n < N) {
         if (kind < 3) {
-          const float c = coeff[(size_t)n * D + mode];
-          const float hi = to_tf32(c);
-          v = kind == 2 ? to_tf32(c - hi) : hi;   // [hi | hi | lo]
+          // in turns: the products give the local phase / 2 pi
+          const double c = (double)coeff[(size_t)n * D + mode] * kInv2PiD;
+          const float hi = to_tf32((float)c);
+          v = kind == 2 ? to_tf32((float)(c - (double)hi)) : hi;   // [hi | hi | lo]
         } else {
-          // rad per pixel, split into L.tp tf32 pieces (piece `mode`)
-          const double cr = (double)coeff[(size_t)n * D + (kind == 3 ? L.tx : L.ty)] / (double)L.R;
+          // turns per pixel, split into L.tp tf32 pieces (piece `mode`)
+          const double cr = (double)coeff[(size_t)n * D + (kind == 3 ? L.tx : L.ty)] / (double)L.R * kInv2PiD;
           double rest = cr;
           for (int q = 0; q <= mode; ++q) {
             const float piece = to_tf32((float)rest);
@@ -136,16 +139,17 @@ static __global__ void k_tc_build_czs(const float* __restrict__ coeff, int N, co
     }
 }
 
-// A phase reduced to [-pi, pi] (the nearfield image's phases stay small,
-// so that phi - x keeps the accuracy of x).
-__device__ __forceinline__ float wrap_phase(float ph) {
-  return fmaf(-6.283185307179586f, rintf(ph * 0.15915494309189535f), ph);
+// A phase in turns, reduced to [-1/2, 1/2] (the nearfield image's phases
+// stay small, so that phi - x keeps the accuracy of x).
+__device__ __forceinline__ float turns_of_phase(float ph) {
+  const float t = ph * 0.15915494309189535f;
+  return t - rintf(t);
 }
 
-// Nearfield in tc layout, as amplitude and phase: f = A exp(i phi) from a
-// phase or from a complex field (A = |f|, phi = arg f), both in user layout;
-// pixels outside the grid are 0. Chunk pixel pair p holds (A_2p, A_2p+1,
-// phi_2p, phi_2p+1).
+// Nearfield in tc layout, as amplitude and phase in turns: f = A exp(i 2 pi
+// phi) from a phase or from a complex field (A = |f|, phi = arg f / 2 pi),
+// both in user layout; pixels outside the grid are 0. Chunk pixel pair p
+// holds (A_2p, A_2p+1, phi_2p, phi_2p+1).
 static __global__ void k_tc_field_img(const Geometry G, const float* __restrict__ amp_img,
                                       const float* __restrict__ phase, const float2* __restrict__ field,
                                       float* __restrict__ fimg) {
@@ -159,11 +163,11 @@ static __global__ void k_tc_field_img(const Geometry G, const float* __restrict_
     const size_t m = (size_t)px.j * G.nx + px.i;
     if (phase) {
       a = amp_img[px.img];
-      ph = wrap_phase(phase[m]);
+      ph = turns_of_phase(phase[m]);
     } else {
       const float2 f = field[m];
       a = hypotf(f.x, f.y);
-      ph = (f.x == 0.0f && f.y == 0.0f) ? 0.0f : atan2f(f.y, f.x);
+      ph = (f.x == 0.0f && f.y == 0.0f) ? 0.0f : atan2f(f.y, f.x) * 0.15915494309189535f;
     }
   }
   float* q = fimg + ((size_t)qc * 32 + (r >> 1)) * 4;
@@ -287,7 +291,7 @@ __device__ __forceinline__ void tc_range_end(uint64_t* bars, const uint32_t* arm
 }
 
 // Adjoint output of row r of chunk qc (in the pixel's user-layout slot and,
-// for kEpiFimg, in the tc-layout nearfield f = A exp(i arg g) as (A, arg g)).
+// for kEpiFimg, in the tc-layout nearfield f = A exp(i arg g) as (A, arg g / 2 pi)).
 __device__ __forceinline__ void tc_adjoint_epilogue(const TcAdjParams& p, long long qc, int r, float gr, float gi) {
   const Geometry& G = p.g;
   const TcPixel px = tc_pixel(G, qc, r);
@@ -296,7 +300,7 @@ __device__ __forceinline__ void tc_adjoint_epilogue(const TcAdjParams& p, long l
   const float a = need_a ? __ldg(p.amp_img + px.img) : 0.0f;
   adjoint_epilogue(p.out, (size_t)px.j * G.nx + px.i, gr, gi, a);
   if (p.out.epilogue & kEpiFimg) {
-    const float ph = (gr == 0.0f && gi == 0.0f) ? 0.0f : atan2f(gi, gr);
+    const float ph = (gr == 0.0f && gi == 0.0f) ? 0.0f : atan2f(gi, gr) * 0.15915494309189535f;
     float* q = reinterpret_cast<float*>(p.fimg + (size_t)qc * 32 + (r >> 1));
     q[r & 1] = a;
     q[2 + (r & 1)] = ph;
@@ -450,8 +454,9 @@ __device__ __forceinline__ void tc_adjoint_range(const TcAdjParams& p, long long
           const float4 yq = yw[8 * q + pp];
           const float2 yr = make_float2(yq.x, yq.y), yi = make_float2(yq.z, yq.w);
           float2 sn, cs;
-          sincos2_mixed<ASH_POLY_ADJ>(8 * q + pp, make_float2(__uint_as_float(x[q][2 * pp]), __uint_as_float(x[q][2 * pp + 1])),
-                        sn, cs);
+          // the local phase in turns
+          sincos2_turns_mixed<ASH_POLY_ADJ>(
+              8 * q + pp, make_float2(__uint_as_float(x[q][2 * pp]), __uint_as_float(x[q][2 * pp + 1])), sn, cs);
           // y exp(+i x) = (yr cs - yi sn) + i (yi cs + yr sn)
           B1 = fma2(yr, cs, B1);
           B2 = fma2(yi, sn, B2);
@@ -706,8 +711,8 @@ __device__ __forceinline__ void tc_forward_range(const TcFwdParams& p, long long
             const float2 am = make_float2(fq.x, fq.y), ph = make_float2(fq.z, fq.w);
             const float2 xv = make_float2(__uint_as_float(x[qq][2 * pp]), __uint_as_float(x[qq][2 * pp + 1]));
             float2 sn, cs;
-            // f exp(-i x) = A exp(i (phi - x))
-            sincos2_mixed<ASH_POLY_FWD>(8 * qq + pp, fma2(xv, make_float2(-1.0f, -1.0f), ph), sn, cs);
+            // f exp(-i x) = A exp(i 2 pi (phi - x)), phi and x in turns
+            sincos2_turns_mixed<ASH_POLY_FWD>(8 * qq + pp, fma2(xv, make_float2(-1.0f, -1.0f), ph), sn, cs);
             A1 = fma2(am, cs, A1);
             A2 = fma2(am, sn, A2);
           }
@@ -871,7 +876,7 @@ static __global__ void k_tc_field_img_batch(const TcFieldDesc* __restrict__ ds, 
   float a = 0.0f, ph = 0.0f;
   if (px.i < G.nx && px.j < G.ny) {
     a = d.amp_img[px.img];
-    ph = wrap_phase(d.phase[(size_t)px.j * G.nx + px.i]);
+    ph = turns_of_phase(d.phase[(size_t)px.j * G.nx + px.i]);
   }
   float* q = reinterpret_cast<float*>(d.fimg) + ((size_t)qc * 32 + (r >> 1)) * 4;
   q[r & 1] = a;

@@ -93,8 +93,8 @@ __host__ __device__ inline void tc_slot(const TcLayout& L, int col, int& kind, i
 //  czs : spot rows, chunk j = spots 64 j .. 64 j + 63 (an even number of
 //        chunks, rows >= N zero, so a 128-spot block is two chunks), then
 //        two chunks holding the last block's spots replicated (tc_fwd_rep);
-//  fimg: the nearfield f_m of each pixel chunk as 32 float4 (fr, fr', fi, fi')
-//        of pixel pairs (2p, 2p + 1).
+//  fimg: the nearfield f_m of each pixel chunk as 32 float4 (A, A', phi, phi')
+//        of pixel pairs (2p, 2p + 1), phases in turns (phi = arg f / 2 pi).
 inline size_t tc_zs_floats(const Geometry& g, int NA) { return (size_t)g.T * kTcChunksPerTile * NA * 2048; }
 inline int tc_spot_chunks(int N) { return 2 * ((N + kTcRows - 1) / kTcRows); }
 inline size_t tc_czs_floats(int N, int NA) { return (size_t)(tc_spot_chunks(N) + 2) * NA * 2048; }
