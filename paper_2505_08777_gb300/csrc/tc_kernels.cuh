@@ -125,7 +125,7 @@ static __global__ void k_tc_build_czs(const float* __restrict__ coeff, int N, co
           const float hi = to_tf32((float)c);
           v = kind == 2 ? to_tf32((float)(c - (double)hi)) : hi;   // [hi | hi | lo]
         } else {
-          // turns per pixel, split into L.tp tf32 pieces (piece `mode`)
+          // turns per pixel, split into tf32 pieces (piece `mode`)
           const double cr = (double)coeff[(size_t)n * D + (kind == 3 ? L.tx : L.ty)] / (double)L.R * kInv2PiD;
           double rest = cr;
           for (int q = 0; q <= mode; ++q) {

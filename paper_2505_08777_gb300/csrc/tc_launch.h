@@ -36,23 +36,23 @@ struct TcLayout {
   int NA;        // K-atoms of 32 tf32 per row
   int tx, ty;    // positions of the x / y tilt among the D modes (tilt-exact), else -1
   float R;       // min(nx, ny_full) / 2 (grid_radius)
-  int tp;        // tf32 pieces of each tilt's c / R (tilt-exact: 2 or 3)
+  int tpx, tpy;  // tf32 pieces of the x / y tilt's c / R (tilt-exact: 2 or 3)
 };
 __host__ __device__ constexpr int tc_na(int D) { return 3 * D <= 32 ? 1 : 2; }
 inline TcLayout tc_layout(int D, const int* noll, const Geometry& g) {
-  TcLayout L{D, tc_na(D), -1, -1, (float)grid_radius(g), 0};
+  TcLayout L{D, tc_na(D), -1, -1, (float)grid_radius(g), 0, 0};
   if (noll && D >= 2) {
     int tx = -1, ty = -1;
     for (int d = 0; d < D; ++d) {
       if (noll[d] == 2) tx = d;
       if (noll[d] == 3) ty = d;
     }
-    if (tx >= 0 && ty >= 0) {
-      if (3 * (D - 2) + 6 <= 32) {
-        L = TcLayout{D, 1, tx, ty, L.R, 3};
-      } else if (3 * (D - 2) + 4 <= 32) {
-        L = TcLayout{D, 1, tx, ty, L.R, 2};
-      }
+    // as many pieces as one K-atom holds: three each, else three for x
+    // and two for y, else two each
+    const int room = 32 - 3 * (D - 2);
+    if (tx >= 0 && ty >= 0 && room >= 4) {
+      const int tpx = room >= 5 ? 3 : 2, tpy = room >= 6 ? 3 : 2;
+      L = TcLayout{D, 1, tx, ty, L.R, tpx, tpy};
     }
   }
   return L;
@@ -80,10 +80,10 @@ __host__ __device__ inline void tc_slot(const TcLayout& L, int col, int& kind, i
         break;
       }
     }
-  } else if (col < 3 * Dp + 2 * L.tp) {
+  } else if (col < 3 * Dp + L.tpx + L.tpy) {
     const int c = col - 3 * Dp;
-    kind = c < L.tp ? 3 : 4;
-    mode = c % L.tp;
+    kind = c < L.tpx ? 3 : 4;
+    mode = c < L.tpx ? c : c - L.tpx;
   }
 }
 
