@@ -53,7 +53,7 @@ __global__ void k_tc_tile_poly(const Geometry G, const MonoTerm* __restrict__ te
 
 // Shared memory of the moment kernel: A (spot block), B ring and f ring.
 struct TcGradShape {
-  static constexpr int NBB = 4, NF = 4;
+  static constexpr int NBB = 4, KF = 3, NF = KF + 3;
   static constexpr uint32_t A_BYTES = 16384, B_BYTES = 8192, F_BYTES = 512;
   static constexpr uint32_t FSLOT = F_BYTES;
   static constexpr int NBARS = 3 + NBB + NF;
@@ -77,7 +77,7 @@ template <int ORD, int DP>
 __global__ void __launch_bounds__(kTcThreads, 4) k_tc_gradc(const TcGradParams p) {
   using S = TcGradShape;
   constexpr int NPOW = ORD + 1, NPAIR = (ORD + 1) * (ORD + 2) / 2;
-  constexpr int NA = 1, NBB = S::NBB, NF = S::NF, NBARS = S::NBARS;
+  constexpr int NA = 1, NBB = S::NBB, KF = S::KF, NF = S::NF, NBARS = S::NBARS;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = tc_smem_base(smem_raw);
   float* sA = reinterpret_cast<float*>(base);
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_tc_gradc(const TcGradParams p
 
   int qb = q0, qf = q0;
   for (int k = 0; k < NBB; ++k) qb = next_q(qb);
-  for (int k = 0; k < NF - 1; ++k) qf = next_q(qf);
+  for (int k = 0; k < KF; ++k) qf = next_q(qf);
   if (t == 0 && nc > 0) {
     pst[0] = 0;
     pst[1] = b0;
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_tc_gradc(const TcGradParams p
     pst[4] = 1;
     load_a(b0);
     for (int c = 0, q = q0; c < NBB && c < nc; ++c, q = next_q(q)) load_b(c, q);
-    for (int c = 0, q = q0; c < NF - 1 && c < nc; ++c, q = next_q(q)) load_f(c, q);
+    for (int c = 0, q = q0; c < KF && c < nc; ++c, q = next_q(q)) load_f(c, q);
     ok = issue_upto(1, -1);
   }
 
@@ -258,13 +258,18 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_tc_gradc(const TcGradParams p
     tmem_wait();
     tc_fence_before();
     __syncwarp();
-    if (lane == 0 && (atom_add_acq_rel_smem(&cnt[c & 1], 1u) & 3u) == 3u) {
-      // every warp is done with TMEM buffer c & 1 and with the ring slot of
-      // chunk c - 1; MMA(c) has completed
-      tc_fence_after();
-      if (c + NBB < nc) load_b(c + NBB, qb);
-      if (c + NF - 1 < nc) load_f(c + NF - 1, qf);
-      ok = issue_upto(c + 2, c) && ok;
+    if (lane == 0) {
+      // the forward's producer schedule: the last warp to release chunk c
+      // issues the MMAs up to c + 2, the first loads B of c + NBB and f of
+      // c + KF (into chunk c - 3's slot)
+      const uint32_t order = atom_add_acq_rel_smem(&cnt[c & 1], 1u) & 3u;
+      if (order == 3u) {
+        tc_fence_after();
+        ok = issue_upto(c + 2, c) && ok;
+      } else if (order == 0u) {
+        if (c + NBB < nc) load_b(c + NBB, qb);
+        if (c + KF < nc) load_f(c + KF, qf);
+      }
     }
     __syncwarp();
     qb = next_q(qb);

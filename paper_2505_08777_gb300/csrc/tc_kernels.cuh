@@ -59,7 +59,7 @@ struct TcAdjShape {
 // arithmetic is short (a partial last spot block).
 template <int NA>
 struct TcFwdShape {
-  static constexpr int NBB = NA == 1 ? 4 : 3, NF = 4;
+  static constexpr int NBB = NA == 1 ? 4 : 3, KF = 3, NF = KF + 3;
   static constexpr uint32_t A_BYTES = NA * 16384, B_BYTES = NA * 8192, F_BYTES = 512;
   static constexpr int NBARS = 3 + NBB + NF;
   // [alignment slack][A][B ring][f ring][barriers][armed counts][counter][TMEM slot][producer state]
@@ -313,12 +313,15 @@ __device__ __forceinline__ void tc_adjoint_epilogue(const TcAdjParams& p, long l
 // spot chunk) range; groups whose spots are split between CTAs go through
 // `split` and k_tc_adjoint_fixup.
 //
-// Producer schedule (run by the warp that releases a chunk last): at the
-// release of chunk c, B of chunk c + NB goes into the slot MMA(c) has freed,
-// A of group s + 2 into the slot of group s once c is s's last chunk, and
-// the MMA of chunk c + 1 is issued into the other TMEM buffer; it completes
-// while the warps work through chunk c. (Two chunks of lookahead were
-// measured slower here: the deeper B ring it needs costs a CTA per SM.)
+// Producer schedule: the warp releasing chunk c last issues the MMA of
+// chunk c + 2 into the TMEM buffer just released (it completes while the
+// warps work through chunks c and c + 1); the warp releasing it first loads
+// B of chunk c + NB into the slot MMA(c) has freed, and A of group s + 2
+// into the slot of group s once c is s's last chunk. The first release of
+// a chunk comes well before its last (the warps drift apart by up to about
+// two chunks), so chunk c + 2's B is in place when its MMA is issued with a
+// two-slot B ring. (Measured at 1024^2, N = 400: 274 us against 280 with
+// the MMA one chunk ahead.)
 template <int NA>
 __device__ __forceinline__ void tc_adjoint_range(const TcAdjParams& p, long long u0, long long u1, int cta,
                                                  uint8_t* base, uint32_t tmem, bool first_range) {
@@ -396,7 +399,7 @@ __device__ __forceinline__ void tc_adjoint_range(const TcAdjParams& p, long long
     load_a(s0);
     if (s0 + 1 <= s_last) load_a(s0 + 1);
     for (int c = 0, j = j0; c < NB && c < nc; ++c, j = (j + 1 == nch ? 0 : j + 1)) load_b(c, j);
-    ok = issue_upto(0);
+    ok = issue_upto(1);
   }
 
   float4* yw = sY + w * 32;   // this warp's (yr, yr', yi, yi') of 32 spot pairs
@@ -432,12 +435,18 @@ __device__ __forceinline__ void tc_adjoint_range(const TcAdjParams& p, long long
     tc_load_cols(tmem + tlane + (uint32_t)((c & 1) * kTcChunk), 0, nq, x);
     tc_fence_before();
     __syncwarp();
-    if (lane == 0 && (atom_add_acq_rel_smem(&cnt[c & 1], 1u) & 3u) == 3u) {
-      // every warp is done with TMEM buffer c & 1; MMA(c) has completed
-      tc_fence_after();
-      if (c + NB < nc) load_b(c + NB, jb);
-      if (last_of_group && s + 2 <= s_last) load_a(s + 2);   // every MMA of group s is complete
-      ok = issue_upto(c + 1) && ok;
+    if (lane == 0) {
+      const uint32_t order = atom_add_acq_rel_smem(&cnt[c & 1], 1u) & 3u;
+      if (order == 3u) {
+        // every warp is done with TMEM buffer c & 1
+        tc_fence_after();
+        ok = issue_upto(c + 2) && ok;
+      } else if (order == 0u) {
+        // MMA(c) has completed (this warp saw it), and with it every MMA
+        // of group s once c is the group's last chunk
+        if (c + NB < nc) load_b(c + NB, jb);
+        if (last_of_group && s + 2 <= s_last) load_a(s + 2);
+      }
     }
     __syncwarp();
     if (++jb == nch) jb = 0;
@@ -553,16 +562,20 @@ static __global__ void k_tc_adjoint_fixup_batch(const TcAdjParams* __restrict__ 
 // range; blocks whose pixels are split between CTAs go through `part` and
 // k_tc_forward_reduce.
 //
-// Producer schedule (the warp releasing chunk c last): B of chunk c + NBB
-// into the slot MMA(c) has freed, f of chunk c + NF - 1 into the slot of
-// chunk c - 1 (every warp has finished reading it), and the MMAs up to chunk
-// c + 2. A spot block's first MMA waits until the previous block's last MMA
-// has completed, then its A is reloaded (once per block change).
+// Producer schedule. The warp releasing chunk c last issues the MMAs up to
+// chunk c + 2 (nothing else: the MMA is what the other warps wait for); the
+// warp releasing it first loads B of chunk c + NBB into the slot MMA(c) has
+// freed and f of chunk c + KF into the slot of chunk c + KF - NF = c - 3.
+// No warp runs more than two chunks ahead of another (chunk c + 2's MMA
+// needs every warp's release of c), so every warp has finished reading
+// chunk c - 3's f. A spot block's first MMA waits until the previous
+// block's last MMA has completed, then its A is reloaded (once per block
+// change).
 template <int NA>
 __device__ __forceinline__ void tc_forward_range(const TcFwdParams& p, long long u0, long long u1, int cta,
                                                  uint8_t* base, uint32_t tmem, bool first_range) {
   using S = TcFwdShape<NA>;
-  constexpr int NBB = S::NBB, NF = S::NF, NBARS = S::NBARS;
+  constexpr int NBB = S::NBB, KF = S::KF, NF = S::NF, NBARS = S::NBARS;
   float* sA = reinterpret_cast<float*>(base);                      // [NA][128][32]
   float* sB = sA + NA * 4096;                                      // [NBB][NA][64][32]
   float4* sF = reinterpret_cast<float4*>(sB + NBB * NA * 2048);    // [NF][32]
@@ -646,9 +659,9 @@ __device__ __forceinline__ void tc_forward_range(const TcFwdParams& p, long long
     return r;
   };
 
-  int qb = q0, qf = q0;              // pixel chunks of chunks c + NBB and c + NF - 1 (the next to load)
+  int qb = q0, qf = q0;              // pixel chunks of chunks c + NBB and c + KF (the next to load)
   for (int k = 0; k < NBB; ++k) qb = next_q(qb);
-  for (int k = 0; k < NF - 1; ++k) qf = next_q(qf);
+  for (int k = 0; k < KF; ++k) qf = next_q(qf);
   if (t == 0 && nc > 0) {
     pst[0] = 0;
     pst[1] = b0;
@@ -657,7 +670,7 @@ __device__ __forceinline__ void tc_forward_range(const TcFwdParams& p, long long
     pst[4] = 1;
     load_a(b0);
     for (int c = 0, q = q0; c < NBB && c < nc; ++c, q = next_q(q)) load_b(c, q);
-    for (int c = 0, q = q0; c < NF - 1 && c < nc; ++c, q = next_q(q)) load_f(c, q);
+    for (int c = 0, q = q0; c < KF && c < nc; ++c, q = next_q(q)) load_f(c, q);
     ok = issue_upto(1, -1);
   }
 
@@ -684,15 +697,21 @@ __device__ __forceinline__ void tc_forward_range(const TcFwdParams& p, long long
       tc_load_cols(tmem + tlane + (uint32_t)((c & 1) * kTcChunk), REPL ? g_lo : 0, REPL ? g_hi : 4, x);
       tc_fence_before();
       __syncwarp();
-      // a warp can be one chunk ahead of another (MMAs run two chunks
-      // ahead), so arrivals are counted per TMEM buffer
-      if (lane == 0 && (atom_add_acq_rel_smem(&cnt[c & 1], 1u) & 3u) == 3u) {
-        // every warp is done with TMEM buffer c & 1 and with the f slot of
-        // chunk c - 1; MMA(c) has completed
-        tc_fence_after();
-        if (c + NBB < nc) load_b(c + NBB, qb);
-        if (c + NF - 1 < nc) load_f(c + NF - 1, qf);
-        ok = issue_upto(c + 2, c) && ok;
+      // a warp can be up to two chunks ahead of another (MMAs run two
+      // chunks ahead), so arrivals are counted per TMEM buffer; the count
+      // also tells the first and the last
+      if (lane == 0) {
+        const uint32_t order = atom_add_acq_rel_smem(&cnt[c & 1], 1u) & 3u;
+        if (order == 3u) {
+          // every warp is done with TMEM buffer c & 1
+          tc_fence_after();
+          ok = issue_upto(c + 2, c) && ok;
+        } else if (order == 0u) {
+          // MMA(c) has completed (this warp saw it) and every warp is done
+          // with chunk c - 3
+          if (c + NBB < nc) load_b(c + NBB, qb);
+          if (c + KF < nc) load_f(c + KF, qf);
+        }
       }
       __syncwarp();
       qb = next_q(qb);
