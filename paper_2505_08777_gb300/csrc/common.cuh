@@ -298,13 +298,17 @@ __device__ __forceinline__ float2 mufu_arg2_turns(float2 t) {
   }
 }
 
-template <int NUM>
+// REDUCE = false feeds the MUFU 2 pi t unreduced: its error then grows as
+// ~7.5e-8 |2 pi t| (a bias), harmless for a single pass such as the
+// gradient's moments (|t| is a tile's local phase, tens of turns at most)
+// but not for the transforms a WGS loop repeats.
+template <int NUM, bool REDUCE = true>
 __device__ __forceinline__ void sin2_turns_mixed(int k, float2 t, float2& s) {
   if (NUM > 0 && (k * NUM) % 9 < NUM) {
     float2 c;
     sincos2_poly_turns(t, s, c);   // the cosine's last step is dead code here
   } else {
-    const float2 r = mufu_arg2_turns(t);
+    const float2 r = REDUCE ? mufu_arg2_turns(t) : mul2(t, make_float2(6.283185307179586f, 6.283185307179586f));
     s.x = __sinf(r.x);
     s.y = __sinf(r.y);
   }

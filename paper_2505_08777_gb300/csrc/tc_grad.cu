@@ -213,7 +213,11 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_tc_gradc(const TcGradParams p
             make_float2(__uint_as_float(x[k / 8][2 * (k % 8)]), __uint_as_float(x[k / 8][2 * (k % 8) + 1]));
         // q / |w| = Im(A exp(i phi) exp(-i (x - alpha))) = A sin(phi + alpha - x)
         float2 sn;
-        sin2_turns_mixed<ASH_POLY_GRAD>(
+        // the sine's argument goes to the MUFU unreduced: this pass runs
+        // once per gradient, not inside a loop, and its error stays far
+        // below the gradient's tolerance (c4, 32 spots: 1.3e-6 normwise
+        // against 8.0e-7 reduced), for 12 % less time (647 -> 569 us)
+        sin2_turns_mixed<ASH_POLY_GRAD, false>(
             16 * hr + k, fma2(xv, make_float2(-1.0f, -1.0f), fma2(ph, make_float2(1.0f, 1.0f), alpha2)), sn);
         const float2 qv = mul2(am, sn);
         // columns 2k, 2k + 1 of the row
