@@ -314,12 +314,12 @@ __device__ __forceinline__ void sin2_turns_mixed(int k, float2 t, float2& s) {
   }
 }
 
-template <int NUM>
+template <int NUM, bool REDUCE = true>
 __device__ __forceinline__ void sincos2_turns_mixed(int k, float2 t, float2& s, float2& c) {
   if (NUM > 0 && (k * NUM) % 9 < NUM) {
     sincos2_poly_turns(t, s, c);
   } else {
-    sincos2(mufu_arg2_turns(t), s, c);
+    sincos2(REDUCE ? mufu_arg2_turns(t) : mul2(t, make_float2(6.283185307179586f, 6.283185307179586f)), s, c);
   }
 }
 

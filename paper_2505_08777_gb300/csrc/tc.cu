@@ -41,17 +41,24 @@ cudaError_t prepare_na(int* adj, int* fwd) {
                                   (int)cudaSharedmemCarveoutMaxShared)))
       return e;
   }
-  if ((e = cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcAdjShape<NA>::SMEM)))
-    return e;
-  if ((e = cudaFuncSetAttribute(ka, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                (int)cudaSharedmemCarveoutMaxShared)))
-    return e;
+  for (const void* k : {ka, (const void*)k_tc_adjoint<NA, false>}) {
+    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcAdjShape<NA>::SMEM)))
+      return e;
+    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  (int)cudaSharedmemCarveoutMaxShared)))
+      return e;
+  }
   if ((e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcFwdShape<NA>::SMEM)))
     return e;
   if ((e = cudaFuncSetAttribute(kf, cudaFuncAttributePreferredSharedMemoryCarveout,
                                 (int)cudaSharedmemCarveoutMaxShared)))
     return e;
   if ((e = tc_ctas_per_sm(ka, TcAdjShape<NA>::SMEM, 2 * kTcChunk, adj))) return e;
+  // the gradient's instantiation must fit the same grid
+  int adj_grad = 0;
+  if ((e = tc_ctas_per_sm((const void*)k_tc_adjoint<NA, false>, TcAdjShape<NA>::SMEM, 2 * kTcChunk, &adj_grad)))
+    return e;
+  if (adj_grad < *adj) *adj = adj_grad;
   return tc_ctas_per_sm(kf, TcFwdShape<NA>::SMEM, 2 * kTcChunk, fwd);
 }
 
@@ -79,8 +86,11 @@ cudaError_t tc_batch_ctas_per_sm(int NA, int* adj, int* fwd) {
 }
 
 cudaError_t tc_launch_adjoint(int NA, const TcAdjParams& p, int grid, cudaStream_t s) {
-  if (NA == 1) k_tc_adjoint<1><<<grid, kTcThreads, TcAdjShape<1>::SMEM, s>>>(p);
-  else if (NA == 2) k_tc_adjoint<2><<<grid, kTcThreads, TcAdjShape<2>::SMEM, s>>>(p);
+  const bool grad = (p.out.epilogue & kEpiGradPhase) != 0;   // a gradient's single pass: MUFU unreduced
+  if (NA == 1 && !grad) k_tc_adjoint<1><<<grid, kTcThreads, TcAdjShape<1>::SMEM, s>>>(p);
+  else if (NA == 1) k_tc_adjoint<1, false><<<grid, kTcThreads, TcAdjShape<1>::SMEM, s>>>(p);
+  else if (NA == 2 && !grad) k_tc_adjoint<2><<<grid, kTcThreads, TcAdjShape<2>::SMEM, s>>>(p);
+  else if (NA == 2) k_tc_adjoint<2, false><<<grid, kTcThreads, TcAdjShape<2>::SMEM, s>>>(p);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }

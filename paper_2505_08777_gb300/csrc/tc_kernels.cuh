@@ -322,7 +322,7 @@ __device__ __forceinline__ void tc_adjoint_epilogue(const TcAdjParams& p, long l
 // two chunks), so chunk c + 2's B is in place when its MMA is issued with a
 // two-slot B ring. (Measured at 1024^2, N = 400: 274 us against 280 with
 // the MMA one chunk ahead.)
-template <int NA>
+template <int NA, bool REDUCE = true>
 __device__ __forceinline__ void tc_adjoint_range(const TcAdjParams& p, long long u0, long long u1, int cta,
                                                  uint8_t* base, uint32_t tmem, bool first_range) {
   using S = TcAdjShape<NA>;
@@ -464,7 +464,7 @@ __device__ __forceinline__ void tc_adjoint_range(const TcAdjParams& p, long long
           const float2 yr = make_float2(yq.x, yq.y), yi = make_float2(yq.z, yq.w);
           float2 sn, cs;
           // the local phase in turns
-          sincos2_turns_mixed<ASH_POLY_ADJ>(
+          sincos2_turns_mixed<ASH_POLY_ADJ, REDUCE>(
               8 * q + pp, make_float2(__uint_as_float(x[q][2 * pp]), __uint_as_float(x[q][2 * pp + 1])), sn, cs);
           // y exp(+i x) = (yr cs - yi sn) + i (yi cs + yr sn)
           B1 = fma2(yr, cs, B1);
@@ -491,13 +491,16 @@ __device__ __forceinline__ void tc_adjoint_range(const TcAdjParams& p, long long
   if (!ok && t == 0) atomicOr(p.err, kErrTimeout);
 }
 
-template <int NA>
+// REDUCE = false: the dL/dphi pass of a gradient (epilogue kEpiGradPhase),
+// run once per gradient rather than inside a loop, feeds the MUFU the local
+// phase unreduced (see sin2_turns_mixed).
+template <int NA, bool REDUCE = true>
 __global__ void __launch_bounds__(kTcThreads, 4) k_tc_adjoint(const TcAdjParams p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = tc_smem_base(smem_raw);
   const uint32_t tmem = tc_tmem_alloc(reinterpret_cast<uint32_t*>(base + TcAdjShape<NA>::TSLOT));
   const int g = blockIdx.x;
-  tc_adjoint_range<NA>(p, p.begin[g], p.begin[g + 1], g, base, tmem, true);
+  tc_adjoint_range<NA, REDUCE>(p, p.begin[g], p.begin[g + 1], g, base, tmem, true);
   tc_tmem_free(tmem);
 }
 
