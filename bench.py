@@ -502,7 +502,7 @@ def main():
     kernel_names = {"forward": (f"k_tc_forward<{NA}> (spot-stationary: tcgen05 split-tf32 MMA of 128 spots x 64 "
                                 f"pixels into TMEM, sincos + packed complex MAC)") if fwd_tc else
                                f"k_forward<D={p.D},P={P}> (pixel-stationary forward, warp transpose reduction)",
-                    "adjoint": (f"k_tc_adjoint<{NA}, true> (pixel-stationary: tcgen05 split-tf32 MMA of 128 pixels x 64 "
+                    "adjoint": (f"k_tc_adjoint<{NA},true> (pixel-stationary: tcgen05 split-tf32 MMA of 128 pixels x 64 "
                                 f"spots into TMEM, sincos + packed complex MAC, arg epilogue)") if adj_tc else
                                f"k_adjoint<D={p.D},P={P}> (pixel-stationary adjoint, arg epilogue)"}
     achieved = gterm[dom]

@@ -131,3 +131,28 @@ def _check_grad(nx, ny, N, noll, variant=0):
     r2 = np.linalg.norm(dC - dC_ref) / np.linalg.norm(dC_ref)
     assert r1 <= GRAD_TOL and r2 <= GRAD_TOL, (r1, r2)
     return bool(h.launch_info()["kernels"] & 8)
+
+
+def test_grad_tensor_cores_at_large_local_phases():
+    """The gradient's tensor-core passes feed the MUFU the tile-local phase
+    unreduced (they run once per gradient, not inside a loop): strong tilts
+    (0.45 Nyquist), defocus up to 20 rad and larger higher modes give the
+    largest local phases per 32 x 32 tile, where that error is largest. It
+    stays a decade inside the gradient tolerance."""
+    p = random_problem(77, 256, 224, 300, list(range(2, 13)), aberr_sigma=2.0, defocus_max=20.0,
+                       target_range=(0.5, 1.5))
+    h = _holo(p)
+    h.set_variant(2)
+    Z, C, A = oracle_inputs(p)
+    phase = p.phase0.astype(np.float64).ravel()
+    E = transform.forward(transform.field(A, phase), C, Z)
+    gE = ograd.grad_E(E, p.target).astype(np.complex64)
+    dph_ref, dC_ref = ograd.backward(A, phase, C, Z, gE.astype(np.complex128))
+    dph, dC = h.grad(torch.from_numpy(p.phase0).cuda(), torch.from_numpy(gE).cuda())
+    assert h.launch_info()["kernels"] & 10 == 10   # tensor-core adjoint and moment pass
+    dph = dph.cpu().numpy().astype(np.float64).ravel()
+    dC = dC.cpu().numpy().astype(np.float64)
+    r1 = np.linalg.norm(dph - dph_ref) / np.linalg.norm(dph_ref)
+    r2 = np.linalg.norm(dC - dC_ref) / np.linalg.norm(dC_ref)
+    print(f"large local phases: dL/dphi {r1:.3g}, dL/dC {r2:.3g}, max |C.Z| {np.abs(C @ Z).max():.3g}")
+    assert r1 <= 0.1 * GRAD_TOL and r2 <= 0.1 * GRAD_TOL, (r1, r2)
