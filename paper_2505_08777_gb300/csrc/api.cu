@@ -671,6 +671,11 @@ ash_status create_impl(ash_hologram** out, int nx, int ny, int row0, int ny_full
     // MMA chunks per CTA
     h->tc_layout = tc_layout(D, noll, g);
     h->tc_na = h->tc_layout.NA;
+    // the spot-side kernels between tensor-core launches keep the SMs'
+    // shared-memory carveout (see tc_small_kernels_max_shared)
+    for (const void* k : {(const void*)k_wgs_update, (const void*)k_metrics, (const void*)k_spot_loss,
+                          (const void*)k_col_reduce, (const void*)k_fill_c})
+      cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     ce = tc_prepare(h->tc_na, &h->li.tc_adj_ctas_per_sm, &h->li.tc_fwd_ctas_per_sm);
     if (ce != cudaSuccess) return fail(cuda_fail(ce, "tensor-core kernel preparation"));
     h->tc_ok = true;
