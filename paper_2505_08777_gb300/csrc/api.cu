@@ -275,6 +275,8 @@ TcFwdParams tc_fwd_params(const ash_hologram* h, float2* E) {
   p.part = h->tc_part;
   p.spans = h->tfwd_spans;
   p.err = h->err_word;
+  p.claim = h->tfwd_nfull >= 0 ? h->tfwd_claim : nullptr;
+  p.n_full = h->tfwd_nfull;
   return p;
 }
 
@@ -716,9 +718,21 @@ ash_status create_impl(ash_hologram** out, int nx, int ny, int row0, int ny_full
       const int rep = tc_fwd_rep(N);
       const double cheap = rep == 4 ? ASH_FWD_REP4_COST : rep == 2 ? ASH_FWD_REP2_COST : 1.0;
       const long long u_rep = (long long)(f.nb - 1) * f.nq;
-      tfwd_begin = balanced_begins(f.units(), f.G, [&](long long u) {
-        return (double)(u < u_rep ? u : u_rep) + cheap * (double)(u > u_rep ? u - u_rep : 0);
-      });
+      const int per_sm = h->li.tc_fwd_ctas_per_sm;
+      h->tfwd_nfull = -1;
+      if (rep > 1 && f.nb >= 2 && per_sm >= 2 && f.G == sms * per_sm && sms <= kTcClaimSms) {
+        // a replicated last block: one of its ranges per SM, claimed by each
+        // SM's last CTA (tc_claim_range), the full blocks' in the others
+        const int n_full = f.G - sms;
+        tfwd_begin = balanced_begins(u_rep, n_full, [](long long u) { return (double)u; });
+        const std::vector<long long> tail = balanced_begins(f.nq, sms, [](long long u) { return (double)u; });
+        for (int k = 1; k <= sms; ++k) tfwd_begin.push_back(u_rep + tail[k]);
+        h->tfwd_nfull = n_full;
+      } else {
+        tfwd_begin = balanced_begins(f.units(), f.G, [&](long long u) {
+          return (double)(u < u_rep ? u : u_rep) + cheap * (double)(u > u_rep ? u - u_rep : 0);
+        });
+      }
     }
     for (int b = 1; b < f.G; ++b)
       if (tfwd_begin[b] % f.nq != 0) h->tfwd_split = true;
@@ -778,6 +792,7 @@ ash_status create_impl(ash_hologram** out, int nx, int ny, int row0, int ny_full
     if ((st = ws(h, &h->tc_part, (size_t)h->tfwd.G * 2 * kTcRows)) != ASH_OK) return fail(st);
     if ((st = ws(h, &h->tfwd_begin, tfwd_begin.size())) != ASH_OK) return fail(st);
     if ((st = ws(h, &h->tfwd_spans, tfwd_spans.size())) != ASH_OK) return fail(st);
+    if ((st = ws(h, &h->tfwd_claim, (size_t)kTcClaimInts)) != ASH_OK) return fail(st);
     if ((st = ws(h, &h->tadj_begin, tadj_begin.size())) != ASH_OK) return fail(st);
     if ((st = ws(h, &h->tadj_groups, tadj_groups.size() + 1)) != ASH_OK) return fail(st);
   }
@@ -848,6 +863,7 @@ ash_status create_impl(ash_hologram** out, int nx, int ny, int row0, int ny_full
                                 cudaMemcpyHostToDevice, s));
     CREATE_CUDA(cudaMemcpyAsync(h->tfwd_spans, tfwd_spans.data(), tfwd_spans.size() * sizeof(int2),
                                 cudaMemcpyHostToDevice, s));
+    CREATE_CUDA(cudaMemsetAsync(h->tfwd_claim, 0, (size_t)kTcClaimInts * sizeof(int), s));
     CREATE_CUDA(cudaMemcpyAsync(h->tadj_begin, tadj_begin.data(), tadj_begin.size() * sizeof(long long),
                                 cudaMemcpyHostToDevice, s));
     if (!tadj_groups.empty())

@@ -48,6 +48,8 @@ struct ash_hologram {
   float2* tc_part = nullptr;    // [tfwd.G][2][128]
   long long* tfwd_begin = nullptr;   // [tfwd.G + 1] CTA range starts of the forward
   int2* tfwd_spans = nullptr;        // [tfwd.nb] first and last CTA meeting each spot block
+  int* tfwd_claim = nullptr;         // [kTcClaimInts] range-claim counters (SM-aware ranges)
+  int tfwd_nfull = -1;               // ranges of the full spot blocks, or -1: CTA g runs range g
   long long* tadj_begin = nullptr;   // [tadj.G + 1] CTA range starts of the adjoint
   int4* tadj_groups = nullptr;  // (group, first CTA, last CTA, -) of the groups split between adjoint CTA ranges
   int tadj_nsplit = 0;

@@ -565,6 +565,48 @@ static __global__ void k_tc_adjoint_fixup_batch(const TcAdjParams* __restrict__ 
 // range; blocks whose pixels are split between CTAs go through `part` and
 // k_tc_forward_reduce.
 //
+// Range of the forward's units this CTA runs, when the last spot block is
+// replicated. Its chunks carry a quarter (or half) of a full chunk's
+// arithmetic but the same MMAs, so two of its CTAs on one SM make that SM
+// finish last; where the block scheduler puts a launch's CTAs depends on
+// the kernels before it. Each SM's CTAs count themselves on a per-SM
+// counter, and the last of them takes one of the replicated block's ranges
+// (one per SM); the others take the full blocks' ranges in claim order. A CTA
+// whose preferred pool is empty takes from the other, so every range is
+// run exactly once whatever the placement (the results do not depend on
+// which CTA runs a range: each writes its own partial sums).
+__device__ __forceinline__ int tc_claim_range(int* claim, int n_full, int G, unsigned* err) {
+  unsigned smid;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+  const int slot = smid < (unsigned)kTcClaimSms ? atomicAdd(&claim[3 + smid], 1) : 0;
+  const int n_rep = G - n_full;                 // one per SM
+  const int per_sm = n_rep > 0 ? G / n_rep : 1;   // resident CTAs per SM
+  const bool rep_first = slot % per_sm == per_sm - 1;
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool rep = (pass == 0) == rep_first;
+    const int k = atomicAdd(&claim[rep ? 1 : 0], 1);
+    if (k < (rep ? n_rep : n_full)) return rep ? n_full + k : k;
+  }
+  atomicOr(err, kErrClaim);   // more CTAs than ranges: not launched that way
+  return -1;
+}
+
+// The launch's last CTA zeroes the claim counters for the next launch
+// (stream order makes them visible to it).
+__device__ __forceinline__ void tc_claim_done(int* claim, int G) {
+  __shared__ int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(&claim[2], 1) == G - 1;
+  }
+  __syncthreads();
+  if (s_last) {
+    for (int k = threadIdx.x; k < kTcClaimInts; k += blockDim.x) claim[k] = 0;
+    __threadfence();
+  }
+}
+
 // Producer schedule. The warp releasing chunk c last issues the MMAs up to
 // chunk c + 2 (nothing else: the MMA is what the other warps wait for); the
 // warp releasing it first loads B of chunk c + NBB into the slot MMA(c) has
@@ -804,8 +846,12 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_tc_forward(const TcFwdParams 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = tc_smem_base(smem_raw);
   const uint32_t tmem = tc_tmem_alloc(reinterpret_cast<uint32_t*>(base + TcFwdShape<NA>::TSLOT));
-  const int g = blockIdx.x;
-  tc_forward_range<NA>(p, p.begin[g], p.begin[g + 1], g, base, tmem, true);
+  __shared__ int s_range;
+  if (threadIdx.x == 0) s_range = p.claim ? tc_claim_range(p.claim, p.n_full, (int)gridDim.x, p.err) : blockIdx.x;
+  __syncthreads();
+  const int g = s_range;
+  if (g >= 0) tc_forward_range<NA>(p, p.begin[g], p.begin[g + 1], g, base, tmem, true);
+  if (p.claim) tc_claim_done(p.claim, (int)gridDim.x);
   tc_tmem_free(tmem);
 }
 

@@ -16,6 +16,7 @@ constexpr int kTcChunksPerTile = kTilePix / kTcChunk;  // 16 chunks of 64 pixels
 constexpr int kTcGroupsPerTile = kTilePix / kTcRows;   // 8 groups of 128 pixels
 constexpr unsigned kTcWaitPolls = 1u << 24;
 constexpr unsigned kErrTimeout = 2u;
+constexpr unsigned kErrClaim = 4u;      // a forward CTA found no range to claim
 constexpr int kTcMaxModes = 21;                        // 3 D <= 64
 
 // K layout of the operand rows. Regular: the pixel row [hi | lo | hi] and the
@@ -211,7 +212,17 @@ struct TcFwdParams {
   float2* part;           // [G][2][128] partial sums of spot blocks split between CTAs
   const int2* spans;      // [nb] first and last CTA meeting each spot block (host-tabulated)
   unsigned* err;
+  // SM-aware range claiming (null: CTA g runs range g). Ranges [0, n_full)
+  // cover the full spot blocks, [n_full, G) the replicated last block, one
+  // per SM: each SM's fourth CTA takes a range of the latter (see
+  // tc_claim_range). claim: [0] next full range, [1] next replicated range,
+  // [2] CTAs done, [3 + smid] CTAs started on that SM; the last CTA of a
+  // launch zeroes it for the next.
+  int* claim;
+  int n_full;
 };
+constexpr int kTcClaimSms = 1024;                 // bound on %smid values
+constexpr int kTcClaimInts = 3 + kTcClaimSms;
 
 // Coefficient-gradient moments on the tensor cores (one K-atom, D <= 12,
 // polynomial basis of total degree ORD <= 4): spot-stationary like the

@@ -422,3 +422,54 @@ def _caught(cls, per_range):
 @pytest.mark.parametrize("cls,per", [(ForwardRingTooSmall, 5), (ForwardThreeAhead, 5), (AdjointEarlyA, 3)])
 def test_planted_schedule_mistakes_are_caught(cls, per):
     assert _caught(cls, per)
+
+
+# SM-aware range claiming of the forward (tc_claim_range): G CTAs claim G
+# ranges, [0, n_full) of the full spot blocks and one per SM of the
+# replicated last block. Every range must be run exactly once whatever the
+# placement; with per_sm CTAs on every SM, each SM runs exactly one
+# replicated range.
+
+def claim_ranges(placement, n_full, G, order):
+    """placement[c] = SM of CTA c; order: the order in which CTAs claim."""
+    per_sm_ctr, pools = {}, [0, 0]
+    n_rep = G - n_full
+    per_sm = G // n_rep if n_rep > 0 else 1
+    got = {}
+    for c in order:
+        sm = placement[c]
+        slot = per_sm_ctr.get(sm, 0)
+        per_sm_ctr[sm] = slot + 1
+        rep_first = slot % per_sm == per_sm - 1
+        got[c] = -1
+        for pas in range(2):
+            rep = (pas == 0) == rep_first
+            k = pools[1 if rep else 0]
+            pools[1 if rep else 0] += 1
+            if k < (n_rep if rep else n_full):
+                got[c] = n_full + k if rep else k
+                break
+    return got
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_claimed_ranges_cover_every_range_once(seed):
+    rng = random.Random(seed)
+    sms, per_sm = rng.choice([(152, 4), (148, 4), (20, 2), (7, 3)])
+    G = sms * per_sm
+    n_full = G - sms
+    if seed % 2:
+        placement = [c // per_sm for c in range(G)]            # per_sm CTAs on every SM
+        rng.shuffle(placement)
+    else:
+        placement = [rng.randrange(sms) for _ in range(G)]     # uneven placement
+    order = list(range(G))
+    rng.shuffle(order)
+    got = claim_ranges(placement, n_full, G, order)
+    assert sorted(got.values()) == list(range(G))
+    if seed % 2:
+        rep_per_sm = {}
+        for c, r in got.items():
+            if r >= n_full:
+                rep_per_sm[placement[c]] = rep_per_sm.get(placement[c], 0) + 1
+        assert sorted(rep_per_sm.values()) == [1] * sms
