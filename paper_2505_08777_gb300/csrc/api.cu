@@ -720,9 +720,12 @@ ash_status create_impl(ash_hologram** out, int nx, int ny, int row0, int ny_full
       const long long u_rep = (long long)(f.nb - 1) * f.nq;
       const int per_sm = h->li.tc_fwd_ctas_per_sm;
       h->tfwd_nfull = -1;
-      if (rep > 1 && f.nb >= 2 && per_sm >= 2 && f.G == sms * per_sm && sms <= kTcClaimSms) {
+      if (rep > 1 && f.nb >= 2 && per_sm >= 2 && f.G == sms * per_sm && sms <= kTcClaimSms &&
+          f.units() >= 32LL * f.G) {
         // a replicated last block: one of its ranges per SM, claimed by each
-        // SM's last CTA (tc_claim_range), the full blocks' in the others
+        // SM's last CTA (tc_claim_range), the full blocks' in the others.
+        // Only for ranges of 32 chunks or more: claiming costs about 2 us
+        // per launch, a tenth of a small forward.
         const int n_full = f.G - sms;
         tfwd_begin = balanced_begins(u_rep, n_full, [](long long u) { return (double)u; });
         const std::vector<long long> tail = balanced_begins(f.nq, sms, [](long long u) { return (double)u; });
