@@ -433,7 +433,8 @@ ash_status ash_grad(ash_hologram *h, const float *phase, const float *grad_E, fl
  *    (forward), (adjoint), CTAs of the tensor-core adjoint and of the
  *    tensor-core forward (0 if not available), split flags (bit 0: FMA schedule
  *    splits tiles, bit 1: tensor-core schedule splits sub-tiles, bit 2:
- *    the tensor-core forward splits spot blocks), kernels in use (adjoint:
+ *    the tensor-core forward splits spot blocks, bit 3: the tensor-core
+ *    forward's CTAs claim their ranges by SM), kernels in use (adjoint:
  *    1 FMA or 2 tensor core, plus 4 if the forward and 8 if the
  *    coefficient-gradient moments use the tensor core), pixels per thread}.
  */

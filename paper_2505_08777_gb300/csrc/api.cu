@@ -1164,7 +1164,8 @@ ash_status ash_hologram_launch_info(const ash_hologram* h, int* out) {
   out[2] = h->li.adj_ctas_per_sm;
   out[3] = h->tc_ok ? h->tadj.G : 0;
   out[4] = h->tc_ok ? h->tfwd.G : 0;
-  out[5] = (h->split_tiles ? 1 : 0) | (h->tadj_split ? 2 : 0) | (h->tfwd_split ? 4 : 0);
+  out[5] = (h->split_tiles ? 1 : 0) | (h->tadj_split ? 2 : 0) | (h->tfwd_split ? 4 : 0) |
+           (h->tfwd_nfull >= 0 ? 8 : 0);
   out[6] = (use_tc_adj(h) ? 2 : 1) | (use_tc_fwd(h) ? 4 : 0) | (use_tc_grad(h) ? 8 : 0);
   out[7] = h->g.P;
   return ASH_OK;

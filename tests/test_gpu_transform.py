@@ -260,3 +260,23 @@ def test_forward_kernel_variants_agree_with_oracle(nx, ny, N, noll, dmax):
         assert_close(E, E_ref, what=f"forward variant {variant}")
         Ef = h.forward_field(torch.from_numpy(x).cuda()).cpu().numpy()
         assert_close(Ef, Ef_ref, what=f"forward_field variant {variant}")
+
+
+@pytest.mark.parametrize("N", [530, 560])
+def test_forward_with_ranges_claimed_by_sm(N):
+    """A replicated last spot block (N mod 128 <= 64) on a grid large enough
+    that the tensor-core forward claims its CTA ranges by SM (every range of
+    32 chunks or more): against the oracle, bitwise identical over repeated
+    launches (which CTA runs a range changes, each range's arithmetic does
+    not), forward after forward, and with no error raised."""
+    p = random_problem(900 + N, 512, 512, N, list(range(2, 12)), defocus_max=6.0)
+    h = _holo(p)
+    li = h.launch_info()
+    assert li["kernels"] & 4 and li["split_flags"] & 8   # tensor-core forward, ranges claimed by SM
+    ph = torch.from_numpy(p.phase0).cuda()
+    outs = [h.forward(ph).cpu().numpy() for _ in range(4)]
+    torch.cuda.synchronize()
+    h.check()
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+    assert_close(outs[0], oracle_forward(p, p.phase0, workers=8), what=f"forward N={N} (ranges claimed by SM)")
