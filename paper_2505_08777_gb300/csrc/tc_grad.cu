@@ -53,7 +53,7 @@ __global__ void k_tc_tile_poly(const Geometry G, const MonoTerm* __restrict__ te
 
 // Shared memory of the moment kernel: A (spot block), B ring and f ring.
 struct TcGradShape {
-  static constexpr int NBB = 4, KF = 3, NF = KF + 3;
+  static constexpr int NBB = 4, KF = 5, NF = KF + 3;   // as the forward's rings
   static constexpr uint32_t A_BYTES = 16384, B_BYTES = 8192, F_BYTES = 512;
   static constexpr uint32_t FSLOT = F_BYTES;
   static constexpr int NBARS = 3 + NBB + NF;

@@ -59,7 +59,8 @@ struct TcAdjShape {
 // arithmetic is short (a partial last spot block).
 template <int NA>
 struct TcFwdShape {
-  static constexpr int NBB = NA == 1 ? 4 : 3, KF = 3, NF = KF + 3;
+  // KF = 5 (an 8-slot f ring) measured 1-2 % faster than 3, 4, 7 or 10
+  static constexpr int NBB = NA == 1 ? 4 : 3, KF = 5, NF = KF + 3;
   static constexpr uint32_t A_BYTES = NA * 16384, B_BYTES = NA * 8192, F_BYTES = 512;
   static constexpr int NBARS = 3 + NBB + NF;
   // [alignment slack][A][B ring][f ring][barriers][armed counts][counter][TMEM slot][producer state]

@@ -108,7 +108,7 @@ class ForwardModel(Pipeline):
     """tc_forward_range: spot blocks of nq pixel chunks; this range covers
     units u0 .. u0 + nc - 1 (unit u = block u // nq, pixel chunk u % nq)."""
 
-    NBB, KF, NF = 4, 3, 6
+    NBB, KF, NF = 4, 5, 8
 
     def __init__(self, rng, nc, nq, u0):
         super().__init__(rng, nc)
